@@ -1,0 +1,373 @@
+"""Benchmark: Gedges/s of y = x A on the BV-delta layout (uncompressed edges m
+per second), beside the plain CSR product on the same GPU and the seconds of
+PageRank to L1 < 1e-8, on a synthetic web-like graph of n = 862,664 nodes and
+~19.2 M edges (copying model; stands in for a web crawl of that size).
+
+One step = one product y = x A through the C ABI (push-chain kernel + push-
+gather kernel), inputs resident in HBM, L2 flushed (256 MiB write) before
+every timed step. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bv|reference] [--k K]
+
+--impl reference times the CPU oracle (the plain FP64 compressed product of
+Sec. 4 in C, single thread) on the same workload.
+Under torchrun each rank runs its own replica (weak scaling, no collective
+on the data path); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gedges/s of x·A on BV layout vs CSR SpMV on GB300; PageRank s to L1<1e-8"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="bv", choices=["bv", "reference"])
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload_spec():
+    import synth
+    return synth.web_862k()
+
+
+def workload_name(g):
+    return f"web-like copying model n={g.n:,} m={g.m:,} (row copy p=0.8, window 7)"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.dev = device_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi():
+    import torch
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        return vis or "0"
+
+
+# ----------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel: str, source_digest: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (line 'traffic_bytes_per_launch: <B> source: <digest>')."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.startswith(kernel) or not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(d, fn)):
+            m = re.match(r"\s*traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source:\s*([0-9a-f]+)", line)
+            if m and m.group(2) == source_digest:
+                return float(m.group(1))
+    return None
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_1708_07271_gb300", "csrc"))):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(ROOT, "paper_1708_07271_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- CPU oracle
+def cpu_oracle_run(g, k, seconds, max_runs=None):
+    """Times the oracle's compressed product (Sec. 4 push form, FP64, 1 thread)."""
+    import oracle
+    import synth
+    ref, _ = oracle.choose_refs(g.row_ptr, g.col)
+    x = synth.rhs(g.n, k, synth.seed_for(2, 1)).astype(np.float64)
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.bv_xA(g.row_ptr, g.col, ref, x)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all >= seconds and len(times) >= 3:
+            break
+        if max_runs and len(times) >= max_runs:
+            break
+    return times
+
+
+def run_reference(args):
+    import synth
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    g = synth.copying_model(workload_spec())
+    # each step is one full product of the oracle
+    for _ in range(max(0, args.warmup)):
+        cpu_oracle_run(g, args.k, 0.0, max_runs=1)
+    times = []
+    for _ in range(args.steps):
+        times += cpu_oracle_run(g, args.k, 0.0, max_runs=1)
+    t = float(np.sum(times))
+    val = g.m * args.k * args.steps / t / 1e9
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gedges/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(g), "k": args.k, "parallelism": "single CPU thread"},
+        "cpu_baseline": {"value": val, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full products of the oracle's compressed x A (FP64, C, 1 thread)"},
+        "e2e": {"value": val, "unit": "Gedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_bv(args):
+    import torch
+    import synth
+    import paper_1708_07271_gb300 as bvg
+    from paper_1708_07271_gb300 import bytemodel
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    k = args.k
+    g = synth.copying_model(workload_spec())
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    st = bvg.bvg_stats(hg)
+    dg = bvg.bvg_upload(hg)
+    L = bvg.bvg_dev_layout(dg)
+    cg = bvg.bvg_csr_upload(g.row_ptr, g.col)
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(synth.rhs(g.n, k, synth.seed_for(2, 1))).cuda()
+    if k == 1:
+        x = x.reshape(-1)
+    y = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps, trace_graph=None):
+        """per-step CUDA-event time (ms) with an L2 flush before each step."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    xa = lambda: bvg.bvg_spmv_xA(dg, x, y)  # noqa: E731
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        xa()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps of x A
+    sampler = ClockSampler(gpu_id_for_smi()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    bvg.bvg_trace_enable(dg, True)
+    barrier()
+    step_ms = timed(xa, args.steps)
+    barrier()
+    trace = bvg.bvg_trace_read(dg)
+    bvg.bvg_trace_enable(dg, False)
+    clocks = sampler.stop() if sampler else None
+    t_total = max_over_ranks(float(np.sum(step_ms)))
+    value = world * g.m * k * args.steps / (t_total * 1e-3) / 1e9
+    launches = sum(v[0] for v in trace.values())
+
+    # ---- roofline of the dominant kernel (largest share of the step)
+    peak, peak_kind = measured_peaks()
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    dom_bytes = {"push_gather": bytemodel.push_gather(L, k), "push_chain": bytemodel.push_chain(L, k)}[dom_name]
+    dom_avg_s = dom_ms / dom_launches * 1e-3
+    achieved = dom_bytes / dom_avg_s / 1e9
+    traffic = profile_traffic(dom_name, kernel_source_digest())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom_name, "algorithmic_bytes": dom_bytes,
+                "avg_launch_us": dom_avg_s * 1e6, "peak_kind": f"{peak_kind} HBM copy",
+                "share": dom_ms / sum(v[1] for v in trace.values()),
+                "kernels": {kk: {"launches": vv[0], "avg_us": 1e3 * vv[1] / vv[0]} for kk, vv in trace.items()}}
+
+    # ---- same protocol: CSR baseline, pull product
+    csr_ms = timed(lambda: bvg.bvg_csr_spmv_xA(cg, x, y), args.steps)
+    pull_ms = timed(lambda: bvg.bvg_spmv_Ax(dg, x, y), args.steps)
+    csr_ax_ms = timed(lambda: bvg.bvg_csr_spmv_Ax(cg, x, y), args.steps)
+    gedges = lambda ms: g.m * k * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    hx = torch.from_numpy(synth.rhs(g.n, k, synth.seed_for(2, 1))).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    for _ in range(2):
+        bvg.bvg_spmv_xA_host(dg, hx, hy)
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bvg.bvg_spmv_xA_host(dg, hx, hy)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(float(np.sum(e2e_s)))
+    e2e = {"value": world * g.m * k * args.steps / e2e_total / 1e9, "unit": "Gedges/s",
+           "h2d_bytes_per_step": int(hx.numel() * 4), "d2h_bytes_per_step": int(hy.numel() * 4)}
+
+    # ---- PageRank to L1 < 1e-8, uniform start, single vector
+    pr_runs = []
+    p = torch.empty(g.n, device="cuda")
+    bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000, out=p)
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000, out=p)
+        pr_runs.append((time.perf_counter() - t0, iters, float(res[0]), rc))
+    pr_runs.sort()
+    pr_s, pr_it, pr_res, pr_rc = pr_runs[len(pr_runs) // 2]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = cpu_oracle_run(g, k, args.cpu_seconds)
+        cpu = {"value": g.m * k / float(np.mean(times)) / 1e9, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} full products of the oracle's compressed x A (FP64, C, 1 thread) on the "
+                         f"same graph, {np.sum(times):.1f} s; host has {os.cpu_count()} cores"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(g), "k": k,
+                       "l2": "flushed by a 256 MiB write before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "csr_gedges_s": gedges(csr_ms), "bv_over_csr": float(np.sum(csr_ms) / np.sum(step_ms)),
+            "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
+            "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
+                         "start": "uniform", "k": 1},
+            "compression": {"m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
+                            "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"],
+                            "structure_MB": L["structure_bytes"] / 1e6},
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_bv(args)
+
+
+if __name__ == "__main__":
+    main()

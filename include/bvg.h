@@ -1,0 +1,216 @@
+/*
+ * bvg.h -- C ABI of the BV-delta adjacency-product library for GB300 (sm_103a).
+ *
+ * The library computes y = A x^T and y = x A for a binary adjacency matrix A
+ * directly on a reference/difference ("BV-delta") representation of A, and
+ * PageRank on top of x A (Francisco, Gagie, Ladra, Navarro, "Exploiting
+ * Computation-Friendly Graph Compression Methods for Adjacency-Matrix
+ * Multiplication", Sec. 3-5).
+ *
+ * Representation (Sec. 4): row i of A is v_i; a reference r_i < i within a
+ * window of W rows is chosen for each row (or none, the sentinel v_0 = 0),
+ * and the difference row a'_i = v_i - v_{r_i} is stored: ids of v_{r_i}
+ * missing from v_i (dropped, -1 entries), and ids added to it, split into
+ * intervals (runs of >= min_interval consecutive ids) and residual ids.
+ * Chains of references are at most max_chain long.
+ *
+ * Conventions for every call:
+ *   - Return value: BVG_OK (0) or a negative bvg_status. No exception or
+ *     abort crosses the ABI. bvg_last_error() gives a one-line reason for the
+ *     last failure on the calling thread.
+ *   - Ids are 0-based; n < 2^30 (two tag bits of a 32-bit word are used by
+ *     the device layout).
+ *   - Vectors with k right-hand sides are row-major n x k FP32 with leading
+ *     dimension ld >= k (element (i, c) at ptr[i * ld + c]); device pointers
+ *     must be 4-byte aligned, and 16-byte aligned with ld % 4 == 0 to use
+ *     128-bit loads (otherwise narrower loads are used).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Device calls are asynchronous on that stream unless stated.
+ *   - The caller owns every vector buffer; the library owns handles and their
+ *     device memory and frees them only in bvg_free_*().
+ *   - Handles are immutable after creation (bvg_autotune only updates the
+ *     launch configuration stored in it); concurrent calls that use one
+ *     handle must use one stream, since a handle holds scratch buffers.
+ */
+#ifndef BVG_H
+#define BVG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BVG_OK = 0,
+    BVG_ERR_INVALID_ARG = -1,   /* NULL or out-of-range argument, misaligned pointer */
+    BVG_ERR_BAD_GRAPH = -2,     /* CSR not sorted, duplicate or out-of-range ids */
+    BVG_ERR_OOM = -3,           /* host or device allocation failed */
+    BVG_ERR_CUDA = -4,          /* a CUDA runtime call failed */
+    BVG_ERR_NOT_CONVERGED = -5, /* PageRank hit max_iter; outputs hold the last iterate */
+    BVG_ERR_NUMERIC = -6,       /* NaN/Inf met (e.g. in a PageRank iterate) */
+    BVG_ERR_TIMEOUT = -7,       /* a bounded device wait ran out */
+    BVG_ERR_CORRUPT = -8,       /* bitstream fails to decode */
+    BVG_ERR_UNSUPPORTED = -9    /* size or option outside what this build handles */
+} bvg_status;
+
+typedef struct bvg_host_graph bvg_host_graph; /* host encoding: refs, difference rows, bitstream */
+typedef struct bvg_dev_graph bvg_dev_graph;   /* device-resident BV-delta layout + scratch */
+typedef struct bvg_csr_graph bvg_csr_graph;   /* device CSR of A and of A^T (plain baseline) */
+typedef struct bvg_batch bvg_batch;           /* many device graphs for one persistent launch */
+typedef struct bvg_mlp bvg_mlp;               /* warm-start network 6 -> 64 -> 64 -> 1 */
+
+/* Encoder parameters (Sec. 4: window W; chain bound and interval length are
+ * this library's choices). Zero fields take the defaults shown. */
+typedef struct {
+    int32_t window;       /* W, candidates r in [i - W, i - 1]; default 7, max 7 */
+    int32_t max_chain;    /* R, longest reference chain; default 3, max 3 */
+    int32_t min_interval; /* shortest run stored as an interval; default 4 */
+    int32_t threads;      /* host threads for the cost pass; 0 = hardware concurrency */
+} bvg_encode_params;
+
+/* Sizes of an encoding. nnz_diff is nnz(A') (Table 1's m'); words is what the
+ * device layout stores per row: dropped + residual + 2 * intervals. */
+typedef struct {
+    int64_t n, m;
+    int64_t dropped, added, residual, intervals, interval_members;
+    int64_t nnz_diff, words, rows_with_ref;
+    int64_t depth_hist[4];   /* rows per chain depth 0..3 */
+    int64_t bitstream_bits;  /* size of the gamma/delta-coded bitstream */
+    double bits_per_edge;    /* bitstream_bits / m */
+    int64_t device_bytes;    /* structure bytes of the device layout (both orientations) */
+} bvg_graph_stats;
+
+/* PageRank parameters (Sec. 3, Eq. 1). alpha = 1 - damping is the teleport
+ * probability. */
+typedef struct {
+    double damping;   /* 1 - alpha; default 0.85 when 0 */
+    double tol_l1;    /* stop when ||p_t - p_{t-1}||_1 < tol_l1 in every column */
+    int32_t max_iter; /* bound on the number of updates; default 1000 when 0 */
+    int32_t dangling; /* mass of zero-out-degree rows: 0 = along p0, 1 = uniform */
+} bvg_pr_params;
+
+/* ---------------------------------------------------------------- host side */
+
+/* Encodes the binary matrix given by CSR (row_ptr: n+1 entries, row_ptr[0] = 0,
+ * nondecreasing; col_idx: row_ptr[n] ids, strictly increasing within a row,
+ * 0 <= id < n). Chooses references (Sec. 4 window, Sec. 5 keep-raw rule:
+ * a reference is kept only if it is strictly cheaper than the raw row and
+ * |v_i - v_r| < |v_i|), splits each difference row, and writes the bitstream.
+ * Host-only and synchronous; the inputs are copied. *out is owned by the
+ * caller (bvg_free_host). Errors: INVALID_ARG, BAD_GRAPH, UNSUPPORTED, OOM. */
+int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+               const bvg_encode_params* params, bvg_host_graph** out);
+
+/* Decodes the bitstream of `g` back into CSR. row_ptr (n+1) and col_idx (m)
+ * are caller-allocated host arrays. decode(encode(A)) == A bit for bit.
+ * Errors: INVALID_ARG, CORRUPT. */
+int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx);
+
+/* Fills *out with the sizes of the encoding. */
+int bvg_stats(const bvg_host_graph* g, bvg_graph_stats* out);
+
+/* Copies the reference vector (r_i, or -1 for none; n entries) and, if
+ * depth != NULL, the chain depth of every row. */
+int bvg_get_refs(const bvg_host_graph* g, int32_t* ref, int32_t* depth);
+
+/* Number of rows n and edges m of an encoding. */
+int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
+
+/* -------------------------------------------------------------- device side */
+
+/* Builds the device layout of `g` (row-major difference rows for A x^T, the
+ * same entries grouped by column for x A, per-row reference offsets and
+ * chain depths, 1/outdeg) and copies it to the current device on `stream`.
+ * Also allocates the scratch the products use, so no later product call
+ * allocates. The host graph may be freed after this returns. *out is owned
+ * by the caller (bvg_free_dev). Errors: INVALID_ARG, OOM, CUDA. */
+int bvg_upload(const bvg_host_graph* g, void* stream, bvg_dev_graph** out);
+
+/* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j, evaluated per
+ * row tile with the chains resolved in shared memory. x, y: device n x k,
+ * leading dimension ld. Asynchronous. Errors: INVALID_ARG, CUDA. */
+int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+
+/* y = x A (push, Proposition 1 read for the left product): z_k = sum of x_i
+ * over rows whose chain passes through k (x pushed down the reference chains
+ * in reverse level order), then y = sum_k z_k a'_k, gathered per column with
+ * no atomics (deterministic). x, y: device n x k. Asynchronous. */
+int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+
+/* Same as bvg_spmv_xA with x and y in HOST memory (pinned or pageable):
+ * copies x to device scratch, runs the product, copies y back, and
+ * synchronises `stream` before returning. ld == k. */
+int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host, int32_t k, void* stream);
+
+/* PageRank by power iteration, Eq. (1): p_t = alpha p0 + (1 - alpha) p_{t-1} M,
+ * M = D^-1 A, for k teleport vectors at once (columns of p0, device n x k;
+ * NULL = uniform 1/n, then k must be 1). p_init (device n x k or NULL =
+ * start from p0) is the starting iterate. Iterates are FP32; the dangling
+ * mass, the normalisation sum and the L1 change are FP64 on the device.
+ * Stops after the first update with ||p_t - p_{t-1}||_1 < tol in every
+ * column, or after max_iter updates. On return p_out (device n x k) holds the
+ * last iterate normalised to sum 1 per column, *iters_out the number of
+ * updates and resid_out[c] (host, k entries, may be NULL) the last L1 change.
+ * Synchronises `stream`. Errors: INVALID_ARG, CUDA, NOT_CONVERGED (outputs
+ * valid), NUMERIC. */
+int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0, const float* p_init,
+                 int32_t k, float* p_out, int32_t* iters_out, double* resid_out, void* stream);
+
+/* Number of rows n of a device graph. */
+int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);
+
+/* Sizes of the device layout, for byte models: 32-bit words of the row-major
+ * difference rows and of the column-major entries, carry-list entries
+ * (interval sources open at each 128-column tile start), structure bytes. */
+typedef struct {
+    int64_t n, m, words, col_entries, carry_tiles, carry_entries, structure_bytes;
+} bvg_layout_info;
+int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
+
+/* --------------------------------------------------- plain CSR baseline */
+
+/* Device CSR of A and of A^T built from a host CSR (same input rules as
+ * bvg_encode), for the plain sparse product the compressed one is compared
+ * with (Sec. 5 compares A' against A). */
+int bvg_csr_upload(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, void* stream,
+                   bvg_csr_graph** out);
+/* y = A x^T over the CSR of A (row per thread group, no atomics). */
+int bvg_csr_spmv_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+/* y = x A over the CSR of A^T (same kernel, transposed pattern). */
+int bvg_csr_spmv_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+
+/* -------------------------------------------------------------- tracing */
+
+/* Per-kernel timing: while enabled, every kernel the library launches for
+ * graph `g` is bracketed by two CUDA events on the launching stream. */
+typedef struct {
+    char name[32];     /* kernel family, e.g. "push_gather" */
+    int64_t launches;  /* launches recorded since the last read */
+    double total_ms;   /* sum of event-measured durations */
+} bvg_trace_entry;
+
+/* Turns tracing on (enable != 0) or off. Enabling allocates a pool of events
+ * (host-side setup; call outside any stream capture). */
+int bvg_trace_enable(bvg_dev_graph* g, int enable);
+/* Waits for the recorded events, aggregates them per kernel family into out
+ * (at most cap entries; *count = families written) and clears the record.
+ * Launches beyond the pool (65536 per read) are not recorded. */
+int bvg_trace_read(bvg_dev_graph* g, bvg_trace_entry* out, int32_t cap, int32_t* count);
+
+/* ------------------------------------------------------------- lifetime */
+
+void bvg_free_host(bvg_host_graph* g);
+void bvg_free_dev(bvg_dev_graph* g);
+void bvg_free_csr(bvg_csr_graph* g);
+
+/* Static description of a status code. */
+const char* bvg_status_string(int status);
+/* Reason for the last failure on this thread ("" if none). */
+const char* bvg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BVG_H */

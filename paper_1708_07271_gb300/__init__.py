@@ -1,0 +1,353 @@
+"""Python binding of libbvg (include/bvg.h): BV-delta adjacency products and
+PageRank on GB300.
+
+Argument marshalling only: every step of the products runs in the CUDA
+kernels of libbvg.so. PyTorch supplies device memory and streams. The
+functions keep the C names. If the library is missing (not built) every call
+raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+BVG_OK = 0
+BVG_ERR_INVALID_ARG = -1
+BVG_ERR_BAD_GRAPH = -2
+BVG_ERR_OOM = -3
+BVG_ERR_CUDA = -4
+BVG_ERR_NOT_CONVERGED = -5
+BVG_ERR_NUMERIC = -6
+BVG_ERR_TIMEOUT = -7
+BVG_ERR_CORRUPT = -8
+BVG_ERR_UNSUPPORTED = -9
+
+EXPORTED = [
+    "bvg_encode", "bvg_decode", "bvg_stats", "bvg_get_refs", "bvg_host_size", "bvg_upload", "bvg_spmv_Ax",
+    "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
+    "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
+    "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout",
+]
+
+
+class BvgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+
+class EncodeParams(ctypes.Structure):
+    _fields_ = [("window", _I32), ("max_chain", _I32), ("min_interval", _I32), ("threads", _I32)]
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n", _I64), ("m", _I64), ("dropped", _I64), ("added", _I64), ("residual", _I64),
+                ("intervals", _I64), ("interval_members", _I64), ("nnz_diff", _I64), ("words", _I64),
+                ("rows_with_ref", _I64), ("depth_hist", _I64 * 4), ("bitstream_bits", _I64),
+                ("bits_per_edge", ctypes.c_double), ("device_bytes", _I64)]
+
+
+class LayoutInfo(ctypes.Structure):
+    _fields_ = [(f, _I64) for f in ("n", "m", "words", "col_entries", "carry_tiles", "carry_entries",
+                                      "structure_bytes")]
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _I64), ("total_ms", ctypes.c_double)]
+
+
+class PrParams(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_double), ("tol_l1", ctypes.c_double), ("max_iter", _I32), ("dangling", _I32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Loads libbvg.so (building it first if asked and out of date)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libbvg.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        sig = {
+            "bvg_encode": ([_I64, _P, _P, ctypes.POINTER(EncodeParams), ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_decode": ([_P, _P, _P], ctypes.c_int),
+            "bvg_stats": ([_P, ctypes.POINTER(GraphStats)], ctypes.c_int),
+            "bvg_get_refs": ([_P, _P, _P], ctypes.c_int),
+            "bvg_host_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_upload": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_spmv_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_spmv_xA_host": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+            "bvg_pagerank": ([_P, ctypes.POINTER(PrParams), _P, _P, _I32, _P, ctypes.POINTER(_I32),
+                              _P, _P], ctypes.c_int),
+            "bvg_dev_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_csr_upload": ([_I64, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_csr_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_csr_spmv_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_free_host": ([_P], None),
+            "bvg_free_dev": ([_P], None),
+            "bvg_free_csr": ([_P], None),
+            "bvg_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "bvg_last_error": ([], ctypes.c_char_p),
+            "bvg_trace_enable": ([_P, ctypes.c_int], ctypes.c_int),
+            "bvg_dev_layout": ([_P, ctypes.POINTER(LayoutInfo)], ctypes.c_int),
+            "bvg_trace_read": ([_P, ctypes.POINTER(TraceEntry), _I32, ctypes.POINTER(_I32)], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str, allow=()):
+    if rc != BVG_OK and rc not in allow:
+        lib = load(False)
+        raise BvgError(rc, f"{what}: {lib.bvg_status_string(rc).decode()}: {lib.bvg_last_error().decode()}")
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class HostGraph:
+    """Owns a bvg_host_graph*."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_host(self.ptr)
+            self.ptr = None
+
+
+class DevGraph:
+    """Owns a bvg_dev_graph*."""
+
+    def __init__(self, ptr, n, m):
+        self.ptr, self.n, self.m = ptr, n, m
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_dev(self.ptr)
+            self.ptr = None
+
+
+class CsrGraph:
+    def __init__(self, ptr, n, m):
+        self.ptr, self.n, self.m = ptr, n, m
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_csr(self.ptr)
+            self.ptr = None
+
+
+def _csr_arrays(row_ptr, col):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    return rp, ci, len(rp) - 1
+
+
+def bvg_encode(row_ptr, col, window=7, max_chain=3, min_interval=4, threads=0) -> HostGraph:
+    lib = load()
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    prm = EncodeParams(window, max_chain, min_interval, threads)
+    out = _P()
+    _check(lib.bvg_encode(n, rp.ctypes.data, ci.ctypes.data if len(ci) else None, ctypes.byref(prm),
+                          ctypes.byref(out)), "bvg_encode")
+    return HostGraph(out)
+
+
+def bvg_host_size(hg: HostGraph):
+    n, m = _I64(), _I64()
+    _check(load().bvg_host_size(hg.ptr, ctypes.byref(n), ctypes.byref(m)), "bvg_host_size")
+    return n.value, m.value
+
+
+def bvg_decode(hg: HostGraph):
+    n, m = bvg_host_size(hg)
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(max(m, 1), np.int32)
+    _check(load().bvg_decode(hg.ptr, rp.ctypes.data, ci.ctypes.data), "bvg_decode")
+    return rp, ci[:m]
+
+
+def bvg_stats(hg: HostGraph) -> dict:
+    st = GraphStats()
+    _check(load().bvg_stats(hg.ptr, ctypes.byref(st)), "bvg_stats")
+    d = {name: getattr(st, name) for name, _ in GraphStats._fields_}
+    d["depth_hist"] = list(st.depth_hist)
+    return d
+
+
+def bvg_get_refs(hg: HostGraph):
+    n, _ = bvg_host_size(hg)
+    ref = np.empty(n, np.int32)
+    depth = np.empty(n, np.int32)
+    _check(load().bvg_get_refs(hg.ptr, ref.ctypes.data, depth.ctypes.data), "bvg_get_refs")
+    return ref, depth
+
+
+def bvg_upload(hg: HostGraph, stream=None) -> DevGraph:
+    lib = load()
+    out = _P()
+    _check(lib.bvg_upload(hg.ptr, _stream(stream), ctypes.byref(out)), "bvg_upload")
+    n, m = _I64(), _I64()
+    lib.bvg_dev_size(out, ctypes.byref(n), ctypes.byref(m))
+    return DevGraph(out, n.value, m.value)
+
+
+def _km(t, n):
+    """(k, ld) of a row-major n x k tensor (1-D means k = 1)."""
+    if t.dim() == 1:
+        if t.shape[0] != n or t.stride(0) != 1:
+            raise ValueError("vector must be contiguous with n entries")
+        return 1, 1
+    if t.dim() != 2 or t.shape[0] != n or t.stride(1) != 1:
+        raise ValueError("expected a row-major n x k tensor")
+    return t.shape[1], t.stride(0)
+
+
+def _fp32_cuda(*ts):
+    import torch
+    for t in ts:
+        if t is None:
+            continue
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError("tensors must be float32 CUDA tensors")
+
+
+def bvg_spmv_Ax(g: DevGraph, x, y, stream=None):
+    """y = A x^T on the device (x, y: float32 CUDA tensors, n or n x k)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    if _km(y, g.n) != (k, ld):
+        raise ValueError("x and y must have the same shape and strides")
+    _check(load().bvg_spmv_Ax(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_spmv_Ax")
+    return y
+
+
+def bvg_spmv_xA(g: DevGraph, x, y, stream=None):
+    """y = x A on the device."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    if _km(y, g.n) != (k, ld):
+        raise ValueError("x and y must have the same shape and strides")
+    _check(load().bvg_spmv_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_spmv_xA")
+    return y
+
+
+def bvg_spmv_xA_host(g: DevGraph, x, y, stream=None):
+    """y = x A with x, y in host memory (numpy float32 or CPU tensors, n x k contiguous)."""
+    def ptr(a):
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float32 or not a.flags.c_contiguous:
+                raise ValueError("host arrays must be contiguous float32")
+            return a.ctypes.data, (a.shape[1] if a.ndim == 2 else 1)
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors")
+        return a.data_ptr(), (a.shape[1] if a.dim() == 2 else 1)
+    xp, k = ptr(x)
+    yp, k2 = ptr(y)
+    if k != k2:
+        raise ValueError("x and y must have the same shape")
+    _check(load().bvg_spmv_xA_host(g.ptr, xp, yp, k, _stream(stream)), "bvg_spmv_xA_host")
+    return y
+
+
+def bvg_pagerank(g: DevGraph, p0=None, p_init=None, k=1, damping=0.85, tol=1e-8, max_iter=1000, dangling=0,
+                 out=None, stream=None):
+    """PageRank (Eq. 1) for k teleport vectors. Returns (p, iterations, residuals, status);
+    status is BVG_OK or BVG_ERR_NOT_CONVERGED (other failures raise)."""
+    import torch
+    if p0 is not None:
+        _fp32_cuda(p0)
+        k = 1 if p0.dim() == 1 else p0.shape[1]
+    if out is None:
+        out = torch.empty((g.n, k) if k > 1 or (p0 is not None and p0.dim() == 2) else (g.n,),
+                          dtype=torch.float32, device="cuda")
+    for t in (p0, p_init, out):
+        if t is not None and (not t.is_contiguous()):
+            raise ValueError("PageRank vectors must be contiguous n x k")
+    prm = PrParams(damping, tol, max_iter, dangling)
+    iters = _I32()
+    resid = np.zeros(k, np.float64)
+    rc = load().bvg_pagerank(g.ptr, ctypes.byref(prm), None if p0 is None else p0.data_ptr(),
+                             None if p_init is None else p_init.data_ptr(), k, out.data_ptr(), ctypes.byref(iters),
+                             resid.ctypes.data, _stream(stream))
+    _check(rc, "bvg_pagerank", allow=(BVG_ERR_NOT_CONVERGED,))
+    return out, iters.value, resid, rc
+
+
+def bvg_csr_upload(row_ptr, col, stream=None) -> CsrGraph:
+    lib = load()
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    out = _P()
+    _check(lib.bvg_csr_upload(n, rp.ctypes.data, ci.ctypes.data if len(ci) else None, _stream(stream),
+                              ctypes.byref(out)), "bvg_csr_upload")
+    return CsrGraph(out, n, int(rp[-1]))
+
+
+def bvg_csr_spmv_Ax(g: CsrGraph, x, y, stream=None):
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    _check(load().bvg_csr_spmv_Ax(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_csr_spmv_Ax")
+    return y
+
+
+def bvg_csr_spmv_xA(g: CsrGraph, x, y, stream=None):
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    _check(load().bvg_csr_spmv_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_csr_spmv_xA")
+    return y
+
+
+def bvg_dev_layout(g: DevGraph) -> dict:
+    info = LayoutInfo()
+    _check(load().bvg_dev_layout(g.ptr, ctypes.byref(info)), "bvg_dev_layout")
+    return {f: getattr(info, f) for f, _ in LayoutInfo._fields_}
+
+
+def bvg_trace_enable(g: DevGraph, enable: bool = True):
+    _check(load().bvg_trace_enable(g.ptr, int(bool(enable))), "bvg_trace_enable")
+
+
+def bvg_trace_read(g: DevGraph) -> dict:
+    """{kernel family: (launches, total ms)} recorded since the last read."""
+    buf = (TraceEntry * 32)()
+    cnt = _I32()
+    _check(load().bvg_trace_read(g.ptr, buf, 32, ctypes.byref(cnt)), "bvg_trace_read")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(cnt.value)}
+
+
+def bvg_status_string(status: int) -> str:
+    return load().bvg_status_string(status).decode()

@@ -1,0 +1,643 @@
+// C-ABI entry points of the device side: upload of the BV-delta layout,
+// products, PageRank driver.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace bvg;
+
+namespace bvg {
+
+// ----------------------------------------------------------------- helpers
+static int dev_alloc(void** p, size_t bytes, int64_t* total) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BVG_ERR_OOM : BVG_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    if (total) *total += (int64_t)bytes;
+    return BVG_OK;
+}
+
+template <class T>
+static int upload_vec(T** dst, const std::vector<T>& v, cudaStream_t st, int64_t* total) {
+    int rc = dev_alloc((void**)dst, v.size() * sizeof(T), total);
+    if (rc) return rc;
+    if (!v.empty()) BVG_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return BVG_OK;
+}
+
+static int device_of(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -2;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+    return at.device;
+}
+
+// Largest power of two <= min(32, r).
+static int block_k(int64_t r) {
+    int kb = 32;
+    while (kb > r) kb >>= 1;
+    return kb;
+}
+
+// Vector width usable for a column block starting at `col` of buffers with
+// leading dimension ld.
+static int pick_v(int kb, int64_t ld, int64_t col, std::initializer_list<const void*> ptrs) {
+    auto ok = [&](int v) {
+        if (kb % v || ld % v || col % v) return false;
+        for (const void* p : ptrs)
+            if (p && ((uintptr_t)((const float*)p + col) % (4 * v))) return false;
+        return true;
+    };
+    if (kb >= 4 && ok(4)) return 4;
+    if (kb == 2 && ok(2)) return 2;
+    return 1;
+}
+
+#define BVG_KV_CASES(FN, ...)                              \
+    switch (kb * 8 + v) {                                  \
+        case 1 * 8 + 1: FN<1, 1>(__VA_ARGS__); break;      \
+        case 2 * 8 + 1: FN<2, 1>(__VA_ARGS__); break;      \
+        case 2 * 8 + 2: FN<2, 2>(__VA_ARGS__); break;      \
+        case 4 * 8 + 1: FN<4, 1>(__VA_ARGS__); break;      \
+        case 4 * 8 + 4: FN<4, 4>(__VA_ARGS__); break;      \
+        case 8 * 8 + 1: FN<8, 1>(__VA_ARGS__); break;      \
+        case 8 * 8 + 4: FN<8, 4>(__VA_ARGS__); break;      \
+        case 16 * 8 + 1: FN<16, 1>(__VA_ARGS__); break;    \
+        case 16 * 8 + 4: FN<16, 4>(__VA_ARGS__); break;    \
+        case 32 * 8 + 1: FN<32, 1>(__VA_ARGS__); break;    \
+        case 32 * 8 + 4: FN<32, 4>(__VA_ARGS__); break;    \
+        default: break;                                    \
+    }
+
+constexpr int kThreads = 256;
+
+// Rows per CTA: the halo of kHalo rows is recomputed by two CTAs, so tiles
+// stay large; shared memory grows with kb.
+static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
+static int chain_tile(int kb, const LaunchCfg& c) { return std::max(256, c.chain_tile / kb); }
+template <int KB, int V>
+constexpr int gather_cpt() {
+    return (KB / V) == 1 ? (KB == 1 || KB == 2 ? 4 : 2) : ((KB / V) <= 2 ? 2 : 1);
+}
+static int gather_cols_per_pass(int kb, int v) {
+    int G = kb / v, NG = kThreads / G;
+    int cpt = G == 1 ? (kb <= 2 ? 4 : 2) : (G <= 2 ? 2 : 1);
+    return NG * cpt;
+}
+static int gather_tile(int kb, int v, const LaunchCfg& c) {
+    int per = gather_cols_per_pass(kb, v);
+    int t = std::max(c.gather_tile / kb, per);
+    t = (t + kCarryTile - 1) / kCarryTile * kCarryTile;
+    return t;
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory (once per
+// kernel and size).
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& d : done)
+        if (d.first == (const void*)kernel && d.second >= bytes) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done.push_back({(const void*)kernel, bytes});
+}
+
+// ----------------------------------------------------------------- tracing
+struct Tracer {
+    static constexpr int kPool = 65536;
+    std::vector<cudaEvent_t> ev;  // 2 * kPool
+    struct Rec {
+        const char* name;
+        int slot;
+    };
+    std::vector<Rec> recs;
+    int next = 0;
+    bool on = false;
+};
+
+struct TraceScope {
+    Tracer* t;
+    int slot = -1;
+    cudaStream_t st;
+    TraceScope(const bvg_dev_graph* g, const char* name, cudaStream_t s) : t(g->tracer), st(s) {
+        if (t && t->on && t->next < Tracer::kPool) {
+            slot = t->next++;
+            t->recs.push_back({name, slot});
+            cudaEventRecord(t->ev[2 * slot], st);
+        }
+    }
+    ~TraceScope() {
+        if (slot >= 0) cudaEventRecord(t->ev[2 * slot + 1], st);
+    }
+};
+
+// ----------------------------------------------------------------- launchers
+template <int KB, int V>
+static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy, cudaStream_t st) {
+    const int tile = pull_tile(KB, g->cfg);
+    const size_t smem = (size_t)(tile + kHalo) * KB * sizeof(df);
+    set_smem(k_pull<KB, V>, smem);
+    const int64_t grid = (g->n + tile - 1) / tile;
+    TraceScope ts(g, "pull", st);
+    k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile);
+}
+
+template <int KB, int V>
+static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
+                         int64_t ldz, const PrState* pst, cudaStream_t st) {
+    const int tile = chain_tile(KB, g->cfg);
+    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(df) + (tile + kHalo) + 15) / 16 * 16;
+    set_smem(k_chain<KB, V>, smem);
+    const int64_t grid = (g->n + tile - 1) / tile;
+    TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
+    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, x, ldx, rowscale, z, ldz, g->n, tile, pst);
+}
+
+template <int KB, int V>
+static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, float* y, int64_t ldy, cudaStream_t st) {
+    const int tile = gather_tile(KB, V, g->cfg);
+    const int64_t grid = (g->n + tile - 1) / tile;
+    PrArgs pa{};
+    TraceScope ts(g, "push_gather", st);
+    k_gather<KB, V, gather_cpt<KB, V>(), 0><<<(unsigned)grid, kThreads, 0, st>>>(
+        g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, y, ldy, g->n, tile, pa);
+}
+
+template <int KB, int V>
+static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz, const PrArgs& pa, cudaStream_t st) {
+    const int tile = gather_tile(KB, V, g->cfg);
+    const int64_t grid = (g->n + tile - 1) / tile;
+    TraceScope ts(g, "pr_gather", st);
+    k_gather<KB, V, gather_cpt<KB, V>(), 1><<<(unsigned)grid, kThreads, 0, st>>>(
+        g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, nullptr, 0, g->n, tile, pa);
+}
+
+template <int KB, int V>
+static void launch_pr_init(const bvg_dev_graph* g, const float* p_init, int64_t ldi, const PrArgs& pa,
+                           cudaStream_t st) {
+    const int tile = gather_tile(KB, V, g->cfg);
+    const int64_t grid = (g->n + tile - 1) / tile;
+    TraceScope ts(g, "pr_init", st);
+    k_pr_init<KB, V><<<(unsigned)grid, kThreads, 0, st>>>(p_init, ldi, g->n, tile, pa);
+}
+
+template <int KB, int V>
+static void launch_pr_final(const bvg_dev_graph* g, const PrState* pst, float* out, cudaStream_t st) {
+    const int G = KB / V;
+    const int64_t rows_per_block = kThreads / G;
+    int64_t grid = (g->n + rows_per_block - 1) / rows_per_block;
+    if (grid > 4096) grid = 4096;
+    TraceScope ts(g, "pr_final", st);
+    k_pr_final<KB, V><<<(unsigned)grid, kThreads, 0, st>>>(g->s.q[0], g->s.q[1], KB, g->s.sc[0], g->s.sc[1], pst,
+                                                            out, KB, g->n);
+}
+
+// Grows the z scratch to n x kb floats.
+static int ensure_z(bvg_dev_graph* g, int kb) {
+    if (g->s.kcap >= kb) return BVG_OK;
+    if (g->s.z) cudaFree(g->s.z);
+    g->s.z = nullptr;
+    g->s.kcap = 0;
+    int rc = dev_alloc((void**)&g->s.z, (size_t)g->n * kb * sizeof(float), nullptr);
+    if (rc) return rc;
+    g->s.kcap = kb;
+    return BVG_OK;
+}
+
+static int64_t max_grid(const bvg_dev_graph* g) {
+    // largest grid of any launch that writes per-CTA partials
+    int64_t best = 0;
+    for (int kb = 1; kb <= 32; kb *= 2)
+        for (int v : {1, 2, 4}) {
+            if (v > kb || kb % v) continue;
+            int t = gather_tile(kb, v, g->cfg);
+            best = std::max(best, (g->n + t - 1) / t);
+        }
+    return std::max<int64_t>(best, 1);
+}
+
+static int ensure_pr(bvg_dev_graph* g, int kb) {
+    int rc = ensure_z(g, kb);
+    if (rc) return rc;
+    if (g->s.pr_kcap < kb) {
+        for (int p = 0; p < 2; p++) {
+            if (g->s.q[p]) cudaFree(g->s.q[p]);
+            g->s.q[p] = nullptr;
+        }
+        g->s.pr_kcap = 0;
+        for (int p = 0; p < 2; p++) {
+            rc = dev_alloc((void**)&g->s.q[p], (size_t)g->n * kb * sizeof(float), nullptr);
+            if (rc) return rc;
+        }
+        g->s.pr_kcap = kb;
+    }
+    if (!g->s.st) {
+        rc = dev_alloc((void**)&g->s.st, sizeof(PrState), nullptr);
+        if (rc) return rc;
+        for (int p = 0; p < 2; p++) {
+            rc = dev_alloc((void**)&g->s.sc[p], 3 * 32 * sizeof(double), nullptr);
+            if (rc) return rc;
+        }
+        rc = dev_alloc((void**)&g->s.counter, sizeof(unsigned int), nullptr);
+        if (rc) return rc;
+        BVG_CUDA_TRY(cudaMemset(g->s.counter, 0, sizeof(unsigned int)));
+        int64_t cap = max_grid(g) * 3 * 32;
+        rc = dev_alloc((void**)&g->s.partial, (size_t)cap * sizeof(double), nullptr);
+        if (rc) return rc;
+        g->s.partial_cap = cap;
+        BVG_CUDA_TRY(cudaMallocHost((void**)&g->s.host_state, sizeof(PrState) + 64 * sizeof(double)));
+    }
+    return BVG_OK;
+}
+
+static int check_vec(const bvg_dev_graph* g, const void* p, const char* what) {
+    if (!p) return fail(BVG_ERR_INVALID_ARG, "%s is NULL", what);
+    if ((uintptr_t)p % 4) return fail(BVG_ERR_INVALID_ARG, "%s is not 4-byte aligned", what);
+    int d = device_of(p);
+    if (d != g->device) return fail(BVG_ERR_INVALID_ARG, "%s is not device memory of device %d", what, g->device);
+    return BVG_OK;
+}
+
+}  // namespace bvg
+
+// =================================================================== upload
+extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph** out) {
+    if (!hg || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_upload: NULL argument");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = hg->n;
+    const int64_t words = hg->stats.words;
+    if (words >= ((int64_t)1 << 32)) return fail(BVG_ERR_UNSUPPORTED, "bvg_upload: more than 2^32 words");
+    bvg_dev_graph* g = new (std::nothrow) bvg_dev_graph();
+    if (!g) return fail(BVG_ERR_OOM, "bvg_upload: host allocation failed");
+    int rc = BVG_OK;
+    try {
+        BVG_CUDA_TRY(cudaGetDevice(&g->device));
+        g->n = n;
+        g->m = hg->m;
+        // ---- row-major layout
+        std::vector<uint8_t> meta(n);
+        std::vector<uint32_t> rowp(n + 1), ent((size_t)words);
+        std::vector<float> inv_outdeg(n);
+        rowp[0] = 0;
+        size_t w = 0;
+        for (int64_t i = 0; i < n; i++) {
+            const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
+            meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
+            inv_outdeg[i] = hg->outdeg[i] ? 1.0f / (float)hg->outdeg[i] : 0.0f;
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) ent[w++] = pack(kTagMinus, hg->drop[t]);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) ent[w++] = pack(kTagPlus, hg->res[t]);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                ent[w++] = pack(kTagIvS, hg->iv_s[t]);
+                ent[w++] = pack(kTagIvL, hg->iv_len[t]);
+            }
+            rowp[i + 1] = (uint32_t)w;
+        }
+        // ---- column-major entries (counting sort by column, rows in order)
+        std::vector<uint32_t> colp(n + 1, 0);
+        auto bump = [&](int64_t j) { colp[j + 1]++; };
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) bump(hg->drop[t]);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) bump(hg->res[t]);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                bump(hg->iv_s[t]);
+                int64_t e = (int64_t)hg->iv_s[t] + hg->iv_len[t];
+                if (e < n) bump(e);
+            }
+        }
+        for (int64_t j = 0; j < n; j++) {
+            if ((int64_t)colp[j] + colp[j + 1] >= ((int64_t)1 << 32)) {
+                delete g;
+                return fail(BVG_ERR_UNSUPPORTED, "bvg_upload: more than 2^32 column entries");
+            }
+            colp[j + 1] += colp[j];
+        }
+        std::vector<uint32_t> tent(colp[n]);
+        std::vector<uint32_t> fillp(colp.begin(), colp.end() - 1);
+        const int64_t ntiles = (n + kCarryTile - 1) / kCarryTile;
+        std::vector<uint32_t> carry_ptr(ntiles + 1, 0);
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++)
+                tent[fillp[hg->drop[t]]++] = pack(kTagMinus, (uint32_t)i);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++)
+                tent[fillp[hg->res[t]]++] = pack(kTagPlus, (uint32_t)i);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
+                tent[fillp[s0]++] = pack(kTagIvS, (uint32_t)i);
+                if (e < n) tent[fillp[e]++] = pack(kTagIvL, (uint32_t)i);
+                for (int64_t ct = s0 / kCarryTile + 1; ct <= (e - 1) / kCarryTile; ct++) carry_ptr[ct + 1]++;
+            }
+        }
+        for (int64_t t = 0; t < ntiles; t++) carry_ptr[t + 1] += carry_ptr[t];
+        std::vector<uint32_t> carry(carry_ptr[ntiles]);
+        std::vector<uint32_t> cfill(carry_ptr.begin(), carry_ptr.end() - 1);
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
+                for (int64_t ct = s0 / kCarryTile + 1; ct <= (e - 1) / kCarryTile; ct++) carry[cfill[ct]++] = (uint32_t)i;
+            }
+        g->nwords = words;
+        g->ntent = colp[n];
+        g->ncarry = carry_ptr[ntiles];
+        if ((rc = upload_vec(&g->meta, meta, st, &g->bytes)) || (rc = upload_vec(&g->rowp, rowp, st, &g->bytes)) ||
+            (rc = upload_vec(&g->ent, ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, colp, st, &g->bytes)) ||
+            (rc = upload_vec(&g->tent, tent, st, &g->bytes)) ||
+            (rc = upload_vec(&g->carry_ptr, carry_ptr, st, &g->bytes)) ||
+            (rc = upload_vec(&g->carry, carry, st, &g->bytes)) ||
+            (rc = upload_vec(&g->inv_outdeg, inv_outdeg, st, &g->bytes))) {
+            bvg_free_dev(g);
+            return rc;
+        }
+        if ((rc = ensure_z(g, 1))) {
+            bvg_free_dev(g);
+            return rc;
+        }
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            bvg_free_dev(g);
+            return fail(BVG_ERR_CUDA, "bvg_upload: %s", cudaGetErrorString(e));
+        }
+    } catch (const std::bad_alloc&) {
+        bvg_free_dev(g);
+        return fail(BVG_ERR_OOM, "bvg_upload: host allocation failed");
+    }
+    *out = g;
+    return BVG_OK;
+}
+
+extern "C" void bvg_free_dev(bvg_dev_graph* g) {
+    if (!g) return;
+    void* ptrs[] = {g->meta, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
+                    g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
+                    g->s.hy};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (g->s.host_state) cudaFreeHost(g->s.host_state);
+    if (g->tracer) {
+        for (cudaEvent_t e : g->tracer->ev) cudaEventDestroy(e);
+        delete g->tracer;
+    }
+    delete g;
+}
+
+extern "C" int bvg_trace_enable(bvg_dev_graph* g, int enable) {
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_trace_enable: NULL graph");
+    if (enable && !g->tracer) {
+        Tracer* t = new (std::nothrow) Tracer();
+        if (!t) return fail(BVG_ERR_OOM, "bvg_trace_enable: host allocation failed");
+        t->ev.resize(2 * Tracer::kPool);
+        for (auto& e : t->ev) {
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                for (auto& f : t->ev)
+                    if (f) cudaEventDestroy(f);
+                delete t;
+                return fail(BVG_ERR_CUDA, "bvg_trace_enable: cudaEventCreate failed");
+            }
+        }
+        g->tracer = t;
+    }
+    if (g->tracer) g->tracer->on = enable != 0;
+    return BVG_OK;
+}
+
+extern "C" int bvg_trace_read(bvg_dev_graph* g, bvg_trace_entry* out, int32_t cap, int32_t* count) {
+    if (!g || !count || (cap > 0 && !out)) return fail(BVG_ERR_INVALID_ARG, "bvg_trace_read: bad argument");
+    *count = 0;
+    if (!g->tracer) return BVG_OK;
+    Tracer* t = g->tracer;
+    std::vector<bvg_trace_entry> agg;
+    for (const auto& r : t->recs) {
+        BVG_CUDA_TRY(cudaEventSynchronize(t->ev[2 * r.slot + 1]));
+        float ms = 0.f;
+        BVG_CUDA_TRY(cudaEventElapsedTime(&ms, t->ev[2 * r.slot], t->ev[2 * r.slot + 1]));
+        auto it = std::find_if(agg.begin(), agg.end(), [&](const bvg_trace_entry& e) { return !strcmp(e.name, r.name); });
+        if (it == agg.end()) {
+            bvg_trace_entry e{};
+            strncpy(e.name, r.name, sizeof(e.name) - 1);
+            agg.push_back(e);
+            it = agg.end() - 1;
+        }
+        it->launches++;
+        it->total_ms += ms;
+    }
+    t->recs.clear();
+    t->next = 0;
+    for (int i = 0; i < (int)agg.size() && i < cap; i++) out[i] = agg[i];
+    *count = (int32_t)std::min<size_t>(agg.size(), (size_t)std::max(cap, 0));
+    return BVG_OK;
+}
+
+extern "C" int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m) {
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_dev_size: NULL graph");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return BVG_OK;
+}
+
+extern "C" int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out) {
+    if (!g || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_dev_layout: NULL argument");
+    out->n = g->n;
+    out->m = g->m;
+    out->words = g->nwords;
+    out->col_entries = g->ntent;
+    out->carry_tiles = (g->n + kCarryTile - 1) / kCarryTile;
+    out->carry_entries = g->ncarry;
+    out->structure_bytes = g->bytes;
+    return BVG_OK;
+}
+
+// =================================================================== products
+extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_Ax: NULL graph");
+    if (k < 1 || ld < k) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_Ax: need k >= 1 and ld >= k");
+    if (g->n == 0) return BVG_OK;
+    int rc;
+    if ((rc = check_vec(g, x, "x")) || (rc = check_vec(g, y, "y"))) return rc;
+    if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_Ax: x and y must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t c0 = 0; c0 < k; ) {
+        const int kb = block_k(k - c0);
+        const int v = pick_v(kb, ld, c0, {x, y});
+        BVG_KV_CASES(launch_pull, g, x + c0, ld, y + c0, ld, st);
+        c0 += kb;
+    }
+    BVG_CUDA_TRY(cudaGetLastError());
+    return BVG_OK;
+}
+
+extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
+    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: NULL graph");
+    if (k < 1 || ld < k) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: need k >= 1 and ld >= k");
+    if (g->n == 0) return BVG_OK;
+    int rc;
+    if ((rc = check_vec(g, x, "x")) || (rc = check_vec(g, y, "y"))) return rc;
+    if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: x and y must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t c0 = 0; c0 < k; ) {
+        const int kb = block_k(k - c0);
+        if ((rc = ensure_z(g, kb))) return rc;
+        const int v = pick_v(kb, ld, c0, {x, y});
+        BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
+        BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
+        c0 += kb;
+    }
+    BVG_CUDA_TRY(cudaGetLastError());
+    return BVG_OK;
+}
+
+extern "C" int bvg_spmv_xA_host(const bvg_dev_graph* gc, const float* x_host, float* y_host, int32_t k,
+                                void* stream) {
+    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
+    if (!g || !x_host || !y_host) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_host: NULL argument");
+    if (k < 1) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_host: k < 1");
+    if (g->n == 0) return BVG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t need = g->n * (int64_t)k;
+    if (g->s.stage_cap < need) {
+        if (g->s.hx) cudaFree(g->s.hx);
+        if (g->s.hy) cudaFree(g->s.hy);
+        g->s.hx = g->s.hy = nullptr;
+        g->s.stage_cap = 0;
+        int rc;
+        if ((rc = dev_alloc((void**)&g->s.hx, need * sizeof(float), nullptr)) ||
+            (rc = dev_alloc((void**)&g->s.hy, need * sizeof(float), nullptr)))
+            return rc;
+        g->s.stage_cap = need;
+    }
+    BVG_CUDA_TRY(cudaMemcpyAsync(g->s.hx, x_host, need * sizeof(float), cudaMemcpyHostToDevice, st));
+    int rc = bvg_spmv_xA(g, g->s.hx, g->s.hy, k, k, stream);
+    if (rc) return rc;
+    BVG_CUDA_TRY(cudaMemcpyAsync(y_host, g->s.hy, need * sizeof(float), cudaMemcpyDeviceToHost, st));
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));
+    return BVG_OK;
+}
+
+// =================================================================== PageRank
+extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params, const float* p0,
+                            const float* p_init, int32_t k, float* p_out, int32_t* iters_out, double* resid_out,
+                            void* stream) {
+    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
+    if (!g || !p_out) return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: NULL graph or output");
+    if (k != 1 && k != 2 && k != 4 && k != 8 && k != 16 && k != 32)
+        return fail(BVG_ERR_UNSUPPORTED, "bvg_pagerank: k must be 1, 2, 4, 8, 16 or 32 (got %d)", k);
+    if (!p0 && k != 1) return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: uniform teleport (p0 = NULL) needs k = 1");
+    const double damping = params && params->damping > 0 ? params->damping : 0.85;
+    const double tol = params ? params->tol_l1 : 1e-8;
+    const int max_iter = params && params->max_iter > 0 ? params->max_iter : 1000;
+    const int dangling = params ? params->dangling : 0;
+    if (!(damping > 0 && damping < 1) || !(tol >= 0) || (dangling != 0 && dangling != 1))
+        return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: need 0 < damping < 1, tol >= 0, dangling in {0,1}");
+    if (g->n == 0) {
+        if (iters_out) *iters_out = 0;
+        return BVG_OK;
+    }
+    int rc;
+    if ((rc = check_vec(g, p_out, "p_out"))) return rc;
+    if (p0 && (rc = check_vec(g, p0, "p0"))) return rc;
+    if (p_init && (rc = check_vec(g, p_init, "p_init"))) return rc;
+    if ((rc = ensure_pr(g, k))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int kb = k;
+    const int v = pick_v(kb, kb, 0, {p0, p_init, p_out, g->s.q[0], g->s.q[1]});
+
+    PrState hs{0, 0, 0, max_iter, tol};
+    PrState* pst = (PrState*)g->s.st;
+    BVG_CUDA_TRY(cudaMemcpyAsync(pst, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    PrArgs base{};
+    base.p0 = p0;
+    base.ldp0 = kb;
+    base.inv_outdeg = g->inv_outdeg;
+    base.ldq = kb;
+    base.st = pst;
+    base.partial = g->s.partial;
+    base.counter = g->s.counter;
+    base.alpha = (float)(1.0 - damping);
+    base.dangling_uniform = dangling;
+    base.k = k;
+    // start: q[0] = p_init / p0 / uniform, scalars into sc[0]
+    {
+        PrArgs pa = base;
+        pa.q_new = g->s.q[0];
+        pa.sc_new = g->s.sc[0];
+        const float* start = p_init ? p_init : p0;
+        BVG_KV_CASES(launch_pr_init, g, start, kb, pa, st);
+    }
+    auto launch_update = [&](int par) {
+        // update reading q[par], writing q[1 - par]
+        PrArgs pa = base;
+        pa.q_prev = g->s.q[par];
+        pa.q_new = g->s.q[1 - par];
+        pa.sc_prev = g->s.sc[par];
+        pa.sc_new = g->s.sc[1 - par];
+        BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
+        BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
+    };
+    PrState* hst = (PrState*)g->s.host_state;
+    double* hres = (double*)((char*)g->s.host_state + sizeof(PrState));
+    int launched = 0;
+    int next_poll = std::min(max_iter, 8);
+    double last_res = INFINITY;
+    int last_res_iter = 0;
+    for (;;) {
+        while (launched < next_poll) {
+            launch_update(launched & 1);
+            launched++;
+        }
+        BVG_CUDA_TRY(cudaGetLastError());
+        // state and the residuals of both parities; the state says which is current
+        BVG_CUDA_TRY(cudaMemcpyAsync(hst, pst, sizeof(PrState), cudaMemcpyDeviceToHost, st));
+        BVG_CUDA_TRY(cudaMemcpyAsync(hres, g->s.sc[0] + 2 * kb, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        BVG_CUDA_TRY(cudaMemcpyAsync(hres + 32, g->s.sc[1] + 2 * kb, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        BVG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hst->done || hst->iter >= max_iter) break;
+        if (launched >= max_iter || hst->iter < launched - 1)
+            return fail(BVG_ERR_CUDA, "bvg_pagerank: device state did not advance (%d of %d updates)", hst->iter,
+                        launched);
+        // plan the next poll from the observed contraction of the residual
+        const double* cur = hres + 32 * (hst->iter & 1);
+        double r = 0;
+        for (int c = 0; c < k; c++) r = std::max(r, cur[c]);
+        int ahead = 8;
+        if (std::isfinite(r) && r > 0 && tol > 0) {
+            double rate = 1.0 - (1.0 - damping);
+            if (std::isfinite(last_res) && hst->iter > last_res_iter && r < last_res)
+                rate = std::max(rate, std::pow(r / last_res, 1.0 / (hst->iter - last_res_iter)));
+            rate = std::min(rate, 0.999);
+            double need = std::log(tol / r) / std::log(rate);
+            ahead = (int)std::ceil(need);
+            ahead = std::max(2, std::min(ahead, 64));
+        }
+        last_res = r;
+        last_res_iter = hst->iter;
+        next_poll = std::min(max_iter, launched + ahead);
+    }
+    BVG_KV_CASES(launch_pr_final, g, pst, p_out, st);
+    BVG_CUDA_TRY(cudaGetLastError());
+    BVG_CUDA_TRY(cudaMemcpyAsync(hres, g->s.sc[hst->iter & 1] + 2 * kb, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                                 st));
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (iters_out) *iters_out = hst->iter;
+    if (resid_out)
+        for (int c = 0; c < k; c++) resid_out[c] = hres[c];
+    if (hst->numeric) return fail(BVG_ERR_NUMERIC, "bvg_pagerank: non-finite value at update %d", hst->iter);
+    if (!hst->done) return fail(BVG_ERR_NOT_CONVERGED, "bvg_pagerank: not converged after %d updates", hst->iter);
+    return BVG_OK;
+}

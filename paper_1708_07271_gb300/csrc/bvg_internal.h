@@ -1,0 +1,120 @@
+// Internal structures of the BV-delta library (host and device sides).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bvg.h"
+
+namespace bvg {
+
+// Largest supported window and chain bound. The device layout packs the
+// reference offset (1..7, 0 = none) in 3 bits and the chain depth in 2 bits.
+constexpr int kMaxWindow = 7;
+constexpr int kMaxChain = 3;
+// Halo of rows a tile needs beyond its own range to resolve reference
+// chains locally: a chain spans at most kMaxWindow * kMaxChain rows.
+constexpr int kHalo = kMaxWindow * kMaxChain;
+// Granularity (columns) of the interval carry-in lists of the column layout.
+constexpr int kCarryTile = 128;
+// Two tag bits on top of a 30-bit id.
+constexpr uint32_t kIdBits = 30;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1;
+constexpr int64_t kMaxN = (int64_t)1 << kIdBits;
+
+// Row-major word tags (difference row of row i):
+//   kTagPlus   residual id j       (+x_j)
+//   kTagMinus  dropped id j        (-x_j)
+//   kTagIvS    interval start s    (followed by a kTagIvL word)
+//   kTagIvL    interval length
+// Column-major word tags (entries of column j, payload = source row k):
+//   kTagPlus   +z_k, kTagMinus -z_k,
+//   kTagIvS    an interval of row k starts at j  (D_j += z_k)
+//   kTagIvL    an interval of row k ends before j (D_j -= z_k)
+constexpr uint32_t kTagPlus = 0, kTagMinus = 1, kTagIvS = 2, kTagIvL = 3;
+inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
+
+void set_error(const char* fmt, ...);
+int fail(int status, const char* fmt, ...);
+
+}  // namespace bvg
+
+struct bvg_host_graph {
+    int64_t n = 0, m = 0;
+    int32_t window = 7, max_chain = 3, min_interval = 4;
+    std::vector<int32_t> ref;      // r_i or -1
+    std::vector<uint8_t> depth;    // chain depth
+    std::vector<uint32_t> outdeg;  // |v_i|
+    // difference rows, row-major
+    std::vector<int64_t> drop_ptr, res_ptr, iv_ptr;  // n+1 each
+    std::vector<int32_t> drop, res, iv_s, iv_len;
+    // gamma/delta bitstream
+    std::vector<uint64_t> bits;
+    int64_t nbits = 0;
+    bvg_graph_stats stats{};
+};
+
+namespace bvg {
+
+// Launch configuration of the product kernels (autotuned per graph and k).
+struct LaunchCfg {
+    int pull_tile = 512;    // rows per CTA of the pull kernel
+    int pull_threads = 256;
+    int chain_tile = 1024;  // rows per CTA of the push-chain kernel
+    int gather_tile = 1024; // columns per CTA of the push-gather kernel
+    int gather_threads = 256;
+};
+
+struct DevScratch {
+    float* z = nullptr;                 // pushed weights, n x kcap (x A)
+    float* q[2] = {nullptr, nullptr};   // PageRank iterates (unnormalised), n x pr_kcap
+    double* sc[2] = {nullptr, nullptr}; // PageRank scalars per parity: [3][32] (1/S, dangling, resid)
+    void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
+    double* partial = nullptr;          // per-CTA FP64 partial sums
+    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction)
+    void* host_state = nullptr;         // pinned host copy of the state + residuals
+    float* hx = nullptr;                // device staging for the host-buffer product
+    float* hy = nullptr;
+    int64_t kcap = 0;                   // columns the z buffer holds
+    int64_t pr_kcap = 0;                // columns the PageRank buffers hold
+    int64_t partial_cap = 0;            // doubles in `partial`
+    int64_t stage_cap = 0;              // floats in hx / hy
+};
+
+}  // namespace bvg
+
+namespace bvg {
+struct Tracer;  // api.cu
+}
+
+struct bvg_dev_graph {
+    int64_t n = 0, m = 0;
+    int device = 0;
+    // row-major difference rows (A x^T)
+    uint8_t* meta = nullptr;   // n: bits 0-2 reference offset (0 = none), bits 3-4 depth
+    uint32_t* rowp = nullptr;  // n+1 word offsets
+    uint32_t* ent = nullptr;   // words
+    int64_t nwords = 0;
+    // column-major entries (x A)
+    uint32_t* colp = nullptr;  // n+1
+    uint32_t* tent = nullptr;
+    int64_t ntent = 0;
+    uint32_t* carry_ptr = nullptr;  // ceil(n / kCarryTile) + 1
+    uint32_t* carry = nullptr;      // source rows of intervals open at a carry-tile start
+    int64_t ncarry = 0;
+    float* inv_outdeg = nullptr;    // 1/|v_i|, 0 for rows without successors
+    int64_t bytes = 0;
+    bvg::LaunchCfg cfg;
+    bvg::DevScratch s;
+    bvg::Tracer* tracer = nullptr;
+};
+
+struct bvg_csr_graph {
+    int64_t n = 0, m = 0;
+    int device = 0;
+    int64_t* rp = nullptr;  // CSR of A
+    int32_t* ci = nullptr;
+    int64_t* rpt = nullptr; // CSR of A^T
+    int32_t* cit = nullptr;
+};

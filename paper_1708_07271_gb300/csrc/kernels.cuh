@@ -1,0 +1,464 @@
+// Kernels of the BV-delta products. Everything here is templated on
+//   KB : right-hand sides handled by one launch (1, 2, 4, 8, 16, 32)
+//   V  : floats per vector access (1, 2 or 4; KB % V == 0)
+// A group of G = KB / V consecutive lanes owns one row (or column); lane l of
+// the group owns right-hand sides [l*V, l*V + V).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace bvg {
+
+struct PrState {
+    int done;      // converged (or non-finite): later kernels return at once
+    int numeric;   // a non-finite sum was seen
+    int iter;      // completed updates
+    int max_iter;
+    double tol;
+};
+
+struct PrArgs {
+    const float* p0;           // teleport vectors (n x k, ld ldp0) or NULL = uniform 1/n
+    int64_t ldp0;
+    const float* inv_outdeg;   // 0 marks a row without successors
+    const float* q_prev;       // previous iterate, unnormalised (n x k, ld ldq)
+    float* q_new;
+    int64_t ldq;
+    const double* sc_prev;     // [3][k]: 1/S, dangling mass (normalised), resid
+    double* sc_new;
+    PrState* st;
+    double* partial;           // [grid][3][KB]
+    unsigned int* counter;
+    float alpha;
+    int dangling_uniform;
+    int k;                     // right-hand sides of the solve (== KB)
+};
+
+
+// ---------------------------------------------------------------------------
+// Pull: y = A x^T (Sec. 4). A CTA owns rows [a, a + tile). It first forms the
+// correction sums c_i = sum_j A'_ij x_j for rows [a - kHalo, a + tile) into
+// shared memory (dropped ids subtract, residual ids add, an interval (s, len)
+// adds x_s + ... + x_{s+len-1}), then resolves each owned row's chain
+// y_i = c_i + y_{r_i} = c_i + c_{r_i} + c_{r_{r_i}} + ... with at most
+// max_chain links, all inside the CTA (a chain never leaves kHalo rows).
+// The sums are compensated (hi, lo) pairs; the chain is added from its root
+// outwards, i.e. in the association of the sequential algorithm.
+// ---------------------------------------------------------------------------
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ rowp,
+                                              const uint32_t* __restrict__ ent, const float* __restrict__ x,
+                                              int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n, int tile) {
+    constexpr int G = KB / V;
+    extern __shared__ float4 smem_pull[];
+    df* c = reinterpret_cast<df*>(smem_pull);  // [(tile + kHalo) * KB]
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int64_t a = (int64_t)blockIdx.x * tile;
+    const int64_t lo = a > kHalo ? a - kHalo : 0;
+    const int64_t hi = a + tile < n ? a + tile : n;
+    const int cnt = (int)(hi - lo);
+
+    for (int r = g; r < cnt; r += NG) {
+        const int64_t i = lo + r;
+        df acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = df_zero();
+        const uint32_t w0 = __ldg(rowp + i), w1 = __ldg(rowp + i + 1);
+        for (uint32_t w = w0; w < w1; w++) {
+            const uint32_t word = __ldg(ent + w);
+            const uint32_t tag = tag_of(word), id = id_of(word);
+            if (tag == kTagPlus || tag == kTagMinus) {
+                Vec<V> xv = ldv<V>(x + (int64_t)id * ldx + lane * V);
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], tag == kTagPlus ? xv.v[v] : -xv.v[v]);
+            } else if (tag == kTagIvS) {
+                const uint32_t len = id_of(__ldg(ent + w + 1));
+                w++;
+                for (uint32_t t = 0; t < len; t++) {
+                    Vec<V> xv = ldv<V>(x + (int64_t)(id + t) * ldx + lane * V);
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
+    }
+    __syncthreads();
+
+    for (int r = (int)(a - lo) + g; r < cnt; r += NG) {
+        int idx[kMaxChain + 1];
+        int len = 0, cur = r;
+        idx[len++] = cur;
+        for (int t = 0; t < kMaxChain; t++) {
+            const int off = __ldg(meta + lo + cur) & 7;
+            if (off == 0 || cur - off < 0) break;
+            cur -= off;
+            idx[len++] = cur;
+        }
+        Vec<V> out;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            df s = c[(int64_t)idx[len - 1] * KB + lane * V + v];
+            for (int t = len - 2; t >= 0; t--) s = df_add(c[(int64_t)idx[t] * KB + lane * V + v], s);
+            out.v[v] = df_val(s);
+        }
+        stv<V>(y + (lo + r) * ldy + lane * V, out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Push, chain step: z_k = sum of x_i over the rows i whose reference chain
+// passes through k (Proposition 1 read for the left product: v_i is the sum
+// of the difference rows along its chain). A CTA owns rows [a, a + tile) and
+// reads kHalo rows past its end (a subtree spans at most kHalo rows). Rows
+// are visited in reverse level order: first the rows of depth R-1 gather
+// their children (depth R), then depth R-2, ..., then the roots; each gather
+// scans the W rows after k for those whose reference is k. Optionally x is
+// scaled per row first (x_i * rowscale_i, PageRank's 1/outdeg).
+// ---------------------------------------------------------------------------
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta, const float* __restrict__ x,
+                                               int64_t ldx, const float* __restrict__ rowscale,
+                                               float* __restrict__ z, int64_t ldz, int64_t n, int tile,
+                                               const PrState* __restrict__ st) {
+    if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
+    constexpr int G = KB / V;
+    extern __shared__ float4 smem_chain[];
+    df* zs = reinterpret_cast<df*>(smem_chain);                       // [(tile + kHalo) * KB]
+    uint8_t* ms = reinterpret_cast<uint8_t*>(zs + (int64_t)(tile + kHalo) * KB);  // [tile + kHalo]
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int64_t a = (int64_t)blockIdx.x * tile;
+    const int64_t hi = a + tile + kHalo < n ? a + tile + kHalo : n;
+    const int cnt = (int)(hi - a);
+    const int own = (int)((a + tile < n ? a + tile : n) - a);
+
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) ms[r] = __ldg(meta + a + r);
+    for (int r = g; r < cnt; r += NG) {
+        Vec<V> xv = ldv<V>(x + (a + r) * ldx + lane * V);
+        const float sc = rowscale ? __ldg(rowscale + a + r) : 1.0f;
+#pragma unroll
+        for (int v = 0; v < V; v++) zs[(int64_t)r * KB + lane * V + v] = {__fmul_rn(xv.v[v], sc), 0.f};
+    }
+    __syncthreads();
+    for (int d = kMaxChain - 1; d >= 0; d--) {
+        for (int r = g; r < cnt; r += NG) {
+            if ((ms[r] >> 3) != d) continue;
+            df acc[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = zs[(int64_t)r * KB + lane * V + v];
+            for (int cc = r + 1; cc <= r + kMaxWindow && cc < cnt; cc++) {
+                if ((ms[cc] & 7) != cc - r) continue;
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] = df_add(acc[v], zs[(int64_t)cc * KB + lane * V + v]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) zs[(int64_t)r * KB + lane * V + v] = acc[v];
+        }
+        __syncthreads();
+    }
+    for (int r = g; r < own; r += NG) {
+        Vec<V> out;
+#pragma unroll
+        for (int v = 0; v < V; v++) out.v[v] = df_val(zs[(int64_t)r * KB + lane * V + v]);
+        stv<V>(z + (a + r) * ldz + lane * V, out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Push, scatter step, written as a gather per column (owner computes, no
+// atomics, deterministic): y_j = sum_k z_k A'_kj. The column-major entries of
+// column j are +z_k (residual id j of row k), -z_k (dropped id j of row k),
+// and interval events: D_j += z_k where an interval of row k starts at j,
+// D_j -= z_k where it ends before j. Intervals contribute the running prefix
+// of D. A CTA owns columns [a, a + tile), a multiple of kCarryTile, and
+// starts its running prefix from the intervals open at column a (the carry
+// list), so no grid-wide scan is needed. Each group handles CPT consecutive
+// columns per pass; the prefix across groups is a compensated block scan.
+// EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
+// ---------------------------------------------------------------------------
+template <int KB>
+struct PrPartials {
+    double S[KB], R[KB], Dg[KB];
+};
+
+// Sums the per-CTA FP64 partials (sum q, sum |q - p_prev|, dangling mass),
+// then the last CTA to finish reduces all CTAs in a fixed order and writes
+// the scalars of this update (deterministic; no spin-waits).
+template <int KB, int V>
+__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init) {
+    constexpr int G = KB / V;
+    __shared__ double sh_part[32][3][KB];
+    __shared__ bool sh_last;
+    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        for (int o = 16; o >= G; o >>= 1) {
+            S[v] += __shfl_xor_sync(0xffffffffu, S[v], o);
+            R[v] += __shfl_xor_sync(0xffffffffu, R[v], o);
+            Dg[v] += __shfl_xor_sync(0xffffffffu, Dg[v], o);
+        }
+    }
+    if (lane32 < G) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            sh_part[warp][0][lane32 * V + v] = S[v];
+            sh_part[warp][1][lane32 * V + v] = R[v];
+            sh_part[warp][2][lane32 * V + v] = Dg[v];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 * KB) {
+        const int f = threadIdx.x / KB, c = threadIdx.x % KB;
+        double t = 0.0;
+        for (int w = 0; w < NW; w++) t += sh_part[w][f][c];
+        pa.partial[((int64_t)blockIdx.x * 3 + f) * KB + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(pa.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    __shared__ double sh_red[256];
+    __shared__ double sh_tot[3][KB];
+    for (int item = 0; item < 3 * KB; item++) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            t += __ldcg(pa.partial + ((int64_t)b * 3 + item / KB) * KB + item % KB);
+        sh_red[threadIdx.x] = t;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) sh_red[threadIdx.x] += sh_red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sh_tot[item / KB][item % KB] = sh_red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bool conv = true, bad = false;
+        for (int c = 0; c < pa.k; c++) {
+            const double Ssum = sh_tot[0][c], Rsum = sh_tot[1][c], Dsum = sh_tot[2][c];
+            pa.sc_new[0 * KB + c] = 1.0 / Ssum;
+            pa.sc_new[1 * KB + c] = Dsum / Ssum;
+            pa.sc_new[2 * KB + c] = init ? INFINITY : Rsum;
+            if (!(Rsum < pa.st->tol)) conv = false;
+            if (!isfinite(Ssum) || !isfinite(Dsum) || (!init && !isfinite(Rsum)) || Ssum <= 0.0) bad = true;
+        }
+        if (init) {
+            pa.st->iter = 0;
+            pa.st->done = bad ? 1 : 0;
+            pa.st->numeric = bad ? 1 : 0;
+        } else {
+            pa.st->iter += 1;
+            if (bad) pa.st->numeric = 1;
+            if (conv || bad) pa.st->done = 1;
+        }
+        *pa.counter = 0u;
+        __threadfence();
+    }
+}
+
+template <int KB, int V, int CPT, int EPI>
+__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                                const uint32_t* __restrict__ carry_ptr,
+                                                const uint32_t* __restrict__ carry, const float* __restrict__ z,
+                                                int64_t ldz, float* __restrict__ y, int64_t ldy, int64_t n,
+                                                int tile, PrArgs pa) {
+    constexpr int G = KB / V;
+    if constexpr (EPI == 1) {
+        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+    }
+    __shared__ df sh_run[KB];
+    __shared__ df sh_wtot[32][KB];
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    const int64_t a = (int64_t)blockIdx.x * tile;
+    const int64_t end = a + tile < n ? a + tile : n;
+
+    // running interval prefix at column a: intervals open across the tile start
+    if (threadIdx.x < G) {
+        df acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = df_zero();
+        const int64_t ct = a / kCarryTile;
+        for (uint32_t e = __ldg(carry_ptr + ct); e < __ldg(carry_ptr + ct + 1); e++) {
+            Vec<V> zv = ldv<V>(z + (int64_t)__ldg(carry + e) * ldz + lane * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], zv.v[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) sh_run[lane * V + v] = acc[v];
+    }
+    __syncthreads();
+    df run[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) run[v] = sh_run[lane * V + v];
+
+    double S[V], R[V], Dg[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
+    double inv_s[V], delta[V];
+    if constexpr (EPI == 1) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            inv_s[v] = pa.sc_prev[0 * KB + lane * V + v];
+            delta[v] = pa.sc_prev[1 * KB + lane * V + v];
+        }
+    }
+
+    for (int64_t base = a; base < end; base += (int64_t)NG * CPT) {
+        const int64_t c0 = base + (int64_t)g * CPT;
+        df P[CPT][V], Dinc[CPT][V], tot[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) tot[v] = df_zero();
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            const int64_t j = c0 + q;
+#pragma unroll
+            for (int v = 0; v < V; v++) P[q][v] = df_zero();
+            if (j < end) {
+                const uint32_t e0 = __ldg(colp + j), e1 = __ldg(colp + j + 1);
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t word = __ldg(tent + e);
+                    const uint32_t tag = tag_of(word);
+                    Vec<V> zv = ldv<V>(z + (int64_t)id_of(word) * ldz + lane * V);
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
+                        if (tag < 2) P[q][v] = df_addf(P[q][v], val);
+                        else tot[v] = df_addf(tot[v], val);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) Dinc[q][v] = tot[v];
+        }
+        // compensated exclusive scan of the group totals across the block
+        df inc[V], ex[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) inc[v] = tot[v];
+        for (int d = G; d < 32; d <<= 1) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                df o = df_shfl_up(inc[v], d);
+                if (lane32 >= d) inc[v] = df_add(o, inc[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            df o = df_shfl_up(inc[v], G);
+            ex[v] = lane32 >= G ? o : df_zero();
+        }
+        if (lane32 >= 32 - G) {
+#pragma unroll
+            for (int v = 0; v < V; v++) sh_wtot[warp][lane * V + v] = inc[v];
+        }
+        __syncthreads();
+        df wpre[V], btot[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) wpre[v] = btot[v] = df_zero();
+        for (int w = 0; w < NW; w++) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const df t = sh_wtot[w][lane * V + v];
+                if (w < warp) wpre[v] = df_add(wpre[v], t);
+                btot[v] = df_add(btot[v], t);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            const int64_t j = c0 + q;
+            if (j >= end) continue;
+            Vec<V> out;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const df I = df_add(df_add(run[v], wpre[v]), df_add(ex[v], Dinc[q][v]));
+                out.v[v] = df_val(df_add(P[q][v], I));
+            }
+            if constexpr (EPI == 0) {
+                stv<V>(y + j * ldy + lane * V, out);
+            } else {
+                const float io = __ldg(pa.inv_outdeg + j);
+                const float un = 1.0f / (float)n;
+                Vec<V> qn;
+                Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq + lane * V);
+                Vec<V> p0v;
+                if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0 + lane * V);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float p0j = pa.p0 ? p0v.v[v] : un;
+                    const float gj = pa.dangling_uniform ? un : p0j;
+                    const float yj = __fmul_rn(out.v[v], (float)inv_s[v]);
+                    const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (yj + (float)delta[v] * gj);
+                    qn.v[v] = qj;
+                    S[v] += (double)qj;
+                    R[v] += fabs((double)qj - (double)qp.v[v] * inv_s[v]);
+                    if (io == 0.0f) Dg[v] += (double)qj;
+                }
+                stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) run[v] = df_add(run[v], btot[v]);
+    }
+    if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
+}
+
+// PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
+// start (1/S_0, dangling mass) by the same deterministic reduction.
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_init, int64_t ldi, int64_t n,
+                                                 int tile, PrArgs pa) {
+    constexpr int G = KB / V;
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int64_t a = (int64_t)blockIdx.x * tile;
+    const int64_t end = a + tile < n ? a + tile : n;
+    double S[V], R[V], Dg[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
+    const float un = 1.0f / (float)n;
+    for (int64_t j = a + g; j < end; j += NG) {
+        Vec<V> pv;
+        if (p_init) pv = ldv<V>(p_init + j * ldi + lane * V);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; v++) pv.v[v] = un;
+        }
+        stv<V>(pa.q_new + j * pa.ldq + lane * V, pv);
+        const float io = __ldg(pa.inv_outdeg + j);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            S[v] += (double)pv.v[v];
+            if (io == 0.0f) Dg[v] += (double)pv.v[v];
+        }
+    }
+    pr_block_reduce<KB, V>(S, R, Dg, pa, true);
+}
+
+// p_out = q_T / S_T for the final update T (read from the state).
+template <int KB, int V>
+__global__ void k_pr_final(const float* __restrict__ q0, const float* __restrict__ q1, int64_t ldq,
+                           const double* __restrict__ sc0, const double* __restrict__ sc1,
+                           const PrState* __restrict__ st, float* __restrict__ out, int64_t ldo, int64_t n) {
+    constexpr int G = KB / V;
+    const int par = __ldcg(&st->iter) & 1;
+    const float* q = par ? q1 : q0;
+    const double* sc = par ? sc1 : sc0;
+    const int64_t gid = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x / G);
+    for (int64_t j = gid; j < n; j += stride) {
+        Vec<V> qv = ldv_cg<V>(q + j * ldq + lane * V), o;
+#pragma unroll
+        for (int v = 0; v < V; v++) o.v[v] = (float)((double)qv.v[v] * __ldcg(sc + lane * V + v));
+        stv<V>(out + j * ldo + lane * V, o);
+    }
+}
+
+}  // namespace bvg

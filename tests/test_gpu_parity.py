@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element.
+
+Tolerance for a product entry (derived from the arithmetic): FP32 values with
+compensated sums give |y - y*| <= ~2^-23 * (sum of the magnitudes of the
+terms the compressed formula adds); the test allows 1e-5 of
+max(|y*|, s) where s is that magnitude, computed by the oracle on its own
+difference rows. Dyadic inputs make every partial sum exact in FP32, so
+there the results must match bit for bit. PageRank: L1 distance to the
+oracle <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1708_07271_gb300 as bvg  # noqa: E402
+
+RTOL = 1e-5
+
+
+def encode(g):
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    ref, _ = bvg.bvg_get_refs(hg)
+    return hg, bvg.bvg_upload(hg), ref
+
+
+def check_close(got, want, mag, what):
+    err = np.abs(got.astype(np.float64) - want)
+    bound = RTOL * np.maximum(np.abs(want), mag) + 1e-30
+    bad = np.nonzero(err > bound)
+    assert bad[0].size == 0, f"{what}: {bad[0].size} entries off, worst {err.max():.3e} at {np.argmax(err)}"
+
+
+GRAPHS = {
+    "tiny_web": lambda: synth.copying_model(synth.tiny_web()),
+    "ragged_1037": lambda: synth.copying_model(synth.replace(synth.tiny_web(), n=1037, seed=77)),
+    "social_20k": lambda: synth.copying_model(synth.replace(synth.social_5m4(), n=20_000)),
+    "dense_local": lambda: synth.copying_model(synth.GraphSpec(n=3000, seed=5, p_copy=0.9, fidelity=0.9,
+                                                               extra_mean=2.0, fresh_mean=40, q_run=0.6,
+                                                               gap_mean=3.0)),
+    "long_runs": lambda: synth.copying_model(synth.GraphSpec(n=5000, seed=6, p_copy=0.6, fidelity=0.95,
+                                                             extra_mean=1.0, fresh_mean=300, q_run=0.9,
+                                                             run_min=100, run_max=900, gap_mean=50.0)),
+}
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        g = GRAPHS[name]()
+        _cache[name] = (g, *encode(g))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("k", [1, 2, 7, 8, 32, 33])
+def test_products_match_oracle(name, k):
+    g, hg, dg, ref = graph(name)
+    x = synth.rhs(g.n, k, synth.seed_for(1, 100 + k))
+    x64 = x.astype(np.float64)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.full_like(xt, float("nan"))
+    bvg.bvg_spmv_xA(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), f"xA {name} k={k}")
+    y.fill_(float("nan"))
+    bvg.bvg_spmv_Ax(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), f"Ax {name} k={k}")
+
+
+@pytest.mark.parametrize("name", ["tiny_web", "social_20k", "long_runs"])
+@pytest.mark.parametrize("k", [1, 4, 32])
+def test_dyadic_inputs_bit_exact(name, k):
+    g, hg, dg, ref = graph(name)
+    x = synth.dyadic_rhs(g.n, k, synth.seed_for(1, 200 + k))
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, y)
+    np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_xA(g.row_ptr, g.col, x))
+    bvg.bvg_spmv_Ax(dg, xt, y)
+    np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_Ax(g.row_ptr, g.col, x))
+
+
+def test_strided_and_unaligned_views():
+    g, hg, dg, ref = graph("tiny_web")
+    base = torch.from_numpy(synth.rhs(g.n, 11, 5)).cuda()
+    x = base[:, 1:6]  # ld = 11, misaligned start: scalar loads
+    y_full = torch.zeros(g.n, 11, device="cuda")
+    y = y_full[:, 3:8]
+    bvg.bvg_spmv_xA(dg, x, y)
+    x64 = x.cpu().numpy().astype(np.float64)
+    check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), "strided xA")
+    assert (y_full[:, :3] == 0).all() and (y_full[:, 8:] == 0).all()
+
+
+def test_deterministic():
+    g, hg, dg, ref = graph("tiny_web")
+    xt = torch.from_numpy(synth.rhs(g.n, 8, 3)).cuda()
+    y1, y2 = torch.empty_like(xt), torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, y1)
+    bvg.bvg_spmv_xA(dg, xt, y2)
+    assert torch.equal(y1, y2)
+
+
+def test_csr_baseline_matches_oracle():
+    g, hg, dg, ref = graph("tiny_web")
+    cg = bvg.bvg_csr_upload(g.row_ptr, g.col)
+    for k in (1, 8, 33):
+        x = synth.rhs(g.n, k, 9 + k)
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.empty_like(xt)
+        bvg.bvg_csr_spmv_xA(cg, xt, y)
+        np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64), rtol=1e-5)
+        bvg.bvg_csr_spmv_Ax(cg, xt, y)
+        np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64), rtol=1e-5)
+
+
+def test_host_buffer_product():
+    g, hg, dg, ref = graph("ragged_1037")
+    x = synth.rhs(g.n, 3, 17)
+    y = np.zeros_like(x)
+    bvg.bvg_spmv_xA_host(dg, x, y)
+    x64 = x.astype(np.float64)
+    check_close(y, oracle.csr_xA(g.row_ptr, g.col, x64), oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True),
+                "host xA")
+
+
+def test_empty_graph():
+    g = synth.Graph(50, np.zeros(51, np.int64), np.zeros(0, np.int32))
+    hg, dg, ref = encode(g)
+    x = torch.ones(50, 2, device="cuda")
+    y = torch.full_like(x, 7.0)
+    bvg.bvg_spmv_xA(dg, x, y)
+    assert (y == 0).all()
+    bvg.bvg_spmv_Ax(dg, x, y)
+    assert (y == 0).all()
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-12, max_iter=50)
+    np.testing.assert_allclose(p.cpu().numpy(), 1.0 / 50, rtol=1e-6)
+
+
+def test_invalid_arguments():
+    g, hg, dg, ref = graph("tiny_web")
+    x = torch.ones(g.n, device="cuda")
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_spmv_xA(dg, x, x)
+    assert e.value.status == bvg.BVG_ERR_INVALID_ARG
+    lib = bvg.load()
+    hx = np.ones(g.n, np.float32)
+    rc = lib.bvg_spmv_xA(dg.ptr, hx.ctypes.data, x.data_ptr(), 1, 1, None)
+    assert rc == bvg.BVG_ERR_INVALID_ARG  # host pointer given to a device call
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_pagerank(dg, k=3, p0=torch.ones(g.n, 3, device="cuda") / g.n)
+    assert e.value.status == bvg.BVG_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- PageRank
+def l1(a, b):
+    return float(np.abs(np.asarray(a, np.float64).reshape(-1) - np.asarray(b, np.float64).reshape(-1)).sum())
+
+
+@pytest.mark.parametrize("name", ["tiny_web", "ragged_1037", "social_20k"])
+def test_pagerank_fixed_iterations(name):
+    g, hg, dg, ref = graph(name)
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=0.0, max_iter=20)
+    want, it_o, res_o = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=0.0, max_iter=20)
+    assert it == 20 and rc == bvg.BVG_ERR_NOT_CONVERGED
+    assert l1(p.cpu().numpy(), want) <= 1e-6
+    assert abs(res[0] - res_o[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("dangling", [0, 1])
+def test_pagerank_converges_to_oracle(dangling):
+    g, hg, dg, ref = graph("tiny_web")
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500, dangling=dangling)
+    assert rc == bvg.BVG_OK and res[0] < 1e-8
+    pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000, dangling=dangling)
+    assert l1(p.cpu().numpy(), pstar) <= 1e-6
+    assert abs(float(p.double().sum()) - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("k", [2, 8, 32])
+def test_personalized_batch(k):
+    g, hg, dg, ref = graph("tiny_web")
+    seeds = synth.nodes(k, g.n, 31 + k)
+    P0 = np.zeros((g.n, k), np.float32)
+    P0[seeds, np.arange(k)] = 1.0
+    p0 = torch.from_numpy(P0).cuda()
+    p, it, res, rc = bvg.bvg_pagerank(dg, p0=p0, tol=1e-8, max_iter=500)
+    assert rc == bvg.BVG_OK and (res < 1e-8).all()
+    want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, p0=P0.astype(np.float64), tol=1e-13, max_iter=2000)
+    got = p.cpu().numpy()
+    for c in range(k):
+        assert l1(got[:, c], want[:, c]) <= 1e-6, c
+    # batched == one solve per column
+    for c in (0, k - 1):
+        pc, _, _, _ = bvg.bvg_pagerank(dg, p0=p0[:, c:c + 1].contiguous(), tol=1e-8, max_iter=500)
+        assert l1(pc.cpu().numpy()[:, 0], got[:, c]) <= 2e-7
+
+
+def test_pagerank_warm_start_and_not_converged():
+    g, hg, dg, ref = graph("tiny_web")
+    pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000)
+    start = torch.from_numpy(pstar[:, 0].astype(np.float32)).cuda()
+    p, it, res, rc = bvg.bvg_pagerank(dg, p_init=start, tol=1e-8, max_iter=500)
+    p_u, it_u, _, _ = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500)
+    assert rc == bvg.BVG_OK and it < it_u
+    assert l1(p.cpu().numpy(), pstar) <= 1e-6
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-12, max_iter=3)
+    assert rc == bvg.BVG_ERR_NOT_CONVERGED and it == 3
+    want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=0.0, max_iter=3)
+    assert l1(p.cpu().numpy(), want) <= 1e-6
+
+
+def test_pagerank_nan_reported():
+    g, hg, dg, ref = graph("tiny_web")
+    start = torch.full((g.n,), 1.0 / g.n, device="cuda")
+    start[5] = float("nan")
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_pagerank(dg, p_init=start, tol=1e-8, max_iter=50)
+    assert e.value.status == bvg.BVG_ERR_NUMERIC
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def web862k():
+    g = synth.copying_model(synth.web_862k())
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    ref, _ = bvg.bvg_get_refs(hg)
+    return g, hg, bvg.bvg_upload(hg), ref
+
+
+def test_full_size_products(web862k):
+    """n = 862,664, ~19.2 M edges: every entry against the oracle."""
+    g, hg, dg, ref = web862k
+    x = synth.rhs(g.n, 1, synth.seed_for(2, 1))
+    x64 = x.astype(np.float64)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), "xA 862k")
+    bvg.bvg_spmv_Ax(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), "Ax 862k")
+
+
+def test_full_size_pagerank(web862k):
+    g, hg, dg, ref = web862k
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
+    assert rc == bvg.BVG_OK and res[0] < 1e-8
+    pstar, it_o, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-12, max_iter=2000)
+    assert l1(p.cpu().numpy(), pstar) <= 1e-6
