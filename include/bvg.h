@@ -118,6 +118,28 @@ int bvg_get_refs(const bvg_host_graph* g, int32_t* ref, int32_t* depth);
 /* Number of rows n and edges m of an encoding. */
 int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
 
+/* Read-only host view of the device layout that bvg_upload copies to the GPU
+ * (built once per host graph and cached in it; the pointers stay valid until
+ * bvg_free_host). Row-major words carry two tag bits above a 30-bit id:
+ * 0 residual id (+1), 1 dropped id (-1), 2 interval start (next word: 3 |
+ * length). Column-major entries carry the source row with tags 0 (+1 at this
+ * column), 1 (-1), 2 (an interval of that row starts here), 3 (an interval
+ * of that row ended just before this column). carry[carry_ptr[t] ..
+ * carry_ptr[t+1]) lists the rows of intervals [s, e) with
+ * s < t * carry_tile_cols <= e. meta[i] = (i - r_i, or 0) | depth_i << 3. */
+typedef struct {
+    int64_t n, words, col_entries, carry_tiles, carry_entries, carry_tile_cols;
+    const uint8_t* meta;
+    const uint32_t* rowp;
+    const uint32_t* ent;
+    const uint32_t* colp;
+    const uint32_t* tent;
+    const uint32_t* carry_ptr;
+    const uint32_t* carry;
+    const float* inv_outdeg;
+} bvg_layout_view;
+int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out);
+
 /* -------------------------------------------------------------- device side */
 
 /* Builds the device layout of `g` (row-major difference rows for A x^T, the

@@ -34,7 +34,7 @@ EXPORTED = [
     "bvg_encode", "bvg_decode", "bvg_stats", "bvg_get_refs", "bvg_host_size", "bvg_upload", "bvg_spmv_Ax",
     "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
     "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
-    "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout",
+    "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get",
 ]
 
 
@@ -63,6 +63,12 @@ class GraphStats(ctypes.Structure):
 class LayoutInfo(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "m", "words", "col_entries", "carry_tiles", "carry_entries",
                                       "structure_bytes")]
+
+
+class LayoutView(ctypes.Structure):
+    _fields_ = [(f, _I64) for f in ("n", "words", "col_entries", "carry_tiles", "carry_entries",
+                                      "carry_tile_cols")] + \
+               [(f, _P) for f in ("meta", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")]
 
 
 class TraceEntry(ctypes.Structure):
@@ -111,6 +117,7 @@ def load(build_if_needed: bool = True):
             "bvg_last_error": ([], ctypes.c_char_p),
             "bvg_trace_enable": ([_P, ctypes.c_int], ctypes.c_int),
             "bvg_dev_layout": ([_P, ctypes.POINTER(LayoutInfo)], ctypes.c_int),
+            "bvg_layout_view_get": ([_P, ctypes.POINTER(LayoutView)], ctypes.c_int),
             "bvg_trace_read": ([_P, ctypes.POINTER(TraceEntry), _I32, ctypes.POINTER(_I32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -329,6 +336,29 @@ def bvg_csr_spmv_xA(g: CsrGraph, x, y, stream=None):
     k, ld = _km(x, g.n)
     _check(load().bvg_csr_spmv_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_csr_spmv_xA")
     return y
+
+
+def bvg_layout_view_get(hg: HostGraph) -> dict:
+    """Copies of the host-side layout arrays that bvg_upload sends to the GPU."""
+    v = LayoutView()
+    _check(load().bvg_layout_view_get(hg.ptr, ctypes.byref(v)), "bvg_layout_view_get")
+
+    def arr(ptr, count, ct, dt):
+        if count == 0:
+            return np.zeros(0, dt)
+        return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ct)), shape=(count,)).copy()
+    n = v.n
+    return {
+        "n": n, "carry_tile_cols": v.carry_tile_cols,
+        "meta": arr(v.meta, n, ctypes.c_uint8, np.uint8),
+        "rowp": arr(v.rowp, n + 1, ctypes.c_uint32, np.uint32),
+        "ent": arr(v.ent, v.words, ctypes.c_uint32, np.uint32),
+        "colp": arr(v.colp, n + 1, ctypes.c_uint32, np.uint32),
+        "tent": arr(v.tent, v.col_entries, ctypes.c_uint32, np.uint32),
+        "carry_ptr": arr(v.carry_ptr, v.carry_tiles + 1, ctypes.c_uint32, np.uint32),
+        "carry": arr(v.carry, v.carry_entries, ctypes.c_uint32, np.uint32),
+        "inv_outdeg": arr(v.inv_outdeg, n, ctypes.c_float, np.float32),
+    }
 
 
 def bvg_dev_layout(g: DevGraph) -> dict:

@@ -282,85 +282,27 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = hg->n;
-    const int64_t words = hg->stats.words;
-    if (words >= ((int64_t)1 << 32)) return fail(BVG_ERR_UNSUPPORTED, "bvg_upload: more than 2^32 words");
     bvg_dev_graph* g = new (std::nothrow) bvg_dev_graph();
     if (!g) return fail(BVG_ERR_OOM, "bvg_upload: host allocation failed");
     int rc = BVG_OK;
     try {
         BVG_CUDA_TRY(cudaGetDevice(&g->device));
+        const HostLayout* L = nullptr;
+        if ((rc = get_layout(hg, &L))) {
+            delete g;
+            return rc;
+        }
         g->n = n;
         g->m = hg->m;
-        // ---- row-major layout
-        std::vector<uint8_t> meta(n);
-        std::vector<uint32_t> rowp(n + 1), ent((size_t)words);
-        std::vector<float> inv_outdeg(n);
-        rowp[0] = 0;
-        size_t w = 0;
-        for (int64_t i = 0; i < n; i++) {
-            const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
-            meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
-            inv_outdeg[i] = hg->outdeg[i] ? 1.0f / (float)hg->outdeg[i] : 0.0f;
-            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) ent[w++] = pack(kTagMinus, hg->drop[t]);
-            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) ent[w++] = pack(kTagPlus, hg->res[t]);
-            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
-                ent[w++] = pack(kTagIvS, hg->iv_s[t]);
-                ent[w++] = pack(kTagIvL, hg->iv_len[t]);
-            }
-            rowp[i + 1] = (uint32_t)w;
-        }
-        // ---- column-major entries (counting sort by column, rows in order)
-        std::vector<uint32_t> colp(n + 1, 0);
-        auto bump = [&](int64_t j) { colp[j + 1]++; };
-        for (int64_t i = 0; i < n; i++) {
-            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) bump(hg->drop[t]);
-            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) bump(hg->res[t]);
-            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
-                bump(hg->iv_s[t]);
-                int64_t e = (int64_t)hg->iv_s[t] + hg->iv_len[t];
-                if (e < n) bump(e);
-            }
-        }
-        for (int64_t j = 0; j < n; j++) {
-            if ((int64_t)colp[j] + colp[j + 1] >= ((int64_t)1 << 32)) {
-                delete g;
-                return fail(BVG_ERR_UNSUPPORTED, "bvg_upload: more than 2^32 column entries");
-            }
-            colp[j + 1] += colp[j];
-        }
-        std::vector<uint32_t> tent(colp[n]);
-        std::vector<uint32_t> fillp(colp.begin(), colp.end() - 1);
-        const int64_t ntiles = (n + kCarryTile - 1) / kCarryTile;
-        std::vector<uint32_t> carry_ptr(ntiles + 1, 0);
-        for (int64_t i = 0; i < n; i++) {
-            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++)
-                tent[fillp[hg->drop[t]]++] = pack(kTagMinus, (uint32_t)i);
-            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++)
-                tent[fillp[hg->res[t]]++] = pack(kTagPlus, (uint32_t)i);
-            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
-                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
-                tent[fillp[s0]++] = pack(kTagIvS, (uint32_t)i);
-                if (e < n) tent[fillp[e]++] = pack(kTagIvL, (uint32_t)i);
-                for (int64_t ct = s0 / kCarryTile + 1; ct <= (e - 1) / kCarryTile; ct++) carry_ptr[ct + 1]++;
-            }
-        }
-        for (int64_t t = 0; t < ntiles; t++) carry_ptr[t + 1] += carry_ptr[t];
-        std::vector<uint32_t> carry(carry_ptr[ntiles]);
-        std::vector<uint32_t> cfill(carry_ptr.begin(), carry_ptr.end() - 1);
-        for (int64_t i = 0; i < n; i++)
-            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
-                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
-                for (int64_t ct = s0 / kCarryTile + 1; ct <= (e - 1) / kCarryTile; ct++) carry[cfill[ct]++] = (uint32_t)i;
-            }
-        g->nwords = words;
-        g->ntent = colp[n];
-        g->ncarry = carry_ptr[ntiles];
-        if ((rc = upload_vec(&g->meta, meta, st, &g->bytes)) || (rc = upload_vec(&g->rowp, rowp, st, &g->bytes)) ||
-            (rc = upload_vec(&g->ent, ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, colp, st, &g->bytes)) ||
-            (rc = upload_vec(&g->tent, tent, st, &g->bytes)) ||
-            (rc = upload_vec(&g->carry_ptr, carry_ptr, st, &g->bytes)) ||
-            (rc = upload_vec(&g->carry, carry, st, &g->bytes)) ||
-            (rc = upload_vec(&g->inv_outdeg, inv_outdeg, st, &g->bytes))) {
+        g->nwords = (int64_t)L->ent.size();
+        g->ntent = (int64_t)L->tent.size();
+        g->ncarry = (int64_t)L->carry.size();
+        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
+            (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
+            (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
+            (rc = upload_vec(&g->carry_ptr, L->carry_ptr, st, &g->bytes)) ||
+            (rc = upload_vec(&g->carry, L->carry, st, &g->bytes)) ||
+            (rc = upload_vec(&g->inv_outdeg, L->inv_outdeg, st, &g->bytes))) {
             bvg_free_dev(g);
             return rc;
         }

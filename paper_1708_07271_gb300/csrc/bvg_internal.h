@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -38,6 +40,14 @@ inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
 void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);
 
+// Host copy of the device layout (built once per host graph, see layout.cpp).
+struct HostLayout {
+    std::vector<uint8_t> meta;
+    std::vector<uint32_t> rowp, ent, colp, tent, carry_ptr, carry;
+    std::vector<float> inv_outdeg;
+    bool built = false;
+};
+
 }  // namespace bvg
 
 struct bvg_host_graph {
@@ -53,7 +63,14 @@ struct bvg_host_graph {
     std::vector<uint64_t> bits;
     int64_t nbits = 0;
     bvg_graph_stats stats{};
+    mutable std::mutex layout_mu;
+    mutable std::unique_ptr<bvg::HostLayout> layout;
 };
+
+namespace bvg {
+int build_layout(const bvg_host_graph* hg, HostLayout& L);
+int get_layout(const bvg_host_graph* hg, const HostLayout** out);
+}  // namespace bvg
 
 namespace bvg {
 

@@ -415,7 +415,7 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
         int64_t tiles = (n + kCarryTile - 1) / kCarryTile;
         int64_t carry = 0;
         for (int64_t t = 0; t < st.intervals; t++) {
-            int64_t s0 = g->iv_s[t], e0 = s0 + g->iv_len[t] - 1;
+            int64_t s0 = g->iv_s[t], e0 = std::min<int64_t>(s0 + g->iv_len[t], tiles * kCarryTile - 1);
             carry += e0 / kCarryTile - s0 / kCarryTile;
         }
         st.device_bytes = n * 1 + 4 * (n + 1) + 4 * st.words        // row-major

@@ -1,0 +1,132 @@
+// Host construction of the device layout of a BV-delta encoding.
+//
+// Row-major difference rows (for A x^T): per row, 32-bit words tagged
+// (two high bits) as dropped id, residual id, interval start + length word.
+// Column-major entries (for x A): per column j, the source rows k whose
+// difference row holds +1 or -1 at j, and interval events: an interval
+// [s, e) of row k puts a start event at column s and an end event at column
+// e (if e < n); the running sum of start - end events over columns is the
+// interval part of y. Carry lists: for every tile of kCarryTile columns
+// starting at a, the rows k of intervals with s < a <= e, whose start event
+// lies before the tile and whose end event (if any) lies at or after a;
+// summing their z gives the running sum at a without a grid-wide scan.
+#include <algorithm>
+#include <new>
+
+#include "bvg_internal.h"
+
+namespace bvg {
+
+int build_layout(const bvg_host_graph* hg, HostLayout& L) {
+    const int64_t n = hg->n;
+    const int64_t words = hg->stats.words;
+    if (words >= ((int64_t)1 << 32)) return fail(BVG_ERR_UNSUPPORTED, "layout: more than 2^32 words");
+    try {
+        L.meta.assign(n, 0);
+        L.rowp.assign(n + 1, 0);
+        L.ent.assign((size_t)words, 0);
+        L.inv_outdeg.assign(n, 0.f);
+        L.rowp[0] = 0;
+        size_t w = 0;
+        for (int64_t i = 0; i < n; i++) {
+            const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
+            L.meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
+            L.inv_outdeg[i] = hg->outdeg[i] ? 1.0f / (float)hg->outdeg[i] : 0.0f;
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) L.ent[w++] = pack(kTagMinus, hg->drop[t]);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) L.ent[w++] = pack(kTagPlus, hg->res[t]);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                L.ent[w++] = pack(kTagIvS, hg->iv_s[t]);
+                L.ent[w++] = pack(kTagIvL, hg->iv_len[t]);
+            }
+            L.rowp[i + 1] = (uint32_t)w;
+        }
+        // ---- column-major entries (counting sort by column, rows in order)
+        L.colp.assign(n + 1, 0);
+        auto bump = [&](int64_t j) { L.colp[j + 1]++; };
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) bump(hg->drop[t]);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) bump(hg->res[t]);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                bump(hg->iv_s[t]);
+                int64_t e = (int64_t)hg->iv_s[t] + hg->iv_len[t];
+                if (e < n) bump(e);
+            }
+        }
+        for (int64_t j = 0; j < n; j++) {
+            if ((int64_t)L.colp[j] + L.colp[j + 1] >= ((int64_t)1 << 32))
+                return fail(BVG_ERR_UNSUPPORTED, "layout: more than 2^32 column entries");
+            L.colp[j + 1] += L.colp[j];
+        }
+        L.tent.assign(L.colp[n], 0);
+        std::vector<uint32_t> fillp(L.colp.begin(), L.colp.end() - 1);
+        const int64_t ntiles = (n + kCarryTile - 1) / kCarryTile;
+        L.carry_ptr.assign(ntiles + 1, 0);
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++)
+                L.tent[fillp[hg->drop[t]]++] = pack(kTagMinus, (uint32_t)i);
+            for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++)
+                L.tent[fillp[hg->res[t]]++] = pack(kTagPlus, (uint32_t)i);
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
+                L.tent[fillp[s0]++] = pack(kTagIvS, (uint32_t)i);
+                if (e < n) L.tent[fillp[e]++] = pack(kTagIvL, (uint32_t)i);
+                for (int64_t ct = s0 / kCarryTile + 1; ct <= e / kCarryTile && ct < ntiles; ct++) L.carry_ptr[ct + 1]++;
+            }
+        }
+        for (int64_t t = 0; t < ntiles; t++) L.carry_ptr[t + 1] += L.carry_ptr[t];
+        L.carry.assign(L.carry_ptr[ntiles], 0);
+        std::vector<uint32_t> cfill(L.carry_ptr.begin(), L.carry_ptr.end() - 1);
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t t = hg->iv_ptr[i]; t < hg->iv_ptr[i + 1]; t++) {
+                const int64_t s0 = hg->iv_s[t], e = s0 + hg->iv_len[t];
+                for (int64_t ct = s0 / kCarryTile + 1; ct <= e / kCarryTile && ct < ntiles; ct++)
+                    L.carry[cfill[ct]++] = (uint32_t)i;
+            }
+    } catch (const std::bad_alloc&) {
+        return fail(BVG_ERR_OOM, "layout: host allocation failed");
+    }
+    L.built = true;
+    return BVG_OK;
+}
+
+int get_layout(const bvg_host_graph* hg, const HostLayout** out) {
+    std::lock_guard<std::mutex> lk(hg->layout_mu);
+    if (!hg->layout) {
+        HostLayout* L = new (std::nothrow) HostLayout();
+        if (!L) return fail(BVG_ERR_OOM, "layout: host allocation failed");
+        int rc = build_layout(hg, *L);
+        if (rc) {
+            delete L;
+            return rc;
+        }
+        hg->layout.reset(L);
+    }
+    *out = hg->layout.get();
+    return BVG_OK;
+}
+
+}  // namespace bvg
+
+using namespace bvg;
+
+extern "C" int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out) {
+    if (!g || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_layout_view_get: NULL argument");
+    const HostLayout* L = nullptr;
+    int rc = get_layout(g, &L);
+    if (rc) return rc;
+    out->n = g->n;
+    out->words = (int64_t)L->ent.size();
+    out->col_entries = (int64_t)L->tent.size();
+    out->carry_tiles = (int64_t)L->carry_ptr.size() - 1;
+    out->carry_entries = (int64_t)L->carry.size();
+    out->carry_tile_cols = kCarryTile;
+    out->meta = L->meta.data();
+    out->rowp = L->rowp.data();
+    out->ent = L->ent.data();
+    out->colp = L->colp.data();
+    out->tent = L->tent.data();
+    out->carry_ptr = L->carry_ptr.data();
+    out->carry = L->carry.data();
+    out->inv_outdeg = L->inv_outdeg.data();
+    return BVG_OK;
+}

@@ -1,0 +1,103 @@
+"""The device layout, read on the CPU: evaluating its entries with the
+arithmetic the kernels use (in FP64, in NumPy) must give the oracle's
+products. Covers the carry-in lists for every tile size a kernel may use
+(a multiple of the carry tile), the interval start/end events, the chain
+bits of meta, and the row-major words. No GPU needed."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1708_07271_gb300 as bvg
+
+TAG_SHIFT = 30
+MASK = (1 << 30) - 1
+
+
+def emulate_xA(L, x, tile):
+    n = L["n"]
+    meta = L["meta"].astype(np.int64)
+    off = meta & 7
+    depth = meta >> 3
+    z = x.astype(np.float64).copy()
+    # reverse level order: rows of depth d add into their reference
+    for d in range(3, 0, -1):
+        rows = np.nonzero((depth == d) & (off > 0))[0]
+        np.add.at(z, rows - off[rows], z[rows])
+    tent = L["tent"].astype(np.int64)
+    tag = tent >> TAG_SHIFT
+    src = tent & MASK
+    col = np.repeat(np.arange(n), np.diff(L["colp"].astype(np.int64)))
+    sign = np.where(tag == 1, -1.0, 1.0)[:, None]
+    y = np.zeros_like(z)
+    pt = tag < 2
+    np.add.at(y, col[pt], sign[pt] * z[src[pt]])
+    D = np.zeros_like(z)
+    ev = ~pt
+    np.add.at(D, col[ev], np.where(tag[ev] == 3, -1.0, 1.0)[:, None] * z[src[ev]])
+    G = L["carry_tile_cols"]
+    assert tile % G == 0
+    for a in range(0, n, tile):
+        ct = a // G
+        lo, hi = L["carry_ptr"][ct], L["carry_ptr"][ct + 1]
+        run = z[L["carry"][lo:hi].astype(np.int64)].sum(axis=0)
+        e = min(n, a + tile)
+        y[a:e] += run + np.cumsum(D[a:e], axis=0)
+    return y
+
+
+def emulate_Ax(L, x):
+    n = L["n"]
+    x = x.astype(np.float64)
+    c = np.zeros_like(x)
+    rowp = L["rowp"].astype(np.int64)
+    ent = L["ent"].astype(np.int64)
+    for i in range(n):
+        w = rowp[i]
+        while w < rowp[i + 1]:
+            tag, j = ent[w] >> TAG_SHIFT, ent[w] & MASK
+            if tag == 0:
+                c[i] += x[j]
+            elif tag == 1:
+                c[i] -= x[j]
+            elif tag == 2:
+                ln = ent[w + 1] & MASK
+                assert ent[w + 1] >> TAG_SHIFT == 3
+                c[i] += x[j:j + ln].sum(axis=0)
+                w += 1
+            w += 1
+    y = np.zeros_like(c)
+    off = (L["meta"] & 7).astype(np.int64)
+    for i in range(n):
+        y[i] = c[i] + (y[i - off[i]] if off[i] else 0.0)
+    return y
+
+
+GRAPHS = {
+    "tiny_web": lambda: synth.copying_model(synth.tiny_web()),
+    "ragged": lambda: synth.copying_model(synth.replace(synth.tiny_web(), n=1037, seed=77)),
+    "long_runs": lambda: synth.copying_model(synth.GraphSpec(n=3000, seed=6, p_copy=0.6, fidelity=0.95,
+                                                             extra_mean=1.0, fresh_mean=300, q_run=0.9,
+                                                             run_min=100, run_max=900, gap_mean=50.0)),
+    "social": lambda: synth.copying_model(synth.replace(synth.social_5m4(), n=5000)),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_layout_reproduces_products(name):
+    g = GRAPHS[name]()
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    L = bvg.bvg_layout_view_get(hg)
+    x = synth.rhs(g.n, 2, 3).astype(np.float64)
+    want_xA = oracle.csr_xA(g.row_ptr, g.col, x)
+    for tile in (128, 256, 1024, 4096):
+        np.testing.assert_allclose(emulate_xA(L, x, tile), want_xA, rtol=1e-9, atol=1e-9)
+    if g.n <= 5000:
+        np.testing.assert_allclose(emulate_Ax(L, x), oracle.csr_Ax(g.row_ptr, g.col, x), rtol=1e-9, atol=1e-9)
+    # 1/outdeg and chain bits
+    deg = np.diff(g.row_ptr)
+    np.testing.assert_array_equal(L["inv_outdeg"], np.where(deg > 0, 1.0 / np.maximum(deg, 1), 0).astype(np.float32))
+    ref, depth = bvg.bvg_get_refs(hg)
+    off = (L["meta"] & 7).astype(np.int64)
+    np.testing.assert_array_equal(np.where(ref >= 0, np.arange(g.n) - ref, 0), off)
+    np.testing.assert_array_equal(L["meta"] >> 3, depth)
