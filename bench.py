@@ -252,9 +252,13 @@ def run_bv(args):
     y = torch.empty_like(x)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def timed(fn, steps, trace_graph=None):
-        """per-step CUDA-event time (ms) with an L2 flush before each step."""
+    def timed(fn, steps):
+        """Per-step CUDA-event time (ms) with an L2 flush before each step. The
+        steps are queued behind a sleep kernel so the host runs ahead and the
+        events time the device work, not host launch gaps."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        torch.cuda._sleep(int(2.0e6 * min(500.0, 20.0 + 2.0 * steps)))
         for a, b in evs:
             flush.fill_(1.0)
             a.record(stream)

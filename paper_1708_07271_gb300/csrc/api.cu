@@ -232,17 +232,23 @@ static int64_t max_grid(const bvg_dev_graph* g) {
     return std::max<int64_t>(best, 1);
 }
 
+static void drop_pr_graph(bvg_dev_graph* g) {
+    if (g->s.pr_exec) cudaGraphExecDestroy((cudaGraphExec_t)g->s.pr_exec);
+    g->s.pr_exec = nullptr;
+}
+
 static int ensure_pr(bvg_dev_graph* g, int kb) {
     int rc = ensure_z(g, kb);
     if (rc) return rc;
     if (g->s.pr_kcap < kb) {
-        for (int p = 0; p < 2; p++) {
-            if (g->s.q[p]) cudaFree(g->s.q[p]);
-            g->s.q[p] = nullptr;
+        drop_pr_graph(g);
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
+            if (*b) cudaFree(*b);
+            *b = nullptr;
         }
         g->s.pr_kcap = 0;
-        for (int p = 0; p < 2; p++) {
-            rc = dev_alloc((void**)&g->s.q[p], (size_t)g->n * kb * sizeof(float), nullptr);
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
+            rc = dev_alloc((void**)b, (size_t)g->n * kb * sizeof(float), nullptr);
             if (rc) return rc;
         }
         g->s.pr_kcap = kb;
@@ -327,7 +333,8 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
     void* ptrs[] = {g->meta, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
-                    g->s.hy};
+                    g->s.hy, g->s.p0};
+    drop_pr_graph(g);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->s.host_state) cudaFreeHost(g->s.host_state);
@@ -503,6 +510,11 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     PrState hs{0, 0, 0, max_iter, tol};
     PrState* pst = (PrState*)g->s.st;
     BVG_CUDA_TRY(cudaMemcpyAsync(pst, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    // the update graph reads the teleport vectors from the handle's own copy
+    if (p0)
+        BVG_CUDA_TRY(cudaMemcpyAsync(g->s.p0, p0, (size_t)g->n * kb * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    const float* p0_in = p0;
+    p0 = p0 ? g->s.p0 : nullptr;
     PrArgs base{};
     base.p0 = p0;
     base.ldp0 = kb;
@@ -519,9 +531,17 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         PrArgs pa = base;
         pa.q_new = g->s.q[0];
         pa.sc_new = g->s.sc[0];
-        const float* start = p_init ? p_init : p0;
+        const float* start = p_init ? p_init : p0_in;
         BVG_KV_CASES(launch_pr_init, g, start, kb, pa, st);
     }
+    // A chunk of kChunk updates (even, so it starts on parity 0 every time)
+    // is captured once per configuration and replayed; the device state makes
+    // updates past convergence or max_iter return at once.
+    constexpr int kChunk = 8;
+    const int key[4] = {kb, v, dangling, p0 != nullptr};
+    if (g->s.pr_exec && (memcmp(key, g->s.pr_key, sizeof(key)) || g->s.pr_key_alpha != base.alpha ||
+                         g->s.pr_key_ptr != g->s.q[0]))
+        drop_pr_graph(g);
     auto launch_update = [&](int par) {
         // update reading q[par], writing q[1 - par]
         PrArgs pa = base;
@@ -535,13 +555,33 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     PrState* hst = (PrState*)g->s.host_state;
     double* hres = (double*)((char*)g->s.host_state + sizeof(PrState));
     int launched = 0;
-    int next_poll = std::min(max_iter, 8);
+    int next_poll = std::min(max_iter, 2 * kChunk);
     double last_res = INFINITY;
     int last_res_iter = 0;
+    if (!g->s.pr_exec) {
+        Tracer* tr = g->tracer;
+        const bool tr_on = tr && tr->on;
+        if (tr) tr->on = false;
+        cudaGraph_t graph = nullptr;
+        BVG_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        for (int u = 0; u < kChunk; u++) launch_update(u & 1);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (tr) tr->on = tr_on;
+        if (ce != cudaSuccess) return fail(BVG_ERR_CUDA, "bvg_pagerank: capture failed: %s", cudaGetErrorString(ce));
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(BVG_ERR_CUDA, "bvg_pagerank: instantiate failed: %s", cudaGetErrorString(ce));
+        g->s.pr_exec = exec;
+        memcpy(g->s.pr_key, key, sizeof(key));
+        g->s.pr_key_alpha = base.alpha;
+        g->s.pr_key_ptr = g->s.q[0];
+    }
     for (;;) {
         while (launched < next_poll) {
-            launch_update(launched & 1);
-            launched++;
+            TraceScope ts(g, "pr_update_x8", st);
+            BVG_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)g->s.pr_exec, st));
+            launched += kChunk;
         }
         BVG_CUDA_TRY(cudaGetLastError());
         // state and the residuals of both parities; the state says which is current
@@ -550,7 +590,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         BVG_CUDA_TRY(cudaMemcpyAsync(hres + 32, g->s.sc[1] + 2 * kb, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         BVG_CUDA_TRY(cudaStreamSynchronize(st));
         if (hst->done || hst->iter >= max_iter) break;
-        if (launched >= max_iter || hst->iter < launched - 1)
+        if (launched >= max_iter || hst->iter != launched)
             return fail(BVG_ERR_CUDA, "bvg_pagerank: device state did not advance (%d of %d updates)", hst->iter,
                         launched);
         // plan the next poll from the observed contraction of the residual
@@ -565,7 +605,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
             rate = std::min(rate, 0.999);
             double need = std::log(tol / r) / std::log(rate);
             ahead = (int)std::ceil(need);
-            ahead = std::max(2, std::min(ahead, 64));
+            ahead = std::max(kChunk, std::min(ahead, 64));
         }
         last_res = r;
         last_res_iter = hst->iter;

@@ -97,6 +97,12 @@ struct DevScratch {
     int64_t pr_kcap = 0;                // columns the PageRank buffers hold
     int64_t partial_cap = 0;            // doubles in `partial`
     int64_t stage_cap = 0;              // floats in hx / hy
+    float* p0 = nullptr;                // PageRank teleport vectors (copy), n x pr_kcap
+    // CUDA graph of a chunk of PageRank updates, and what it was built for
+    void* pr_exec = nullptr;            // cudaGraphExec_t
+    int pr_key[4] = {0, 0, 0, 0};       // kb, v, dangling, has p0
+    float pr_key_alpha = 0.f;
+    const void* pr_key_ptr = nullptr;   // q[0] when captured
 };
 
 }  // namespace bvg

@@ -24,7 +24,7 @@ struct PrArgs {
     const float* q_prev;       // previous iterate, unnormalised (n x k, ld ldq)
     float* q_new;
     int64_t ldq;
-    const double* sc_prev;     // [3][k]: 1/S, dangling mass (normalised), resid
+    const double* sc_prev;     // [3][k]: 1/S, dangling mass, resid (of the previous update)
     double* sc_new;
     PrState* st;
     double* partial;           // [grid][3][KB]
@@ -242,7 +242,7 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
         for (int c = 0; c < pa.k; c++) {
             const double Ssum = sh_tot[0][c], Rsum = sh_tot[1][c], Dsum = sh_tot[2][c];
             pa.sc_new[0 * KB + c] = 1.0 / Ssum;
-            pa.sc_new[1 * KB + c] = Dsum / Ssum;
+            pa.sc_new[1 * KB + c] = Dsum;
             pa.sc_new[2 * KB + c] = init ? INFINITY : Rsum;
             if (!(Rsum < pa.st->tol)) conv = false;
             if (!isfinite(Ssum) || !isfinite(Dsum) || (!init && !isfinite(Rsum)) || Ssum <= 0.0) bad = true;
@@ -301,13 +301,10 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
     double S[V], R[V], Dg[V];
 #pragma unroll
     for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
-    double inv_s[V], delta[V];
+    double delta[V];
     if constexpr (EPI == 1) {
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            inv_s[v] = pa.sc_prev[0 * KB + lane * V + v];
-            delta[v] = pa.sc_prev[1 * KB + lane * V + v];
-        }
+        for (int v = 0; v < V; v++) delta[v] = pa.sc_prev[1 * KB + lane * V + v];
     }
 
     for (int64_t base = a; base < end; base += (int64_t)NG * CPT) {
@@ -393,11 +390,10 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
                 for (int v = 0; v < V; v++) {
                     const float p0j = pa.p0 ? p0v.v[v] : un;
                     const float gj = pa.dangling_uniform ? un : p0j;
-                    const float yj = __fmul_rn(out.v[v], (float)inv_s[v]);
-                    const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (yj + (float)delta[v] * gj);
+                    const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + (float)delta[v] * gj);
                     qn.v[v] = qj;
                     S[v] += (double)qj;
-                    R[v] += fabs((double)qj - (double)qp.v[v] * inv_s[v]);
+                    R[v] += fabs((double)qj - (double)qp.v[v]);
                     if (io == 0.0f) Dg[v] += (double)qj;
                 }
                 stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);

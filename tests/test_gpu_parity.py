@@ -183,7 +183,7 @@ def test_pagerank_fixed_iterations(name):
 def test_pagerank_converges_to_oracle(dangling):
     g, hg, dg, ref = graph("tiny_web")
     p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500, dangling=dangling)
-    assert rc == bvg.BVG_OK and res[0] < 1e-8
+    assert rc == bvg.BVG_OK and res[0] < 1e-8, (rc, it, res)
     pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000, dangling=dangling)
     assert l1(p.cpu().numpy(), pstar) <= 1e-6
     assert abs(float(p.double().sum()) - 1.0) < 1e-5
@@ -197,7 +197,7 @@ def test_personalized_batch(k):
     P0[seeds, np.arange(k)] = 1.0
     p0 = torch.from_numpy(P0).cuda()
     p, it, res, rc = bvg.bvg_pagerank(dg, p0=p0, tol=1e-8, max_iter=500)
-    assert rc == bvg.BVG_OK and (res < 1e-8).all()
+    assert rc == bvg.BVG_OK and (res < 1e-8).all(), (rc, it, res)
     want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, p0=P0.astype(np.float64), tol=1e-13, max_iter=2000)
     got = p.cpu().numpy()
     for c in range(k):
@@ -214,7 +214,7 @@ def test_pagerank_warm_start_and_not_converged():
     start = torch.from_numpy(pstar[:, 0].astype(np.float32)).cuda()
     p, it, res, rc = bvg.bvg_pagerank(dg, p_init=start, tol=1e-8, max_iter=500)
     p_u, it_u, _, _ = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500)
-    assert rc == bvg.BVG_OK and it < it_u
+    assert rc == bvg.BVG_OK and it < it_u, (rc, it, it_u, res)
     assert l1(p.cpu().numpy(), pstar) <= 1e-6
     p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-12, max_iter=3)
     assert rc == bvg.BVG_ERR_NOT_CONVERGED and it == 3
@@ -258,6 +258,6 @@ def test_full_size_products(web862k):
 def test_full_size_pagerank(web862k):
     g, hg, dg, ref = web862k
     p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
-    assert rc == bvg.BVG_OK and res[0] < 1e-8
+    assert rc == bvg.BVG_OK and res[0] < 1e-8, (rc, it, res)
     pstar, it_o, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-12, max_iter=2000)
     assert l1(p.cpu().numpy(), pstar) <= 1e-6
