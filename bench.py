@@ -166,12 +166,19 @@ def dist_setup(args):
 
 
 # ----------------------------------------------------------------- CPU oracle
-def cpu_oracle_run(g, k, seconds, max_runs=None):
-    """Times the oracle's compressed product (Sec. 4 push form, FP64, 1 thread)."""
+def cpu_oracle_prepare(g, k):
+    """Inputs of the oracle's compressed product: its own references and x."""
     import oracle
     import synth
     ref, _ = oracle.choose_refs(g.row_ptr, g.col)
     x = synth.rhs(g.n, k, synth.seed_for(2, 1)).astype(np.float64)
+    return ref, x
+
+
+def cpu_oracle_run(g, prep, seconds, max_runs=None):
+    """Times the oracle's compressed product (Sec. 4 push form, FP64, 1 thread)."""
+    import oracle
+    ref, x = prep
     times = []
     t_all = time.perf_counter()
     while True:
@@ -191,12 +198,13 @@ def run_reference(args):
     if rank != 0:
         return
     g = synth.copying_model(workload_spec())
+    prep = cpu_oracle_prepare(g, args.k)
     # each step is one full product of the oracle
     for _ in range(max(0, args.warmup)):
-        cpu_oracle_run(g, args.k, 0.0, max_runs=1)
+        cpu_oracle_run(g, prep, 0.0, max_runs=1)
     times = []
     for _ in range(args.steps):
-        times += cpu_oracle_run(g, args.k, 0.0, max_runs=1)
+        times += cpu_oracle_run(g, prep, 0.0, max_runs=1)
     t = float(np.sum(times))
     val = g.m * args.k * args.steps / t / 1e9
     out = {
@@ -338,7 +346,7 @@ def run_bv(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times = cpu_oracle_run(g, k, args.cpu_seconds)
+        times = cpu_oracle_run(g, cpu_oracle_prepare(g, k), args.cpu_seconds)
         cpu = {"value": g.m * k / float(np.mean(times)) / 1e9, "unit": "Gedges/s", "cores": 1, "kind": "oracle",
                "sample": f"{len(times)} full products of the oracle's compressed x A (FP64, C, 1 thread) on the "
                          f"same graph, {np.sum(times):.1f} s; host has {os.cpu_count()} cores"}
