@@ -335,6 +335,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0};
     drop_pr_graph(g);
+    if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->s.host_state) cudaFreeHost(g->s.host_state);
@@ -563,15 +564,34 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         const bool tr_on = tr && tr->on;
         if (tr) tr->on = false;
         cudaGraph_t graph = nullptr;
-        BVG_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-        for (int u = 0; u < kChunk; u++) launch_update(u & 1);
-        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); capturing executes nothing
+        if (!g->s.cap_stream) {
+            cudaStream_t cs = nullptr;
+            BVG_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            g->s.cap_stream = cs;
+        }
+        cudaStream_t cs = (cudaStream_t)g->s.cap_stream;
+        BVG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        {
+            cudaStream_t user = st;
+            st = cs;  // launch_update launches on `st`
+            for (int u = 0; u < kChunk; u++) launch_update(u & 1);
+            st = user;
+        }
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
         if (tr) tr->on = tr_on;
-        if (ce != cudaSuccess) return fail(BVG_ERR_CUDA, "bvg_pagerank: capture failed: %s", cudaGetErrorString(ce));
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BVG_ERR_CUDA, "bvg_pagerank: capture failed: %s", cudaGetErrorString(ce));
+        }
         cudaGraphExec_t exec = nullptr;
         ce = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return fail(BVG_ERR_CUDA, "bvg_pagerank: instantiate failed: %s", cudaGetErrorString(ce));
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BVG_ERR_CUDA, "bvg_pagerank: instantiate failed: %s", cudaGetErrorString(ce));
+        }
         g->s.pr_exec = exec;
         memcpy(g->s.pr_key, key, sizeof(key));
         g->s.pr_key_alpha = base.alpha;

@@ -100,6 +100,7 @@ struct DevScratch {
     float* p0 = nullptr;                // PageRank teleport vectors (copy), n x pr_kcap
     // CUDA graph of a chunk of PageRank updates, and what it was built for
     void* pr_exec = nullptr;            // cudaGraphExec_t
+    void* cap_stream = nullptr;         // private stream the update graph is captured on
     int pr_key[4] = {0, 0, 0, 0};       // kb, v, dangling, has p0
     float pr_key_alpha = 0.f;
     const void* pr_key_ptr = nullptr;   // q[0] when captured

@@ -111,7 +111,9 @@ __device__ __forceinline__ uint32_t id_of(uint32_t w) { return w & kIdMask; }
 #define BVG_CUDA_TRY(expr)                                                                       \
     do {                                                                                         \
         cudaError_t e_ = (expr);                                                                 \
-        if (e_ != cudaSuccess)                                                                   \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError(); /* do not leave a non-sticky error for the caller's next check */ \
             return ::bvg::fail(BVG_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
                                __LINE__);                                                        \
+        }                                                                                        \
     } while (0)
