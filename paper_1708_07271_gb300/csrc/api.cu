@@ -97,7 +97,10 @@ static int gather_cols_per_pass(int kb, int v) {
     int cpt = G == 1 ? (kb <= 2 ? 4 : 2) : (G <= 2 ? 2 : 1);
     return NG * cpt;
 }
+// The staged gather kernel serves kb <= 4 with full-width vector access.
+static bool gather_staged(int kb, int v) { return kb <= 4 && v == kb; }
 static int gather_tile(int kb, int v, const LaunchCfg& c) {
+    if (gather_staged(kb, v)) return 1024 / kb;
     int per = gather_cols_per_pass(kb, v);
     int t = std::max(c.gather_tile / kb, per);
     t = (t + kCarryTile - 1) / kCarryTile * kCarryTile;
@@ -162,11 +165,12 @@ template <int KB, int V>
 static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
                          int64_t ldz, const PrState* pst, cudaStream_t st) {
     const int tile = chain_tile(KB, g->cfg);
-    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(df) + (tile + kHalo) + 15) / 16 * 16;
+    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(df) + 2 * (tile + kHalo) + 15) / 16 * 16;
     set_smem(k_chain<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
-    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, x, ldx, rowscale, z, ldz, g->n, tile, pst);
+    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->kids, x, ldx, rowscale, z, ldz, g->n, tile,
+                                                           pst);
 }
 
 template <int KB, int V>
@@ -175,8 +179,13 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
-    k_gather<KB, V, gather_cpt<KB, V>(), 0><<<(unsigned)grid, kThreads, 0, st>>>(
-        g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, y, ldy, g->n, tile, pa);
+    if constexpr (KB <= 4 && V == KB) {
+        k_gather_st<KB, 0><<<(unsigned)grid, kThreads, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry, z, y,
+                                                                 ldy, g->n, pa);
+    } else {
+        k_gather<KB, V, gather_cpt<KB, V>(), 0><<<(unsigned)grid, kThreads, 0, st>>>(
+            g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, y, ldy, g->n, tile, pa);
+    }
 }
 
 template <int KB, int V>
@@ -184,8 +193,13 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
-    k_gather<KB, V, gather_cpt<KB, V>(), 1><<<(unsigned)grid, kThreads, 0, st>>>(
-        g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, nullptr, 0, g->n, tile, pa);
+    if constexpr (KB <= 4 && V == KB) {
+        k_gather_st<KB, 1><<<(unsigned)grid, kThreads, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry, z,
+                                                                 nullptr, 0, g->n, pa);
+    } else {
+        k_gather<KB, V, gather_cpt<KB, V>(), 1><<<(unsigned)grid, kThreads, 0, st>>>(
+            g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, nullptr, 0, g->n, tile, pa);
+    }
 }
 
 template <int KB, int V>
@@ -303,7 +317,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->nwords = (int64_t)L->ent.size();
         g->ntent = (int64_t)L->tent.size();
         g->ncarry = (int64_t)L->carry.size();
-        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
+        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->kids, L->kids, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
             (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
             (rc = upload_vec(&g->carry_ptr, L->carry_ptr, st, &g->bytes)) ||
@@ -331,7 +345,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
 
 extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
-    void* ptrs[] = {g->meta, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
+    void* ptrs[] = {g->meta, g->kids, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0};
     drop_pr_graph(g);

@@ -42,7 +42,7 @@ int fail(int status, const char* fmt, ...);
 
 // Host copy of the device layout (built once per host graph, see layout.cpp).
 struct HostLayout {
-    std::vector<uint8_t> meta;
+    std::vector<uint8_t> meta, kids;
     std::vector<uint32_t> rowp, ent, colp, tent, carry_ptr, carry;
     std::vector<float> inv_outdeg;
     bool built = false;
@@ -117,6 +117,7 @@ struct bvg_dev_graph {
     int device = 0;
     // row-major difference rows (A x^T)
     uint8_t* meta = nullptr;   // n: bits 0-2 reference offset (0 = none), bits 3-4 depth
+    uint8_t* kids = nullptr;   // n: bit t set iff row i + t + 1 references row i
     uint32_t* rowp = nullptr;  // n+1 word offsets
     uint32_t* ent = nullptr;   // words
     int64_t nwords = 0;

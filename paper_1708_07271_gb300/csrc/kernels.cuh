@@ -113,21 +113,24 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 // passes through k (Proposition 1 read for the left product: v_i is the sum
 // of the difference rows along its chain). A CTA owns rows [a, a + tile) and
 // reads kHalo rows past its end (a subtree spans at most kHalo rows). Rows
-// are visited in reverse level order: first the rows of depth R-1 gather
-// their children (depth R), then depth R-2, ..., then the roots; each gather
-// scans the W rows after k for those whose reference is k. Optionally x is
-// scaled per row first (x_i * rowscale_i, PageRank's 1/outdeg).
+// are visited in reverse level order: first the rows of depth R-1 add their
+// children (depth R, already final), then depth R-2, ..., then the roots.
+// kids[k] lists the children of k as bits (row k + t + 1 for bit t), so a
+// row touches only its real children; the additions of one row happen in a
+// fixed order, so z is bit-reproducible. Optionally x is scaled per row
+// first (x_i * rowscale_i, PageRank's 1/outdeg).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
-__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta, const float* __restrict__ x,
-                                               int64_t ldx, const float* __restrict__ rowscale,
-                                               float* __restrict__ z, int64_t ldz, int64_t n, int tile,
-                                               const PrState* __restrict__ st) {
+__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta, const uint8_t* __restrict__ kids,
+                                               const float* __restrict__ x, int64_t ldx,
+                                               const float* __restrict__ rowscale, float* __restrict__ z,
+                                               int64_t ldz, int64_t n, int tile, const PrState* __restrict__ st) {
     if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
     constexpr int G = KB / V;
     extern __shared__ float4 smem_chain[];
-    df* zs = reinterpret_cast<df*>(smem_chain);                       // [(tile + kHalo) * KB]
-    uint8_t* ms = reinterpret_cast<uint8_t*>(zs + (int64_t)(tile + kHalo) * KB);  // [tile + kHalo]
+    df* zs = reinterpret_cast<df*>(smem_chain);                                   // [(tile + kHalo) * KB]
+    uint8_t* ms = reinterpret_cast<uint8_t*>(zs + (int64_t)(tile + kHalo) * KB);  // depth, [tile + kHalo]
+    uint8_t* ks = ms + tile + kHalo;                                              // children, [tile + kHalo]
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
@@ -135,7 +138,10 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta,
     const int cnt = (int)(hi - a);
     const int own = (int)((a + tile < n ? a + tile : n) - a);
 
-    for (int r = threadIdx.x; r < cnt; r += blockDim.x) ms[r] = __ldg(meta + a + r);
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        ms[r] = __ldg(meta + a + r) >> 3;
+        ks[r] = __ldg(kids + a + r);
+    }
     for (int r = g; r < cnt; r += NG) {
         Vec<V> xv = ldv<V>(x + (a + r) * ldx + lane * V);
         const float sc = rowscale ? __ldg(rowscale + a + r) : 1.0f;
@@ -145,14 +151,17 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta,
     __syncthreads();
     for (int d = kMaxChain - 1; d >= 0; d--) {
         for (int r = g; r < cnt; r += NG) {
-            if ((ms[r] >> 3) != d) continue;
+            unsigned km = ks[r];
+            if (km == 0 || ms[r] != d) continue;
             df acc[V];
 #pragma unroll
             for (int v = 0; v < V; v++) acc[v] = zs[(int64_t)r * KB + lane * V + v];
-            for (int cc = r + 1; cc <= r + kMaxWindow && cc < cnt; cc++) {
-                if ((ms[cc] & 7) != cc - r) continue;
+            while (km) {
+                const int c = r + __ffs(km);  // bit t -> row r + t + 1
+                km &= km - 1;
+                if (c >= cnt) break;
 #pragma unroll
-                for (int v = 0; v < V; v++) acc[v] = df_add(acc[v], zs[(int64_t)cc * KB + lane * V + v]);
+                for (int v = 0; v < V; v++) acc[v] = df_add(acc[v], zs[(int64_t)c * KB + lane * V + v]);
             }
 #pragma unroll
             for (int v = 0; v < V; v++) zs[(int64_t)r * KB + lane * V + v] = acc[v];
@@ -401,6 +410,182 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         }
 #pragma unroll
         for (int v = 0; v < V; v++) run[v] = df_add(run[v], btot[v]);
+    }
+    if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
+}
+
+// ---------------------------------------------------------------------------
+// Push, scatter step for KB <= 4 right-hand sides, shared-memory staged.
+// Same arithmetic as k_gather (owner computes, interval prefix from the carry
+// list), organised so that the irregular work is cheap: a CTA owns T = 1024/KB
+// columns; their column-major entries are staged in chunks of C words; the
+// z-gathers run one entry per thread (balanced, coalesced entry reads); then
+// each thread sums the staged values of its CPT consecutive columns from
+// shared memory, and one compensated block scan forms the interval prefix.
+// ---------------------------------------------------------------------------
+template <int KB, int EPI>
+__global__ void __launch_bounds__(256) k_gather_st(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                                   const uint32_t* __restrict__ carry_ptr,
+                                                   const uint32_t* __restrict__ carry, const float* __restrict__ z,
+                                                   float* __restrict__ y, int64_t ldy, int64_t n, PrArgs pa) {
+    constexpr int V = KB;
+    constexpr int NT = 256;
+    constexpr int CPT = 4 / KB;   // columns per thread
+    constexpr int T = NT * CPT;   // columns per CTA (a multiple of kCarryTile)
+    constexpr int C = 4096 / KB;  // entries staged per chunk
+    static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
+    if constexpr (EPI == 1) {
+        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+    }
+    __shared__ uint32_t cp_s[T + 1];
+    __shared__ uint32_t ent_s[C];
+    __shared__ float val_s[C * KB];
+    __shared__ df run_s[KB];
+    __shared__ df wtot_s[NT / 32][KB];
+    __shared__ df wpre_s[NT / 32][KB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t a = (int64_t)blockIdx.x * T;
+    const int ncols = (int)((a + T < n ? a + T : n) - a);
+
+    for (int i = tid; i <= ncols; i += NT) cp_s[i] = __ldg(colp + a + i);
+    if (warp == 0) {
+        // running interval sum at column a: sources of intervals open there
+        df acc[KB];
+#pragma unroll
+        for (int v = 0; v < KB; v++) acc[v] = df_zero();
+        const int64_t ct = a / kCarryTile;
+        const uint32_t e1 = __ldg(carry_ptr + ct + 1);
+        for (uint32_t e = __ldg(carry_ptr + ct) + lane; e < e1; e += 32) {
+            Vec<V> zv = ldv<V>(z + (int64_t)__ldg(carry + e) * KB);
+#pragma unroll
+            for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], zv.v[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < KB; v++)
+            for (int o = 16; o > 0; o >>= 1) acc[v] = df_add(acc[v], {__shfl_down_sync(0xffffffffu, acc[v].hi, o),
+                                                                        __shfl_down_sync(0xffffffffu, acc[v].lo, o)});
+        if (lane == 0) {
+#pragma unroll
+            for (int v = 0; v < KB; v++) run_s[v] = acc[v];
+        }
+    }
+    __syncthreads();
+
+    df P[CPT][KB], D[CPT][KB];
+#pragma unroll
+    for (int q = 0; q < CPT; q++)
+#pragma unroll
+        for (int v = 0; v < KB; v++) P[q][v] = D[q][v] = df_zero();
+    const uint32_t ebase = cp_s[0], eend = cp_s[ncols];
+    for (uint32_t c0 = ebase; c0 < eend; c0 += C) {
+        const int cnt = (int)(eend - c0 < (uint32_t)C ? eend - c0 : (uint32_t)C);
+        for (int e = tid; e < cnt; e += NT) {
+            const uint32_t w = __ldg(tent + c0 + e);
+            ent_s[e] = w;
+            Vec<V> zv = ldv<V>(z + (int64_t)id_of(w) * KB);
+            const bool neg = (w >> kIdBits) & 1;
+#pragma unroll
+            for (int v = 0; v < KB; v++) val_s[e * KB + v] = neg ? -zv.v[v] : zv.v[v];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            const int jl = tid * CPT + q;
+            if (jl >= ncols) continue;
+            const uint32_t lo = cp_s[jl] > c0 ? cp_s[jl] : c0;
+            const uint32_t hi = cp_s[jl + 1] < c0 + cnt ? cp_s[jl + 1] : c0 + cnt;
+            for (uint32_t e = lo; e < hi; e++) {
+                const int el = (int)(e - c0);
+                const bool point = (ent_s[el] >> kIdBits) < 2;
+#pragma unroll
+                for (int v = 0; v < KB; v++) {
+                    const float val = val_s[el * KB + v];
+                    if (point) P[q][v] = df_addf(P[q][v], val);
+                    else D[q][v] = df_addf(D[q][v], val);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // interval prefix: thread-local over CPT columns, then across threads
+    df tot[KB], Dinc[CPT][KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) tot[v] = df_zero();
+#pragma unroll
+    for (int q = 0; q < CPT; q++)
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            tot[v] = df_add(tot[v], D[q][v]);
+            Dinc[q][v] = tot[v];
+        }
+    df inc[KB], ex[KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) inc[v] = tot[v];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            df o = df_shfl_up(inc[v], d);
+            if (lane >= d) inc[v] = df_add(o, inc[v]);
+        }
+#pragma unroll
+    for (int v = 0; v < KB; v++) {
+        df o = df_shfl_up(inc[v], 1);
+        ex[v] = lane >= 1 ? o : df_zero();
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int v = 0; v < KB; v++) wtot_s[warp][v] = inc[v];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = NT / 32;
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            df t = lane < NW ? wtot_s[lane][v] : df_zero();
+#pragma unroll
+            for (int d = 1; d < NW; d <<= 1) {
+                df o = df_shfl_up(t, d);
+                if (lane >= d) t = df_add(o, t);
+            }
+            df o = df_shfl_up(t, 1);
+            if (lane < NW) wpre_s[lane][v] = lane >= 1 ? o : df_zero();
+        }
+    }
+    __syncthreads();
+
+    double S[V], R[V], Dg[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
+#pragma unroll
+    for (int q = 0; q < CPT; q++) {
+        const int64_t j = a + tid * CPT + q;
+        if (j >= a + ncols) continue;
+        Vec<V> out;
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            const df I = df_add(df_add(run_s[v], wpre_s[warp][v]), df_add(ex[v], Dinc[q][v]));
+            out.v[v] = df_val(df_add(P[q][v], I));
+        }
+        if constexpr (EPI == 0) {
+            stv<V>(y + j * ldy, out);
+        } else {
+            const float io = __ldg(pa.inv_outdeg + j);
+            const float un = 1.0f / (float)n;
+            Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq), qn, p0v;
+            if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float p0j = pa.p0 ? p0v.v[v] : un;
+                const float gj = pa.dangling_uniform ? un : p0j;
+                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + (float)pa.sc_prev[1 * KB + v] * gj);
+                qn.v[v] = qj;
+                S[v] += (double)qj;
+                R[v] += fabs((double)qj - (double)qp.v[v]);
+                if (io == 0.0f) Dg[v] += (double)qj;
+            }
+            stv<V>(pa.q_new + j * pa.ldq, qn);
+        }
     }
     if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
 }

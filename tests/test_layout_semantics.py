@@ -101,3 +101,7 @@ def test_layout_reproduces_products(name):
     off = (L["meta"] & 7).astype(np.int64)
     np.testing.assert_array_equal(np.where(ref >= 0, np.arange(g.n) - ref, 0), off)
     np.testing.assert_array_equal(L["meta"] >> 3, depth)
+    kids = np.zeros(g.n, np.int64)
+    has = ref >= 0
+    np.bitwise_or.at(kids, ref[has], 1 << (np.arange(g.n)[has] - ref[has] - 1))
+    np.testing.assert_array_equal(L["kids"], kids)
