@@ -88,27 +88,12 @@ constexpr int kThreads = 256;
 // stay large; shared memory grows with kb.
 static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
 static int chain_tile(int kb, const LaunchCfg& c) { return std::max(256, c.chain_tile / kb); }
-template <int KB, int V>
-constexpr int gather_cpt() {
-    return (KB / V) == 1 ? (KB == 1 || KB == 2 ? 4 : 2) : ((KB / V) <= 2 ? 2 : 1);
-}
-static int gather_cols_per_pass(int kb, int v) {
-    int G = kb / v, NG = kThreads / G;
-    int cpt = G == 1 ? (kb <= 2 ? 4 : 2) : (G <= 2 ? 2 : 1);
-    return NG * cpt;
-}
-// The staged gather kernel serves kb <= 4 with full-width vector access.
-static bool gather_staged(int kb, int v) { return kb <= 4 && v == kb; }
-static int gather_tile(int kb, int v, const LaunchCfg& c) {
-    if (gather_staged(kb, v)) return 1024 / kb;
-    int per = gather_cols_per_pass(kb, v);
-    int t = std::max(c.gather_tile / kb, per);
-    t = (t + kCarryTile - 1) / kCarryTile * kCarryTile;
-    return t;
+// Columns per CTA of the gather kernel (k_gather's GatherShape).
+static int gather_tile(int kb, int v, const LaunchCfg&) {
+    (void)v;
+    return std::max(128, 1024 / kb);
 }
 
-// Opts a kernel into more than 48 KB of dynamic shared memory (once per
-// kernel and size).
 template <class K>
 static void set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return;
@@ -165,12 +150,11 @@ template <int KB, int V>
 static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
                          int64_t ldz, const PrState* pst, cudaStream_t st) {
     const int tile = chain_tile(KB, g->cfg);
-    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(df) + 2 * (tile + kHalo) + 15) / 16 * 16;
+    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(float) + (tile + kHalo) + 15) / 16 * 16;
     set_smem(k_chain<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
-    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->kids, x, ldx, rowscale, z, ldz, g->n, tile,
-                                                           pst);
+    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->kids, x, ldx, rowscale, z, ldz, g->n, tile, pst);
 }
 
 template <int KB, int V>
@@ -179,13 +163,8 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
-    if constexpr (KB <= 4 && V == KB) {
-        k_gather_st<KB, 0><<<(unsigned)grid, kThreads, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry, z, y,
-                                                                 ldy, g->n, pa);
-    } else {
-        k_gather<KB, V, gather_cpt<KB, V>(), 0><<<(unsigned)grid, kThreads, 0, st>>>(
-            g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, y, ldy, g->n, tile, pa);
-    }
+    k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        z, ldz, y, ldy, g->n, pa);
 }
 
 template <int KB, int V>
@@ -193,13 +172,8 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
-    if constexpr (KB <= 4 && V == KB) {
-        k_gather_st<KB, 1><<<(unsigned)grid, kThreads, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry, z,
-                                                                 nullptr, 0, g->n, pa);
-    } else {
-        k_gather<KB, V, gather_cpt<KB, V>(), 1><<<(unsigned)grid, kThreads, 0, st>>>(
-            g->colp, g->tent, g->carry_ptr, g->carry, z, ldz, nullptr, 0, g->n, tile, pa);
-    }
+    k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        z, ldz, nullptr, 0, g->n, pa);
 }
 
 template <int KB, int V>

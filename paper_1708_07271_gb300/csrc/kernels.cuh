@@ -111,26 +111,25 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 // ---------------------------------------------------------------------------
 // Push, chain step: z_k = sum of x_i over the rows i whose reference chain
 // passes through k (Proposition 1 read for the left product: v_i is the sum
-// of the difference rows along its chain). A CTA owns rows [a, a + tile) and
-// reads kHalo rows past its end (a subtree spans at most kHalo rows). Rows
-// are visited in reverse level order: first the rows of depth R-1 add their
-// children (depth R, already final), then depth R-2, ..., then the roots.
-// kids[k] lists the children of k as bits (row k + t + 1 for bit t), so a
-// row touches only its real children; the additions of one row happen in a
-// fixed order, so z is bit-reproducible. Optionally x is scaled per row
-// first (x_i * rowscale_i, PageRank's 1/outdeg).
+// of the difference rows along its chain), i.e. x summed over the subtree of
+// k in the reference forest. A CTA owns rows [a, a + tile) and stages x for
+// kHalo rows past its end (a subtree spans at most kHalo rows). Each row then
+// walks its own subtree depth first through the child masks (kids[k] bit t =
+// row k + t + 1 references k; at most max_chain levels below any row),
+// adding in a fixed order into a compensated (hi, lo) sum, so z is
+// bit-reproducible and needs a single barrier. Optionally x is scaled per
+// row first (x_i * rowscale_i, PageRank's 1/outdeg).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
-__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta, const uint8_t* __restrict__ kids,
-                                               const float* __restrict__ x, int64_t ldx,
-                                               const float* __restrict__ rowscale, float* __restrict__ z,
-                                               int64_t ldz, int64_t n, int tile, const PrState* __restrict__ st) {
+__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ kids, const float* __restrict__ x,
+                                               int64_t ldx, const float* __restrict__ rowscale,
+                                               float* __restrict__ z, int64_t ldz, int64_t n, int tile,
+                                               const PrState* __restrict__ st) {
     if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
     constexpr int G = KB / V;
     extern __shared__ float4 smem_chain[];
-    df* zs = reinterpret_cast<df*>(smem_chain);                                   // [(tile + kHalo) * KB]
-    uint8_t* ms = reinterpret_cast<uint8_t*>(zs + (int64_t)(tile + kHalo) * KB);  // depth, [tile + kHalo]
-    uint8_t* ks = ms + tile + kHalo;                                              // children, [tile + kHalo]
+    float* xs = reinterpret_cast<float*>(smem_chain);                              // [(tile + kHalo) * KB]
+    uint8_t* ks = reinterpret_cast<uint8_t*>(xs + (int64_t)(tile + kHalo) * KB);  // [tile + kHalo]
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
@@ -138,40 +137,40 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta,
     const int cnt = (int)(hi - a);
     const int own = (int)((a + tile < n ? a + tile : n) - a);
 
-    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-        ms[r] = __ldg(meta + a + r) >> 3;
-        ks[r] = __ldg(kids + a + r);
-    }
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) ks[r] = __ldg(kids + a + r);
     for (int r = g; r < cnt; r += NG) {
         Vec<V> xv = ldv<V>(x + (a + r) * ldx + lane * V);
         const float sc = rowscale ? __ldg(rowscale + a + r) : 1.0f;
 #pragma unroll
-        for (int v = 0; v < V; v++) zs[(int64_t)r * KB + lane * V + v] = {__fmul_rn(xv.v[v], sc), 0.f};
+        for (int v = 0; v < V; v++) xs[(int64_t)r * KB + lane * V + v] = __fmul_rn(xv.v[v], sc);
     }
     __syncthreads();
-    for (int d = kMaxChain - 1; d >= 0; d--) {
-        for (int r = g; r < cnt; r += NG) {
-            unsigned km = ks[r];
-            if (km == 0 || ms[r] != d) continue;
-            df acc[V];
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = zs[(int64_t)r * KB + lane * V + v];
-            while (km) {
-                const int c = r + __ffs(km);  // bit t -> row r + t + 1
-                km &= km - 1;
-                if (c >= cnt) break;
-#pragma unroll
-                for (int v = 0; v < V; v++) acc[v] = df_add(acc[v], zs[(int64_t)c * KB + lane * V + v]);
-            }
-#pragma unroll
-            for (int v = 0; v < V; v++) zs[(int64_t)r * KB + lane * V + v] = acc[v];
-        }
-        __syncthreads();
-    }
+    static_assert(kMaxChain == 3, "the subtree walk below is written for three levels");
     for (int r = g; r < own; r += NG) {
+        df acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = {xs[(int64_t)r * KB + lane * V + v], 0.f};
+        for (unsigned m1 = ks[r]; m1; m1 &= m1 - 1) {
+            const int c1 = r + __ffs(m1);
+            if (c1 >= cnt) break;
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c1 * KB + lane * V + v]);
+            for (unsigned m2 = ks[c1]; m2; m2 &= m2 - 1) {
+                const int c2 = c1 + __ffs(m2);
+                if (c2 >= cnt) break;
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c2 * KB + lane * V + v]);
+                for (unsigned m3 = ks[c2]; m3; m3 &= m3 - 1) {
+                    const int c3 = c2 + __ffs(m3);
+                    if (c3 >= cnt) break;
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c3 * KB + lane * V + v]);
+                }
+            }
+        }
         Vec<V> out;
 #pragma unroll
-        for (int v = 0; v < V; v++) out.v[v] = df_val(zs[(int64_t)r * KB + lane * V + v]);
+        for (int v = 0; v < V; v++) out.v[v] = df_val(acc[v]);
         stv<V>(z + (a + r) * ldz + lane * V, out);
     }
 }
@@ -181,13 +180,23 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ meta,
 // atomics, deterministic): y_j = sum_k z_k A'_kj. The column-major entries of
 // column j are +z_k (residual id j of row k), -z_k (dropped id j of row k),
 // and interval events: D_j += z_k where an interval of row k starts at j,
-// D_j -= z_k where it ends before j. Intervals contribute the running prefix
-// of D. A CTA owns columns [a, a + tile), a multiple of kCarryTile, and
-// starts its running prefix from the intervals open at column a (the carry
-// list), so no grid-wide scan is needed. Each group handles CPT consecutive
-// columns per pass; the prefix across groups is a compensated block scan.
+// D_j -= z_k where it ends just before j. Intervals contribute the running
+// prefix I_j of D. A CTA owns T columns from a, a multiple of kCarryTile, and
+// starts I from the intervals open at a (the carry list), so no grid-wide
+// scan is needed. A group of G = KB/V lanes owns CPT consecutive columns: it
+// sums each column's point entries P_j and events D_j (a few terms, FP32, in
+// storage order), then the prefix of D runs in compensated (hi, lo) form:
+// within the group's columns on the fly, across groups by one block scan.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
 // ---------------------------------------------------------------------------
+template <int KB, int V>
+struct GatherShape {
+    static constexpr int NT = 128;                       // threads per CTA
+    static constexpr int G = KB / V;                     // lanes per column group
+    static constexpr int T = 1024 / KB > 128 ? 1024 / KB : 128;  // columns per CTA
+    static constexpr int CPT = T * G / NT;               // columns per group
+};
+
 template <int KB>
 struct PrPartials {
     double S[KB], R[KB], Dg[KB];
@@ -270,321 +279,137 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
     }
 }
 
-template <int KB, int V, int CPT, int EPI>
-__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+template <int KB, int V, int EPI>
+__global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                                 const uint32_t* __restrict__ carry_ptr,
                                                 const uint32_t* __restrict__ carry, const float* __restrict__ z,
                                                 int64_t ldz, float* __restrict__ y, int64_t ldy, int64_t n,
-                                                int tile, PrArgs pa) {
-    constexpr int G = KB / V;
-    if constexpr (EPI == 1) {
-        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
-    }
-    __shared__ df sh_run[KB];
-    __shared__ df sh_wtot[32][KB];
-    const int NG = blockDim.x / G;
-    const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
-    const int64_t a = (int64_t)blockIdx.x * tile;
-    const int64_t end = a + tile < n ? a + tile : n;
-
-    // running interval prefix at column a: intervals open across the tile start
-    if (threadIdx.x < G) {
-        df acc[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = df_zero();
-        const int64_t ct = a / kCarryTile;
-        for (uint32_t e = __ldg(carry_ptr + ct); e < __ldg(carry_ptr + ct + 1); e++) {
-            Vec<V> zv = ldv<V>(z + (int64_t)__ldg(carry + e) * ldz + lane * V);
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], zv.v[v]);
-        }
-#pragma unroll
-        for (int v = 0; v < V; v++) sh_run[lane * V + v] = acc[v];
-    }
-    __syncthreads();
-    df run[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) run[v] = sh_run[lane * V + v];
-
-    double S[V], R[V], Dg[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
-    double delta[V];
-    if constexpr (EPI == 1) {
-#pragma unroll
-        for (int v = 0; v < V; v++) delta[v] = pa.sc_prev[1 * KB + lane * V + v];
-    }
-
-    for (int64_t base = a; base < end; base += (int64_t)NG * CPT) {
-        const int64_t c0 = base + (int64_t)g * CPT;
-        df P[CPT][V], Dinc[CPT][V], tot[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) tot[v] = df_zero();
-#pragma unroll
-        for (int q = 0; q < CPT; q++) {
-            const int64_t j = c0 + q;
-#pragma unroll
-            for (int v = 0; v < V; v++) P[q][v] = df_zero();
-            if (j < end) {
-                const uint32_t e0 = __ldg(colp + j), e1 = __ldg(colp + j + 1);
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t word = __ldg(tent + e);
-                    const uint32_t tag = tag_of(word);
-                    Vec<V> zv = ldv<V>(z + (int64_t)id_of(word) * ldz + lane * V);
-#pragma unroll
-                    for (int v = 0; v < V; v++) {
-                        const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
-                        if (tag < 2) P[q][v] = df_addf(P[q][v], val);
-                        else tot[v] = df_addf(tot[v], val);
-                    }
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < V; v++) Dinc[q][v] = tot[v];
-        }
-        // compensated exclusive scan of the group totals across the block
-        df inc[V], ex[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) inc[v] = tot[v];
-        for (int d = G; d < 32; d <<= 1) {
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                df o = df_shfl_up(inc[v], d);
-                if (lane32 >= d) inc[v] = df_add(o, inc[v]);
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            df o = df_shfl_up(inc[v], G);
-            ex[v] = lane32 >= G ? o : df_zero();
-        }
-        if (lane32 >= 32 - G) {
-#pragma unroll
-            for (int v = 0; v < V; v++) sh_wtot[warp][lane * V + v] = inc[v];
-        }
-        __syncthreads();
-        df wpre[V], btot[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) wpre[v] = btot[v] = df_zero();
-        for (int w = 0; w < NW; w++) {
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                const df t = sh_wtot[w][lane * V + v];
-                if (w < warp) wpre[v] = df_add(wpre[v], t);
-                btot[v] = df_add(btot[v], t);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < CPT; q++) {
-            const int64_t j = c0 + q;
-            if (j >= end) continue;
-            Vec<V> out;
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                const df I = df_add(df_add(run[v], wpre[v]), df_add(ex[v], Dinc[q][v]));
-                out.v[v] = df_val(df_add(P[q][v], I));
-            }
-            if constexpr (EPI == 0) {
-                stv<V>(y + j * ldy + lane * V, out);
-            } else {
-                const float io = __ldg(pa.inv_outdeg + j);
-                const float un = 1.0f / (float)n;
-                Vec<V> qn;
-                Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq + lane * V);
-                Vec<V> p0v;
-                if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0 + lane * V);
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const float p0j = pa.p0 ? p0v.v[v] : un;
-                    const float gj = pa.dangling_uniform ? un : p0j;
-                    const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + (float)delta[v] * gj);
-                    qn.v[v] = qj;
-                    S[v] += (double)qj;
-                    R[v] += fabs((double)qj - (double)qp.v[v]);
-                    if (io == 0.0f) Dg[v] += (double)qj;
-                }
-                stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < V; v++) run[v] = df_add(run[v], btot[v]);
-    }
-    if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
-}
-
-// ---------------------------------------------------------------------------
-// Push, scatter step for KB <= 4 right-hand sides, shared-memory staged.
-// Same arithmetic as k_gather (owner computes, interval prefix from the carry
-// list), organised so that the irregular work is cheap: a CTA owns T = 1024/KB
-// columns; their column-major entries are staged in chunks of C words; the
-// z-gathers run one entry per thread (balanced, coalesced entry reads); then
-// each thread sums the staged values of its CPT consecutive columns from
-// shared memory, and one compensated block scan forms the interval prefix.
-// ---------------------------------------------------------------------------
-template <int KB, int EPI>
-__global__ void __launch_bounds__(256) k_gather_st(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
-                                                   const uint32_t* __restrict__ carry_ptr,
-                                                   const uint32_t* __restrict__ carry, const float* __restrict__ z,
-                                                   float* __restrict__ y, int64_t ldy, int64_t n, PrArgs pa) {
-    constexpr int V = KB;
-    constexpr int NT = 256;
-    constexpr int CPT = 4 / KB;   // columns per thread
-    constexpr int T = NT * CPT;   // columns per CTA (a multiple of kCarryTile)
-    constexpr int C = 4096 / KB;  // entries staged per chunk
+                                                PrArgs pa) {
+    using Sh = GatherShape<KB, V>;
+    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
     if constexpr (EPI == 1) {
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
     }
-    __shared__ uint32_t cp_s[T + 1];
-    __shared__ uint32_t ent_s[C];
-    __shared__ float val_s[C * KB];
     __shared__ df run_s[KB];
-    __shared__ df wtot_s[NT / 32][KB];
-    __shared__ df wpre_s[NT / 32][KB];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ df wtot_s[NW][KB];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t a = (int64_t)blockIdx.x * T;
-    const int ncols = (int)((a + T < n ? a + T : n) - a);
+    const int64_t end = a + T < n ? a + T : n;
+    const int64_t c0 = a + (int64_t)g * CPT;
 
-    for (int i = tid; i <= ncols; i += NT) cp_s[i] = __ldg(colp + a + i);
+    // running interval prefix at column a: sources of intervals open there
     if (warp == 0) {
-        // running interval sum at column a: sources of intervals open there
         df acc[KB];
 #pragma unroll
-        for (int v = 0; v < KB; v++) acc[v] = df_zero();
+        for (int c = 0; c < KB; c++) acc[c] = df_zero();
         const int64_t ct = a / kCarryTile;
         const uint32_t e1 = __ldg(carry_ptr + ct + 1);
-        for (uint32_t e = __ldg(carry_ptr + ct) + lane; e < e1; e += 32) {
-            Vec<V> zv = ldv<V>(z + (int64_t)__ldg(carry + e) * KB);
+        for (uint32_t e = __ldg(carry_ptr + ct) + lane32; e < e1; e += 32) {
+            const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], zv.v[v]);
+            for (int c = 0; c < KB; c++) acc[c] = df_addf(acc[c], __ldg(zr + c));
         }
 #pragma unroll
-        for (int v = 0; v < KB; v++)
-            for (int o = 16; o > 0; o >>= 1) acc[v] = df_add(acc[v], {__shfl_down_sync(0xffffffffu, acc[v].hi, o),
-                                                                        __shfl_down_sync(0xffffffffu, acc[v].lo, o)});
-        if (lane == 0) {
+        for (int c = 0; c < KB; c++)
+            for (int o = 16; o > 0; o >>= 1)
+                acc[c] = df_add(acc[c], {__shfl_down_sync(0xffffffffu, acc[c].hi, o),
+                                         __shfl_down_sync(0xffffffffu, acc[c].lo, o)});
+        if (lane32 == 0) {
 #pragma unroll
-            for (int v = 0; v < KB; v++) run_s[v] = acc[v];
+            for (int c = 0; c < KB; c++) run_s[c] = acc[c];
         }
     }
-    __syncthreads();
 
-    df P[CPT][KB], D[CPT][KB];
+    // per-column point sums and interval events, FP32 in storage order
+    float P[CPT][V], D[CPT][V];
+    df tot[V];
 #pragma unroll
-    for (int q = 0; q < CPT; q++)
+    for (int v = 0; v < V; v++) tot[v] = df_zero();
 #pragma unroll
-        for (int v = 0; v < KB; v++) P[q][v] = D[q][v] = df_zero();
-    const uint32_t ebase = cp_s[0], eend = cp_s[ncols];
-    for (uint32_t c0 = ebase; c0 < eend; c0 += C) {
-        const int cnt = (int)(eend - c0 < (uint32_t)C ? eend - c0 : (uint32_t)C);
-        for (int e = tid; e < cnt; e += NT) {
-            const uint32_t w = __ldg(tent + c0 + e);
-            ent_s[e] = w;
-            Vec<V> zv = ldv<V>(z + (int64_t)id_of(w) * KB);
-            const bool neg = (w >> kIdBits) & 1;
+    for (int q = 0; q < CPT; q++) {
 #pragma unroll
-            for (int v = 0; v < KB; v++) val_s[e * KB + v] = neg ? -zv.v[v] : zv.v[v];
-        }
-        __syncthreads();
+        for (int v = 0; v < V; v++) P[q][v] = D[q][v] = 0.f;
+        const int64_t j = c0 + q;
+        if (j < end) {
+            const uint32_t e1 = __ldg(colp + j + 1);
+            for (uint32_t e = __ldg(colp + j); e < e1; e++) {
+                const uint32_t w = __ldg(tent + e);
+                Vec<V> zv = ldv<V>(z + (int64_t)id_of(w) * ldz + lane * V);
+                const uint32_t tag = w >> kIdBits;
 #pragma unroll
-        for (int q = 0; q < CPT; q++) {
-            const int jl = tid * CPT + q;
-            if (jl >= ncols) continue;
-            const uint32_t lo = cp_s[jl] > c0 ? cp_s[jl] : c0;
-            const uint32_t hi = cp_s[jl + 1] < c0 + cnt ? cp_s[jl + 1] : c0 + cnt;
-            for (uint32_t e = lo; e < hi; e++) {
-                const int el = (int)(e - c0);
-                const bool point = (ent_s[el] >> kIdBits) < 2;
-#pragma unroll
-                for (int v = 0; v < KB; v++) {
-                    const float val = val_s[el * KB + v];
-                    if (point) P[q][v] = df_addf(P[q][v], val);
-                    else D[q][v] = df_addf(D[q][v], val);
+                for (int v = 0; v < V; v++) {
+                    const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
+                    if (tag < 2) P[q][v] += val;
+                    else D[q][v] += val;
                 }
             }
         }
-        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < V; v++) tot[v] = df_addf(tot[v], D[q][v]);
     }
-    // interval prefix: thread-local over CPT columns, then across threads
-    df tot[KB], Dinc[CPT][KB];
+    // exclusive prefix of the group totals across the block (compensated)
+    df inc[V], ex[V];
 #pragma unroll
-    for (int v = 0; v < KB; v++) tot[v] = df_zero();
+    for (int v = 0; v < V; v++) inc[v] = tot[v];
 #pragma unroll
-    for (int q = 0; q < CPT; q++)
+    for (int d = G; d < 32; d <<= 1)
 #pragma unroll
-        for (int v = 0; v < KB; v++) {
-            tot[v] = df_add(tot[v], D[q][v]);
-            Dinc[q][v] = tot[v];
-        }
-    df inc[KB], ex[KB];
-#pragma unroll
-    for (int v = 0; v < KB; v++) inc[v] = tot[v];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1)
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
+        for (int v = 0; v < V; v++) {
             df o = df_shfl_up(inc[v], d);
-            if (lane >= d) inc[v] = df_add(o, inc[v]);
+            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
         }
 #pragma unroll
-    for (int v = 0; v < KB; v++) {
-        df o = df_shfl_up(inc[v], 1);
-        ex[v] = lane >= 1 ? o : df_zero();
+    for (int v = 0; v < V; v++) {
+        df o = df_shfl_up(inc[v], G);
+        ex[v] = lane32 >= G ? o : df_zero();
     }
-    if (lane == 31) {
+    if (lane32 >= 32 - G) {
 #pragma unroll
-        for (int v = 0; v < KB; v++) wtot_s[warp][v] = inc[v];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int NW = NT / 32;
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
-            df t = lane < NW ? wtot_s[lane][v] : df_zero();
-#pragma unroll
-            for (int d = 1; d < NW; d <<= 1) {
-                df o = df_shfl_up(t, d);
-                if (lane >= d) t = df_add(o, t);
-            }
-            df o = df_shfl_up(t, 1);
-            if (lane < NW) wpre_s[lane][v] = lane >= 1 ? o : df_zero();
-        }
+        for (int v = 0; v < V; v++) wtot_s[warp][lane * V + v] = inc[v];
     }
     __syncthreads();
+    df run[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        df r = run_s[lane * V + v];
+        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w][lane * V + v]);
+        run[v] = df_add(r, ex[v]);
+    }
 
     double S[V], R[V], Dg[V];
 #pragma unroll
     for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
-        const int64_t j = a + tid * CPT + q;
-        if (j >= a + ncols) continue;
+        const int64_t j = c0 + q;
         Vec<V> out;
 #pragma unroll
-        for (int v = 0; v < KB; v++) {
-            const df I = df_add(df_add(run_s[v], wpre_s[warp][v]), df_add(ex[v], Dinc[q][v]));
-            out.v[v] = df_val(df_add(P[q][v], I));
+        for (int v = 0; v < V; v++) {
+            run[v] = df_addf(run[v], D[q][v]);
+            out.v[v] = df_val(df_addf(run[v], P[q][v]));
         }
+        if (j >= end) continue;
         if constexpr (EPI == 0) {
-            stv<V>(y + j * ldy, out);
+            stv<V>(y + j * ldy + lane * V, out);
         } else {
             const float io = __ldg(pa.inv_outdeg + j);
             const float un = 1.0f / (float)n;
-            Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq), qn, p0v;
-            if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0);
+            Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq + lane * V), qn, p0v;
+            if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0 + lane * V);
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float p0j = pa.p0 ? p0v.v[v] : un;
                 const float gj = pa.dangling_uniform ? un : p0j;
-                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + (float)pa.sc_prev[1 * KB + v] * gj);
+                const float dl = (float)pa.sc_prev[1 * KB + lane * V + v];
+                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
                 qn.v[v] = qj;
                 S[v] += (double)qj;
                 R[v] += fabs((double)qj - (double)qp.v[v]);
                 if (io == 0.0f) Dg[v] += (double)qj;
             }
-            stv<V>(pa.q_new + j * pa.ldq, qn);
+            stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
         }
     }
     if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
