@@ -184,9 +184,11 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ kids,
 // prefix I_j of D. A CTA owns T columns from a, a multiple of kCarryTile, and
 // starts I from the intervals open at a (the carry list), so no grid-wide
 // scan is needed. A group of G = KB/V lanes owns CPT consecutive columns: it
-// sums each column's point entries P_j and events D_j (a few terms, FP32, in
-// storage order), then the prefix of D runs in compensated (hi, lo) form:
-// within the group's columns on the fly, across groups by one block scan.
+// sums each column's point entries P_j in FP32 (a few terms in storage order;
+// an error there stays in y_j) and its events D_j in compensated (hi, lo)
+// form, since the prefix of D carries any error to every later column; the
+// prefix runs compensated within the group's columns on the fly and across
+// groups by one block scan.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
@@ -322,15 +324,19 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
         }
     }
 
-    // per-column point sums and interval events, FP32 in storage order
-    float P[CPT][V], D[CPT][V];
+    // per-column point sums (FP32) and interval events (compensated)
+    float P[CPT][V];
+    df D[CPT][V];
     df tot[V];
 #pragma unroll
     for (int v = 0; v < V; v++) tot[v] = df_zero();
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
 #pragma unroll
-        for (int v = 0; v < V; v++) P[q][v] = D[q][v] = 0.f;
+        for (int v = 0; v < V; v++) {
+            P[q][v] = 0.f;
+            D[q][v] = df_zero();
+        }
         const int64_t j = c0 + q;
         if (j < end) {
             const uint32_t e1 = __ldg(colp + j + 1);
@@ -338,16 +344,17 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
                 const uint32_t w = __ldg(tent + e);
                 Vec<V> zv = ldv<V>(z + (int64_t)id_of(w) * ldz + lane * V);
                 const uint32_t tag = w >> kIdBits;
+                if (tag < 2) {
 #pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
-                    if (tag < 2) P[q][v] += val;
-                    else D[q][v] += val;
+                    for (int v = 0; v < V; v++) P[q][v] += (tag & 1) ? -zv.v[v] : zv.v[v];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; v++) D[q][v] = df_addf(D[q][v], (tag & 1) ? -zv.v[v] : zv.v[v]);
                 }
             }
         }
 #pragma unroll
-        for (int v = 0; v < V; v++) tot[v] = df_addf(tot[v], D[q][v]);
+        for (int v = 0; v < V; v++) tot[v] = df_add(tot[v], D[q][v]);
     }
     // exclusive prefix of the group totals across the block (compensated)
     df inc[V], ex[V];
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] = df_addf(run[v], D[q][v]);
+            run[v] = df_add(run[v], D[q][v]);
             out.v[v] = df_val(df_addf(run[v], P[q][v]));
         }
         if (j >= end) continue;
