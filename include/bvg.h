@@ -130,7 +130,7 @@ int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
 typedef struct {
     int64_t n, words, col_entries, carry_tiles, carry_entries, carry_tile_cols;
     const uint8_t* meta;
-    const uint8_t* kids; /* bit t: row i + t + 1 takes row i as its reference */
+    const uint32_t* desc; /* bit t: row i + t + 1 descends from row i (its chain passes through i) */
     const uint32_t* rowp;
     const uint32_t* ent;
     const uint32_t* colp;

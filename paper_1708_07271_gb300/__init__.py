@@ -68,7 +68,7 @@ class LayoutInfo(ctypes.Structure):
 class LayoutView(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "words", "col_entries", "carry_tiles", "carry_entries",
                                       "carry_tile_cols")] + \
-               [(f, _P) for f in ("meta", "kids", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")]
+               [(f, _P) for f in ("meta", "desc", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")]
 
 
 class TraceEntry(ctypes.Structure):
@@ -351,7 +351,7 @@ def bvg_layout_view_get(hg: HostGraph) -> dict:
     return {
         "n": n, "carry_tile_cols": v.carry_tile_cols,
         "meta": arr(v.meta, n, ctypes.c_uint8, np.uint8),
-        "kids": arr(v.kids, n, ctypes.c_uint8, np.uint8),
+        "desc": arr(v.desc, n, ctypes.c_uint32, np.uint32),
         "rowp": arr(v.rowp, n + 1, ctypes.c_uint32, np.uint32),
         "ent": arr(v.ent, v.words, ctypes.c_uint32, np.uint32),
         "colp": arr(v.colp, n + 1, ctypes.c_uint32, np.uint32),

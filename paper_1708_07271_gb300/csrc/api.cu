@@ -146,15 +146,20 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
     k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile);
 }
 
+// The flat fixed-point gather serves kb <= 4 with full-width vector access;
+// its chain step also reduces max|z|.
+static bool flat_gather(int kb, int v) { return kb <= 4 && v == kb; }
+
 template <int KB, int V>
 static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
                          int64_t ldz, const PrState* pst, cudaStream_t st) {
+    unsigned int* zmax = flat_gather(KB, V) ? g->s.zmax : nullptr;
     const int tile = chain_tile(KB, g->cfg);
-    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(float) + (tile + kHalo) + 15) / 16 * 16;
+    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(float) + 15) / 16 * 16;
     set_smem(k_chain<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
-    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->kids, x, ldx, rowscale, z, ldz, g->n, tile, pst);
+    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, tile, pst, zmax);
 }
 
 template <int KB, int V>
@@ -163,8 +168,13 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
-    k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        z, ldz, y, ldy, g->n, pa);
+    if constexpr (KB <= 4 && V == KB) {
+        k_gather_flat<KB, 0><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(
+            g->colp, g->tent, g->carry_ptr, g->carry, z, y, ldy, g->n, g->s.zmax, g->s.counter, pa);
+    } else {
+        k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr,
+                                                                            g->carry, z, ldz, y, ldy, g->n, pa);
+    }
 }
 
 template <int KB, int V>
@@ -172,8 +182,13 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
-    k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        z, ldz, nullptr, 0, g->n, pa);
+    if constexpr (KB <= 4 && V == KB) {
+        k_gather_flat<KB, 1><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(
+            g->colp, g->tent, g->carry_ptr, g->carry, z, nullptr, 0, g->n, g->s.zmax, g->s.counter, pa);
+    } else {
+        k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr,
+                                                                            g->carry, z, ldz, nullptr, 0, g->n, pa);
+    }
 }
 
 template <int KB, int V>
@@ -248,9 +263,6 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
             rc = dev_alloc((void**)&g->s.sc[p], 3 * 32 * sizeof(double), nullptr);
             if (rc) return rc;
         }
-        rc = dev_alloc((void**)&g->s.counter, sizeof(unsigned int), nullptr);
-        if (rc) return rc;
-        BVG_CUDA_TRY(cudaMemset(g->s.counter, 0, sizeof(unsigned int)));
         int64_t cap = max_grid(g) * 3 * 32;
         rc = dev_alloc((void**)&g->s.partial, (size_t)cap * sizeof(double), nullptr);
         if (rc) return rc;
@@ -291,7 +303,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->nwords = (int64_t)L->ent.size();
         g->ntent = (int64_t)L->tent.size();
         g->ncarry = (int64_t)L->carry.size();
-        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->kids, L->kids, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
+        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
             (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
             (rc = upload_vec(&g->carry_ptr, L->carry_ptr, st, &g->bytes)) ||
@@ -300,10 +312,12 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
-        if ((rc = ensure_z(g, 1))) {
+        if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, 2 * sizeof(unsigned int), nullptr))) {
             bvg_free_dev(g);
             return rc;
         }
+        g->s.zmax = g->s.counter + 1;
+        BVG_CUDA_TRY(cudaMemsetAsync(g->s.counter, 0, 2 * sizeof(unsigned int), st));
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             bvg_free_dev(g);
@@ -319,7 +333,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
 
 extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
-    void* ptrs[] = {g->meta, g->kids, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
+    void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0};
     drop_pr_graph(g);

@@ -42,7 +42,8 @@ int fail(int status, const char* fmt, ...);
 
 // Host copy of the device layout (built once per host graph, see layout.cpp).
 struct HostLayout {
-    std::vector<uint8_t> meta, kids;
+    std::vector<uint8_t> meta;
+    std::vector<uint32_t> desc;
     std::vector<uint32_t> rowp, ent, colp, tent, carry_ptr, carry;
     std::vector<float> inv_outdeg;
     bool built = false;
@@ -89,7 +90,8 @@ struct DevScratch {
     double* sc[2] = {nullptr, nullptr}; // PageRank scalars per parity: [3][32] (1/S, dangling, resid)
     void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
     double* partial = nullptr;          // per-CTA FP64 partial sums
-    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction)
+    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction); allocated with zmax
+    unsigned int* zmax = nullptr;       // max |z| as float bits (fixed-point gather scale), = counter + 1
     void* host_state = nullptr;         // pinned host copy of the state + residuals
     float* hx = nullptr;                // device staging for the host-buffer product
     float* hy = nullptr;
@@ -117,7 +119,7 @@ struct bvg_dev_graph {
     int device = 0;
     // row-major difference rows (A x^T)
     uint8_t* meta = nullptr;   // n: bits 0-2 reference offset (0 = none), bits 3-4 depth
-    uint8_t* kids = nullptr;   // n: bit t set iff row i + t + 1 references row i
+    uint32_t* desc = nullptr;  // n: bit t set iff row i + t + 1 descends from row i
     uint32_t* rowp = nullptr;  // n+1 word offsets
     uint32_t* ent = nullptr;   // words
     int64_t nwords = 0;

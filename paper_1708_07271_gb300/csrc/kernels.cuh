@@ -112,24 +112,25 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 // Push, chain step: z_k = sum of x_i over the rows i whose reference chain
 // passes through k (Proposition 1 read for the left product: v_i is the sum
 // of the difference rows along its chain), i.e. x summed over the subtree of
-// k in the reference forest. A CTA owns rows [a, a + tile) and stages x for
-// kHalo rows past its end (a subtree spans at most kHalo rows). Each row then
-// walks its own subtree depth first through the child masks (kids[k] bit t =
-// row k + t + 1 references k; at most max_chain levels below any row),
-// adding in a fixed order into a compensated (hi, lo) sum, so z is
-// bit-reproducible and needs a single barrier. Optionally x is scaled per
-// row first (x_i * rowscale_i, PageRank's 1/outdeg).
+// k in the reference forest. desc[k] bit t marks row k + t + 1 as a
+// descendant (a chain spans at most kHalo rows), so a CTA that owns rows
+// [a, a + tile) stages x for kHalo rows past its end and each row adds its
+// descendants in increasing row order into a compensated (hi, lo) sum:
+// bit-reproducible, one barrier. Optionally x is scaled per row first
+// (x_i * rowscale_i, PageRank's 1/outdeg). If zmax != NULL the largest |z|
+// (as float bits, monotone for non-negative floats; NaN ranks above all) is
+// merged into *zmax for the fixed-point gather.
 // ---------------------------------------------------------------------------
 template <int KB, int V>
-__global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ kids, const float* __restrict__ x,
+__global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc, const float* __restrict__ x,
                                                int64_t ldx, const float* __restrict__ rowscale,
                                                float* __restrict__ z, int64_t ldz, int64_t n, int tile,
-                                               const PrState* __restrict__ st) {
+                                               const PrState* __restrict__ st, unsigned int* __restrict__ zmax) {
     if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
     constexpr int G = KB / V;
     extern __shared__ float4 smem_chain[];
-    float* xs = reinterpret_cast<float*>(smem_chain);                              // [(tile + kHalo) * KB]
-    uint8_t* ks = reinterpret_cast<uint8_t*>(xs + (int64_t)(tile + kHalo) * KB);  // [tile + kHalo]
+    float* xs = reinterpret_cast<float*>(smem_chain);  // [(tile + kHalo) * KB]
+    __shared__ unsigned int wmax[32];
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
@@ -137,7 +138,6 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ kids,
     const int cnt = (int)(hi - a);
     const int own = (int)((a + tile < n ? a + tile : n) - a);
 
-    for (int r = threadIdx.x; r < cnt; r += blockDim.x) ks[r] = __ldg(kids + a + r);
     for (int r = g; r < cnt; r += NG) {
         Vec<V> xv = ldv<V>(x + (a + r) * ldx + lane * V);
         const float sc = rowscale ? __ldg(rowscale + a + r) : 1.0f;
@@ -145,33 +145,33 @@ __global__ void __launch_bounds__(256) k_chain(const uint8_t* __restrict__ kids,
         for (int v = 0; v < V; v++) xs[(int64_t)r * KB + lane * V + v] = __fmul_rn(xv.v[v], sc);
     }
     __syncthreads();
-    static_assert(kMaxChain == 3, "the subtree walk below is written for three levels");
+    unsigned int mx = 0;
     for (int r = g; r < own; r += NG) {
         df acc[V];
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = {xs[(int64_t)r * KB + lane * V + v], 0.f};
-        for (unsigned m1 = ks[r]; m1; m1 &= m1 - 1) {
-            const int c1 = r + __ffs(m1);
-            if (c1 >= cnt) break;
+        for (uint32_t m = __ldg(desc + a + r); m; m &= m - 1) {
+            const int c = r + __ffs(m);  // bit t -> row r + t + 1
+            if (c >= cnt) break;
 #pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c1 * KB + lane * V + v]);
-            for (unsigned m2 = ks[c1]; m2; m2 &= m2 - 1) {
-                const int c2 = c1 + __ffs(m2);
-                if (c2 >= cnt) break;
-#pragma unroll
-                for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c2 * KB + lane * V + v]);
-                for (unsigned m3 = ks[c2]; m3; m3 &= m3 - 1) {
-                    const int c3 = c2 + __ffs(m3);
-                    if (c3 >= cnt) break;
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c3 * KB + lane * V + v]);
-                }
-            }
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c * KB + lane * V + v]);
         }
         Vec<V> out;
 #pragma unroll
-        for (int v = 0; v < V; v++) out.v[v] = df_val(acc[v]);
+        for (int v = 0; v < V; v++) {
+            out.v[v] = df_val(acc[v]);
+            mx = max(mx, __float_as_uint(out.v[v]) & 0x7fffffffu);
+        }
         stv<V>(z + (a + r) * ldz + lane * V, out);
+    }
+    if (zmax) {
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = max(mx, wmax[w]);
+            if (mx) atomicMax(zmax, mx);
+        }
     }
 }
 
@@ -208,7 +208,8 @@ struct PrPartials {
 // then the last CTA to finish reduces all CTAs in a fixed order and writes
 // the scalars of this update (deterministic; no spin-waits).
 template <int KB, int V>
-__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init) {
+__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init,
+                                unsigned int* zmax = nullptr) {
     constexpr int G = KB / V;
     __shared__ double sh_part[32][3][KB];
     __shared__ bool sh_last;
@@ -276,6 +277,7 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
             if (bad) pa.st->numeric = 1;
             if (conv || bad) pa.st->done = 1;
         }
+        if (zmax) *zmax = 0u;
         *pa.counter = 0u;
         __threadfence();
     }
@@ -420,6 +422,272 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
         }
     }
     if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
+}
+
+// ---------------------------------------------------------------------------
+// Push, scatter step for KB <= 4 right-hand sides: flat, entry-parallel,
+// exact. Same result as k_gather (y_j = sum_k z_k A'_kj, intervals by the
+// running prefix of their start/end events, carry list at the tile start),
+// computed as follows. Every value +-z_k is turned into a 64-bit fixed-point
+// integer with a power-of-two scale 2^s per CTA, chosen from max|z| and the
+// number of terms of the tile so that no partial sum can overflow; integer
+// sums are exact and associative, so all prefix sums below are exact and the
+// result does not depend on the order of additions. The tile's column-major
+// entries are processed EPT consecutive entries per thread (balanced and
+// coalesced); two exclusive prefix sums over this flat stream -- C of all
+// values and Bp of the point values (+-z of residual/dropped ids) -- are
+// recorded at every column boundary b_j = colp[j]. Then
+//   y_j = carry + C(b_{j+1}) - Bp(b_j)
+// (the events of columns <= j, plus the point values of column j), converted
+// back to FP32 with a single rounding.
+// ---------------------------------------------------------------------------
+template <int KB>
+struct FlatShape {
+    static constexpr int NT = 256;
+    static constexpr int EPT = 16 / KB;     // entries per thread and chunk
+    static constexpr int CE = NT * EPT;     // entries per chunk
+    static constexpr int T = 1024 / KB;     // columns per CTA
+    static constexpr int CPT = T / NT;      // columns per thread in the output phase
+};
+
+// Scale exponent s with maxabs * terms * 2^s <= 2^62 (maxabs given as float
+// bits); integer exponent arithmetic only.
+__device__ __forceinline__ int fx_exponent(unsigned int maxbits, long long terms) {
+    if (maxbits == 0) return 0;
+    const int e_m = (int)((maxbits >> 23) & 0xff) - 126;  // maxabs < 2^e_m
+    const int e_t = 64 - __clzll((unsigned long long)terms);  // terms < 2^e_t
+    int sexp = 62 - e_m - e_t;
+    return sexp > 100 ? 100 : (sexp < -100 ? -100 : sexp);
+}
+
+__device__ __forceinline__ float pow2f(int e) {  // 2^e for |e| <= 126
+    return __int_as_float((e + 127) << 23);
+}
+
+__device__ __forceinline__ long long to_fx(float v, int sexp) {
+    // v * 2^s is exact (a power-of-two scaling in range); one rounding to integer
+    const float s1 = pow2f(sexp / 2), s2 = pow2f(sexp - sexp / 2);
+    return __float2ll_rn(__fmul_rn(__fmul_rn(v, s1), s2));
+}
+
+__device__ __forceinline__ float from_fx(long long v, int sexp) {
+    const float s1 = pow2f(-(sexp / 2)), s2 = pow2f(-(sexp - sexp / 2));
+    return __fmul_rn(__fmul_rn(__ll2float_rn(v), s1), s2);
+}
+
+template <int KB, int EPI>
+__global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict__ colp,
+                                                     const uint32_t* __restrict__ tent,
+                                                     const uint32_t* __restrict__ carry_ptr,
+                                                     const uint32_t* __restrict__ carry,
+                                                     const float* __restrict__ z, float* __restrict__ y,
+                                                     int64_t ldy, int64_t n, unsigned int* __restrict__ zmax,
+                                                     unsigned int* __restrict__ counter, PrArgs pa) {
+    using Sh = FlatShape<KB>;
+    constexpr int NT = Sh::NT, EPT = Sh::EPT, CE = Sh::CE, T = Sh::T, CPT = Sh::CPT, NW = NT / 32;
+    static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
+    if constexpr (EPI == 1) {
+        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+    }
+    __shared__ uint32_t cp_s[T + 1];
+    __shared__ uint32_t ent_s[CE + NT];     // skewed: entry e at e + e / EPT
+    __shared__ long long cb_s[T + 1][KB];   // C at each column boundary
+    __shared__ long long bb_s[T + 1][KB];   // Bp at each column boundary
+    __shared__ long long run0_s[KB];
+    __shared__ long long wtot_s[NW][2][KB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t a = (int64_t)blockIdx.x * T;
+    const int ncols = (int)((a + T < n ? a + T : n) - a);
+    const int64_t ct = a / kCarryTile;
+
+    for (int i = tid; i <= ncols; i += NT) {
+        cp_s[i] = __ldg(colp + a + i);
+#pragma unroll
+        for (int v = 0; v < KB; v++) cb_s[i][v] = bb_s[i][v] = 0;
+    }
+    const unsigned int mbits = __ldcg(zmax);
+    const bool bad = mbits >= 0x7f800000u;  // a non-finite z: the product is not defined
+    const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
+    __syncthreads();
+    const uint32_t ebase = cp_s[0];
+    const int64_t E = (int64_t)cp_s[ncols] - ebase;
+    const int sexp = fx_exponent(mbits, E + (cr1 - cr0) + 1);
+
+    if (warp == 0) {  // running interval prefix at column a (exact, any order)
+        long long acc[KB];
+#pragma unroll
+        for (int v = 0; v < KB; v++) acc[v] = 0;
+        for (uint32_t e = cr0 + lane; e < cr1; e += 32) {
+            Vec<KB> zv = ldv<KB>(z + (int64_t)__ldg(carry + e) * KB);
+#pragma unroll
+            for (int v = 0; v < KB; v++) acc[v] += to_fx(zv.v[v], sexp);
+        }
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+            if (lane == 0) run0_s[v] = acc[v];
+        }
+    }
+
+    long long chC[KB], chB[KB];  // prefix of the chunks before this one
+#pragma unroll
+    for (int v = 0; v < KB; v++) chC[v] = chB[v] = 0;
+    for (int64_t cs = 0; cs < E; cs += CE) {
+        const int ce = (int)(E - cs < CE ? E - cs : CE);
+        for (int e = tid; e < ce; e += NT) ent_s[e + e / EPT] = __ldg(tent + ebase + cs + e);
+        __syncthreads();
+        const int lo = tid * EPT;
+        const int cnt = ce - lo < 0 ? 0 : (ce - lo > EPT ? EPT : ce - lo);
+        long long val[EPT][KB], tC[KB], tB[KB];
+        unsigned int pmask = 0;
+#pragma unroll
+        for (int v = 0; v < KB; v++) tC[v] = tB[v] = 0;
+#pragma unroll
+        for (int i = 0; i < EPT; i++) {
+#pragma unroll
+            for (int v = 0; v < KB; v++) val[i][v] = 0;
+            if (i < cnt) {
+                const uint32_t w = ent_s[lo + i + tid];
+                const uint32_t tag = w >> kIdBits;
+                Vec<KB> zv = ldv<KB>(z + (int64_t)id_of(w) * KB);
+#pragma unroll
+                for (int v = 0; v < KB; v++) {
+                    const long long f = to_fx(zv.v[v], sexp);
+                    val[i][v] = (tag & 1) ? -f : f;
+                    tC[v] += val[i][v];
+                    if (tag < 2) tB[v] += val[i][v];
+                }
+                if (tag < 2) pmask |= 1u << i;
+            }
+        }
+        // exclusive block scan of the thread totals (exact)
+        long long xC[KB], xB[KB], bC[KB], bB[KB];
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            long long ic = tC[v], ib = tB[v];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long oc = __shfl_up_sync(0xffffffffu, ic, d), ob = __shfl_up_sync(0xffffffffu, ib, d);
+                if (lane >= d) {
+                    ic += oc;
+                    ib += ob;
+                }
+            }
+            if (lane == 31) {
+                wtot_s[warp][0][v] = ic;
+                wtot_s[warp][1][v] = ib;
+            }
+            xC[v] = ic - tC[v];
+            xB[v] = ib - tB[v];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            bC[v] = bB[v] = 0;
+            for (int w2 = 0; w2 < NW; w2++) {
+                if (w2 < warp) {
+                    xC[v] += wtot_s[w2][0][v];
+                    xB[v] += wtot_s[w2][1][v];
+                }
+                bC[v] += wtot_s[w2][0][v];
+                bB[v] += wtot_s[w2][1][v];
+            }
+        }
+        // record the prefixes at the column boundaries inside (lo, lo + cnt]
+        if (cnt > 0) {
+            const uint32_t first = ebase + (uint32_t)(cs + lo);  // boundaries b with b > first
+            int j0 = 0, j1 = ncols + 1;
+            while (j0 < j1) {  // first j with cp_s[j] > first
+                const int mid = (j0 + j1) >> 1;
+                if (cp_s[mid] > first) j1 = mid;
+                else j0 = mid + 1;
+            }
+            int j = j0;
+            long long rc[KB], rb[KB];
+#pragma unroll
+            for (int v = 0; v < KB; v++) {
+                rc[v] = chC[v] + xC[v];
+                rb[v] = chB[v] + xB[v];
+            }
+#pragma unroll
+            for (int i = 0; i < EPT; i++) {
+                if (i < cnt) {
+#pragma unroll
+                    for (int v = 0; v < KB; v++) {
+                        rc[v] += val[i][v];
+                        if (pmask >> i & 1) rb[v] += val[i][v];
+                    }
+                    const uint32_t pos = first + (uint32_t)(i + 1);
+                    while (j <= ncols && cp_s[j] == pos) {
+#pragma unroll
+                        for (int v = 0; v < KB; v++) {
+                            cb_s[j][v] = rc[v];
+                            bb_s[j][v] = rb[v];
+                        }
+                        j++;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            chC[v] += bC[v];
+            chB[v] += bB[v];
+        }
+        __syncthreads();
+    }
+
+    double S[KB], R[KB], Dg[KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) S[v] = R[v] = Dg[v] = 0.0;
+#pragma unroll
+    for (int q = 0; q < CPT; q++) {
+        const int jl = q * NT + tid;  // consecutive threads, consecutive columns
+        if (jl >= ncols) continue;
+        const int64_t j = a + jl;
+        Vec<KB> out;
+#pragma unroll
+        for (int v = 0; v < KB; v++) {
+            const long long t = run0_s[v] + cb_s[jl + 1][v] - bb_s[jl][v];
+            out.v[v] = bad ? __int_as_float(0x7fc00000) : from_fx(t, sexp);
+        }
+        if constexpr (EPI == 0) {
+            stv<KB>(y + j * ldy, out);
+        } else {
+            const float io = __ldg(pa.inv_outdeg + j);
+            const float un = 1.0f / (float)n;
+            Vec<KB> qp = ldv<KB>(pa.q_prev + j * pa.ldq), qn, p0v;
+            if (pa.p0) p0v = ldv<KB>(pa.p0 + j * pa.ldp0);
+#pragma unroll
+            for (int v = 0; v < KB; v++) {
+                const float p0j = pa.p0 ? p0v.v[v] : un;
+                const float gj = pa.dangling_uniform ? un : p0j;
+                const float dl = (float)pa.sc_prev[1 * KB + v];
+                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
+                qn.v[v] = qj;
+                S[v] += (double)qj;
+                R[v] += fabs((double)qj - (double)qp.v[v]);
+                if (io == 0.0f) Dg[v] += (double)qj;
+            }
+            stv<KB>(pa.q_new + j * pa.ldq, qn);
+        }
+    }
+    if constexpr (EPI == 1) {
+        pr_block_reduce<KB, KB>(S, R, Dg, pa, false, zmax);
+    } else {
+        // the last CTA to finish clears zmax for the next product
+        __shared__ bool last;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            last = atomicAdd(counter, 1u) == gridDim.x - 1;
+            if (last) {
+                *zmax = 0u;
+                *counter = 0u;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the

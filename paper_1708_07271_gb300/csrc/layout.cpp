@@ -1,7 +1,8 @@
 // Host construction of the device layout of a BV-delta encoding.
 //
-// kids[k]: bit t set iff row k + t + 1 takes row k as its reference (the
-// children of k in the reference forest, at most kMaxWindow of them).
+// desc[k]: bit t set iff row k + t + 1 is a descendant of row k in the
+// reference forest (its chain passes through k); a chain spans at most kHalo
+// rows, so kHalo bits suffice.
 // Row-major difference rows (for A x^T): per row, 32-bit words tagged
 // (two high bits) as dropped id, residual id, interval start + length word.
 // Column-major entries (for x A): per column j, the source rows k whose
@@ -25,7 +26,7 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
     if (words >= ((int64_t)1 << 32)) return fail(BVG_ERR_UNSUPPORTED, "layout: more than 2^32 words");
     try {
         L.meta.assign(n, 0);
-        L.kids.assign(n, 0);
+        L.desc.assign(n, 0);
         L.rowp.assign(n + 1, 0);
         L.ent.assign((size_t)words, 0);
         L.inv_outdeg.assign(n, 0.f);
@@ -34,7 +35,10 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
         for (int64_t i = 0; i < n; i++) {
             const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
             L.meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
-            if (off) L.kids[i - off] |= (uint8_t)(1u << (off - 1));
+            // every ancestor r of i on its chain (at most kHalo rows back) gets
+            // bit i - r - 1 of its descendant mask
+            for (int64_t r = hg->ref[i], hop = 0; r >= 0 && hop < kMaxChain; r = hg->ref[r], hop++)
+                L.desc[r] |= 1u << (i - r - 1);
             L.inv_outdeg[i] = hg->outdeg[i] ? 1.0f / (float)hg->outdeg[i] : 0.0f;
             for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) L.ent[w++] = pack(kTagMinus, hg->drop[t]);
             for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) L.ent[w++] = pack(kTagPlus, hg->res[t]);
@@ -125,7 +129,7 @@ extern "C" int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out
     out->carry_entries = (int64_t)L->carry.size();
     out->carry_tile_cols = kCarryTile;
     out->meta = L->meta.data();
-    out->kids = L->kids.data();
+    out->desc = L->desc.data();
     out->rowp = L->rowp.data();
     out->ent = L->ent.data();
     out->colp = L->colp.data();

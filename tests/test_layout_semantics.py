@@ -24,6 +24,13 @@ def emulate_xA(L, x, tile):
     for d in range(3, 0, -1):
         rows = np.nonzero((depth == d) & (off > 0))[0]
         np.add.at(z, rows - off[rows], z[rows])
+    # the same weights from the descendant masks (what the chain kernel reads)
+    zd = x.astype(np.float64).copy()
+    desc = L["desc"].astype(np.int64)
+    for t in range(21):
+        rows = np.nonzero((desc >> t) & 1)[0]
+        zd[rows] += x[rows + t + 1]
+    np.testing.assert_allclose(zd, z, rtol=1e-12)
     tent = L["tent"].astype(np.int64)
     tag = tent >> TAG_SHIFT
     src = tent & MASK
@@ -101,7 +108,10 @@ def test_layout_reproduces_products(name):
     off = (L["meta"] & 7).astype(np.int64)
     np.testing.assert_array_equal(np.where(ref >= 0, np.arange(g.n) - ref, 0), off)
     np.testing.assert_array_equal(L["meta"] >> 3, depth)
-    kids = np.zeros(g.n, np.int64)
-    has = ref >= 0
-    np.bitwise_or.at(kids, ref[has], 1 << (np.arange(g.n)[has] - ref[has] - 1))
-    np.testing.assert_array_equal(L["kids"], kids)
+    desc = np.zeros(g.n, np.int64)
+    for i in range(g.n):
+        r = ref[i]
+        while r >= 0:
+            desc[r] |= 1 << (i - r - 1)
+            r = ref[r]
+    np.testing.assert_array_equal(L["desc"], desc)
