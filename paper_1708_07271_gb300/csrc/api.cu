@@ -146,20 +146,19 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
     k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile);
 }
 
-// The flat fixed-point gather serves kb <= 4 with full-width vector access;
-// its chain step also reduces max|z|.
-static bool flat_gather(int kb, int v) { return kb <= 4 && v == kb; }
+// One fused launch (k_xA_fused) serves kb <= 4 with full-width vector access;
+// other shapes run the chain kernel, then the per-column gather.
+static bool fused_xA(int kb, int v) { return kb <= 4 && v == kb; }
 
 template <int KB, int V>
 static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
                          int64_t ldz, const PrState* pst, cudaStream_t st) {
-    unsigned int* zmax = flat_gather(KB, V) ? g->s.zmax : nullptr;
     const int tile = chain_tile(KB, g->cfg);
     const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(float) + 15) / 16 * 16;
     set_smem(k_chain<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
-    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, tile, pst, zmax);
+    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, tile, pst);
 }
 
 template <int KB, int V>
@@ -168,12 +167,19 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
+    k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        z, ldz, y, ldy, g->n, pa);
+}
+
+template <int KB, int V>
+static void launch_xA_fused(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy,
+                            cudaStream_t st) {
     if constexpr (KB <= 4 && V == KB) {
-        k_gather_flat<KB, 0><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(
-            g->colp, g->tent, g->carry_ptr, g->carry, z, y, ldy, g->n, g->s.zmax, g->s.counter, pa);
-    } else {
-        k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr,
-                                                                            g->carry, z, ldz, y, ldy, g->n, pa);
+        const int64_t grid = (g->n + FlatShape<KB>::T - 1) / FlatShape<KB>::T;
+        PrArgs pa{};
+        TraceScope ts(g, "push_fused", st);
+        k_xA_fused<KB, 0><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        g->desc, x, ldx, y, ldy, g->n, pa);
     }
 }
 
@@ -182,12 +188,17 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
+    k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        z, ldz, nullptr, 0, g->n, pa);
+}
+
+template <int KB, int V>
+static void launch_pr_fused(const bvg_dev_graph* g, const float* x, const PrArgs& pa, cudaStream_t st) {
     if constexpr (KB <= 4 && V == KB) {
-        k_gather_flat<KB, 1><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(
-            g->colp, g->tent, g->carry_ptr, g->carry, z, nullptr, 0, g->n, g->s.zmax, g->s.counter, pa);
-    } else {
-        k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr,
-                                                                            g->carry, z, ldz, nullptr, 0, g->n, pa);
+        const int64_t grid = (g->n + FlatShape<KB>::T - 1) / FlatShape<KB>::T;
+        TraceScope ts(g, "pr_fused", st);
+        k_xA_fused<KB, 1><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+                                                                        g->desc, x, KB, nullptr, 0, g->n, pa);
     }
 }
 
@@ -245,12 +256,12 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
     if (rc) return rc;
     if (g->s.pr_kcap < kb) {
         drop_pr_graph(g);
-        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.xb[0], &g->s.xb[1], &g->s.p0}) {
             if (*b) cudaFree(*b);
             *b = nullptr;
         }
         g->s.pr_kcap = 0;
-        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.xb[0], &g->s.xb[1], &g->s.p0}) {
             rc = dev_alloc((void**)b, (size_t)g->n * kb * sizeof(float), nullptr);
             if (rc) return rc;
         }
@@ -312,12 +323,11 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
-        if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, 2 * sizeof(unsigned int), nullptr))) {
+        if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, sizeof(unsigned int), nullptr))) {
             bvg_free_dev(g);
             return rc;
         }
-        g->s.zmax = g->s.counter + 1;
-        BVG_CUDA_TRY(cudaMemsetAsync(g->s.counter, 0, 2 * sizeof(unsigned int), st));
+        BVG_CUDA_TRY(cudaMemsetAsync(g->s.counter, 0, sizeof(unsigned int), st));
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             bvg_free_dev(g);
@@ -335,7 +345,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
     void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
-                    g->s.hy, g->s.p0};
+                    g->s.hy, g->s.p0, g->s.xb[0], g->s.xb[1]};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -447,8 +457,12 @@ extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, in
         const int kb = block_k(k - c0);
         if ((rc = ensure_z(g, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
-        BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
-        BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
+        if (fused_xA(kb, v)) {
+            BVG_KV_CASES(launch_xA_fused, g, x + c0, ld, y + c0, ld, st);
+        } else {
+            BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
+            BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
+        }
         c0 += kb;
     }
     BVG_CUDA_TRY(cudaGetLastError());
@@ -533,6 +547,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     {
         PrArgs pa = base;
         pa.q_new = g->s.q[0];
+        pa.x_new = fused_xA(kb, v) ? g->s.xb[0] : nullptr;
         pa.sc_new = g->s.sc[0];
         const float* start = p_init ? p_init : p0_in;
         BVG_KV_CASES(launch_pr_init, g, start, kb, pa, st);
@@ -552,8 +567,13 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         pa.q_new = g->s.q[1 - par];
         pa.sc_prev = g->s.sc[par];
         pa.sc_new = g->s.sc[1 - par];
-        BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
-        BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
+        if (fused_xA(kb, v)) {
+            pa.x_new = g->s.xb[1 - par];
+            BVG_KV_CASES(launch_pr_fused, g, g->s.xb[par], pa, st);
+        } else {
+            BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
+            BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
+        }
     };
     PrState* hst = (PrState*)g->s.host_state;
     double* hres = (double*)((char*)g->s.host_state + sizeof(PrState));

@@ -90,8 +90,8 @@ struct DevScratch {
     double* sc[2] = {nullptr, nullptr}; // PageRank scalars per parity: [3][32] (1/S, dangling, resid)
     void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
     double* partial = nullptr;          // per-CTA FP64 partial sums
-    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction); allocated with zmax
-    unsigned int* zmax = nullptr;       // max |z| as float bits (fixed-point gather scale), = counter + 1
+    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction)
+    float* xb[2] = {nullptr, nullptr};  // PageRank pushed inputs q / outdeg, n x pr_kcap
     void* host_state = nullptr;         // pinned host copy of the state + residuals
     float* hx = nullptr;                // device staging for the host-buffer product
     float* hy = nullptr;

@@ -23,6 +23,7 @@ struct PrArgs {
     const float* inv_outdeg;   // 0 marks a row without successors
     const float* q_prev;       // previous iterate, unnormalised (n x k, ld ldq)
     float* q_new;
+    float* x_new;              // q_new / outdeg (the next update's input), or NULL
     int64_t ldq;
     const double* sc_prev;     // [3][k]: 1/S, dangling mass, resid (of the previous update)
     double* sc_new;
@@ -117,20 +118,17 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 // [a, a + tile) stages x for kHalo rows past its end and each row adds its
 // descendants in increasing row order into a compensated (hi, lo) sum:
 // bit-reproducible, one barrier. Optionally x is scaled per row first
-// (x_i * rowscale_i, PageRank's 1/outdeg). If zmax != NULL the largest |z|
-// (as float bits, monotone for non-negative floats; NaN ranks above all) is
-// merged into *zmax for the fixed-point gather.
+// (x_i * rowscale_i, PageRank's 1/outdeg).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc, const float* __restrict__ x,
                                                int64_t ldx, const float* __restrict__ rowscale,
                                                float* __restrict__ z, int64_t ldz, int64_t n, int tile,
-                                               const PrState* __restrict__ st, unsigned int* __restrict__ zmax) {
+                                               const PrState* __restrict__ st) {
     if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
     constexpr int G = KB / V;
     extern __shared__ float4 smem_chain[];
     float* xs = reinterpret_cast<float*>(smem_chain);  // [(tile + kHalo) * KB]
-    __shared__ unsigned int wmax[32];
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
@@ -145,7 +143,6 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
         for (int v = 0; v < V; v++) xs[(int64_t)r * KB + lane * V + v] = __fmul_rn(xv.v[v], sc);
     }
     __syncthreads();
-    unsigned int mx = 0;
     for (int r = g; r < own; r += NG) {
         df acc[V];
 #pragma unroll
@@ -158,20 +155,8 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
         }
         Vec<V> out;
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            out.v[v] = df_val(acc[v]);
-            mx = max(mx, __float_as_uint(out.v[v]) & 0x7fffffffu);
-        }
+        for (int v = 0; v < V; v++) out.v[v] = df_val(acc[v]);
         stv<V>(z + (a + r) * ldz + lane * V, out);
-    }
-    if (zmax) {
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = max(mx, wmax[w]);
-            if (mx) atomicMax(zmax, mx);
-        }
     }
 }
 
@@ -208,8 +193,7 @@ struct PrPartials {
 // then the last CTA to finish reduces all CTAs in a fixed order and writes
 // the scalars of this update (deterministic; no spin-waits).
 template <int KB, int V>
-__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init,
-                                unsigned int* zmax = nullptr) {
+__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init) {
     constexpr int G = KB / V;
     __shared__ double sh_part[32][3][KB];
     __shared__ bool sh_last;
@@ -277,7 +261,6 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
             if (bad) pa.st->numeric = 1;
             if (conv || bad) pa.st->done = 1;
         }
-        if (zmax) *zmax = 0u;
         *pa.counter = 0u;
         __threadfence();
     }
@@ -425,28 +408,34 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
 }
 
 // ---------------------------------------------------------------------------
-// Push, scatter step for KB <= 4 right-hand sides: flat, entry-parallel,
-// exact. Same result as k_gather (y_j = sum_k z_k A'_kj, intervals by the
-// running prefix of their start/end events, carry list at the tile start),
-// computed as follows. Every value +-z_k is turned into a 64-bit fixed-point
-// integer with a power-of-two scale 2^s per CTA, chosen from max|z| and the
-// number of terms of the tile so that no partial sum can overflow; integer
-// sums are exact and associative, so all prefix sums below are exact and the
-// result does not depend on the order of additions. The tile's column-major
-// entries are processed EPT consecutive entries per thread (balanced and
-// coalesced); two exclusive prefix sums over this flat stream -- C of all
-// values and Bp of the point values (+-z of residual/dropped ids) -- are
-// recorded at every column boundary b_j = colp[j]. Then
-//   y_j = carry + C(b_{j+1}) - Bp(b_j)
-// (the events of columns <= j, plus the point values of column j), converted
-// back to FP32 with a single rounding.
+// y = x A in ONE launch for KB <= 4 right-hand sides (push: Proposition 1 read
+// for the left product, then the scatter written as a per-column gather).
+//  - Chain step on the fly: the pushed weight of a source row k is
+//    z_k = x_k + sum of x over its descendants (desc[k] bit t = row k+t+1),
+//    added in increasing row order into a compensated (hi, lo) sum.
+//  - Scatter step: y_j = sum_k z_k A'_kj over the column-major entries of the
+//    CTA's T columns: points +-z_k (residual/dropped id j of row k) and
+//    interval events (start at j: +z_k, end before j: -z_k) whose running
+//    prefix is the interval part; the prefix starts from the intervals open
+//    at the tile start (carry list), so no grid-wide scan is needed.
+//  - Exact accumulation: every term is turned into a 64-bit fixed-point
+//    integer with a power-of-two scale chosen per CTA from its own max |z| and
+//    term count, so no partial sum overflows; integer sums are exact and
+//    associative. The entries are processed EPT consecutive ones per thread
+//    (balanced, coalesced); two exclusive prefix sums over this flat stream,
+//    C (all terms) and Bp (point terms), are recorded at every column
+//    boundary b_j = colp[j], and y_j = carry + C(b_{j+1}) - Bp(b_j): the
+//    events of columns <= j plus the points of column j, converted back to
+//    FP32 with one rounding. The result is bit-reproducible.
+// EPI = 0: store y. EPI = 1: PageRank update (see PrArgs): also writes the
+// next iterate q and its pushed input q / outdeg.
 // ---------------------------------------------------------------------------
 template <int KB>
 struct FlatShape {
     static constexpr int NT = 256;
-    static constexpr int EPT = 16 / KB;     // entries per thread and chunk
+    static constexpr int EPT = 8 / KB;      // entries per thread and chunk
     static constexpr int CE = NT * EPT;     // entries per chunk
-    static constexpr int T = 1024 / KB;     // columns per CTA
+    static constexpr int T = 512 / KB;      // columns per CTA
     static constexpr int CPT = T / NT;      // columns per thread in the output phase
 };
 
@@ -475,14 +464,28 @@ __device__ __forceinline__ float from_fx(long long v, int sexp) {
     return __fmul_rn(__fmul_rn(__ll2float_rn(v), s1), s2);
 }
 
+template <int KB>
+__device__ __forceinline__ void subtree_sum(const uint32_t* __restrict__ desc, const float* __restrict__ x,
+                                            int64_t ldx, uint32_t k, float (&zo)[KB]) {
+    Vec<KB> xv = ldv<KB>(x + (int64_t)k * ldx);
+    df acc[KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) acc[v] = {xv.v[v], 0.f};
+    for (uint32_t m = __ldg(desc + k); m; m &= m - 1) {
+        Vec<KB> cv = ldv<KB>(x + (int64_t)(k + __ffs(m)) * ldx);
+#pragma unroll
+        for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], cv.v[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < KB; v++) zo[v] = df_val(acc[v]);
+}
+
 template <int KB, int EPI>
-__global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict__ colp,
-                                                     const uint32_t* __restrict__ tent,
-                                                     const uint32_t* __restrict__ carry_ptr,
-                                                     const uint32_t* __restrict__ carry,
-                                                     const float* __restrict__ z, float* __restrict__ y,
-                                                     int64_t ldy, int64_t n, unsigned int* __restrict__ zmax,
-                                                     unsigned int* __restrict__ counter, PrArgs pa) {
+__global__ void __launch_bounds__(256) k_xA_fused(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                                  const uint32_t* __restrict__ carry_ptr,
+                                                  const uint32_t* __restrict__ carry, const uint32_t* __restrict__ desc,
+                                                  const float* __restrict__ x, int64_t ldx, float* __restrict__ y,
+                                                  int64_t ldy, int64_t n, PrArgs pa) {
     using Sh = FlatShape<KB>;
     constexpr int NT = Sh::NT, EPT = Sh::EPT, CE = Sh::CE, T = Sh::T, CPT = Sh::CPT, NW = NT / 32;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
@@ -493,8 +496,9 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
     __shared__ uint32_t ent_s[CE + NT];     // skewed: entry e at e + e / EPT
     __shared__ long long cb_s[T + 1][KB];   // C at each column boundary
     __shared__ long long bb_s[T + 1][KB];   // Bp at each column boundary
-    __shared__ long long run0_s[KB];
+    __shared__ df run0_s[KB];
     __shared__ long long wtot_s[NW][2][KB];
+    __shared__ unsigned int wmax_s[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t a = (int64_t)blockIdx.x * T;
     const int ncols = (int)((a + T < n ? a + T : n) - a);
@@ -505,62 +509,99 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
 #pragma unroll
         for (int v = 0; v < KB; v++) cb_s[i][v] = bb_s[i][v] = 0;
     }
-    const unsigned int mbits = __ldcg(zmax);
-    const bool bad = mbits >= 0x7f800000u;  // a non-finite z: the product is not defined
     const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
-    __syncthreads();
-    const uint32_t ebase = cp_s[0];
-    const int64_t E = (int64_t)cp_s[ncols] - ebase;
-    const int sexp = fx_exponent(mbits, E + (cr1 - cr0) + 1);
-
-    if (warp == 0) {  // running interval prefix at column a (exact, any order)
-        long long acc[KB];
+    unsigned int mx = 0;  // max |term| as float bits (NaN ranks above every finite value)
+    if (warp == 0) {  // running interval prefix at column a (compensated)
+        df acc[KB];
 #pragma unroll
-        for (int v = 0; v < KB; v++) acc[v] = 0;
+        for (int v = 0; v < KB; v++) acc[v] = df_zero();
         for (uint32_t e = cr0 + lane; e < cr1; e += 32) {
-            Vec<KB> zv = ldv<KB>(z + (int64_t)__ldg(carry + e) * KB);
+            float zc[KB];
+            subtree_sum<KB>(desc, x, ldx, __ldg(carry + e), zc);
 #pragma unroll
-            for (int v = 0; v < KB; v++) acc[v] += to_fx(zv.v[v], sexp);
+            for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], zc[v]);
         }
 #pragma unroll
         for (int v = 0; v < KB; v++) {
-            for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-            if (lane == 0) run0_s[v] = acc[v];
+            for (int o = 16; o > 0; o >>= 1)
+                acc[v] = df_add(acc[v], {__shfl_down_sync(0xffffffffu, acc[v].hi, o),
+                                         __shfl_down_sync(0xffffffffu, acc[v].lo, o)});
+            if (lane == 0) {
+                run0_s[v] = acc[v];
+                mx = max(mx, __float_as_uint(acc[v].hi) & 0x7fffffffu);
+            }
         }
     }
+    __syncthreads();
+    const uint32_t ebase = cp_s[0];
+    const int64_t E = (int64_t)cp_s[ncols] - ebase;
+    const int nch = (int)((E + CE - 1) / CE);
+    const int lo = tid * EPT;
 
-    long long chC[KB], chB[KB];  // prefix of the chunks before this one
-#pragma unroll
-    for (int v = 0; v < KB; v++) chC[v] = chB[v] = 0;
-    for (int64_t cs = 0; cs < E; cs += CE) {
+    // terms of this thread for one chunk: z of the source row, signed
+    float zf[EPT][KB];
+    unsigned int pmask = 0;
+    int cnt = 0;
+    auto load_chunk = [&](int c) {
+        const int64_t cs = (int64_t)c * CE;
         const int ce = (int)(E - cs < CE ? E - cs : CE);
         for (int e = tid; e < ce; e += NT) ent_s[e + e / EPT] = __ldg(tent + ebase + cs + e);
         __syncthreads();
-        const int lo = tid * EPT;
-        const int cnt = ce - lo < 0 ? 0 : (ce - lo > EPT ? EPT : ce - lo);
-        long long val[EPT][KB], tC[KB], tB[KB];
-        unsigned int pmask = 0;
-#pragma unroll
-        for (int v = 0; v < KB; v++) tC[v] = tB[v] = 0;
+        cnt = ce - lo < 0 ? 0 : (ce - lo > EPT ? EPT : ce - lo);
+        pmask = 0;
 #pragma unroll
         for (int i = 0; i < EPT; i++) {
 #pragma unroll
-            for (int v = 0; v < KB; v++) val[i][v] = 0;
+            for (int v = 0; v < KB; v++) zf[i][v] = 0.f;
             if (i < cnt) {
                 const uint32_t w = ent_s[lo + i + tid];
                 const uint32_t tag = w >> kIdBits;
-                Vec<KB> zv = ldv<KB>(z + (int64_t)id_of(w) * KB);
+                subtree_sum<KB>(desc, x, ldx, id_of(w), zf[i]);
 #pragma unroll
                 for (int v = 0; v < KB; v++) {
-                    const long long f = to_fx(zv.v[v], sexp);
-                    val[i][v] = (tag & 1) ? -f : f;
-                    tC[v] += val[i][v];
-                    if (tag < 2) tB[v] += val[i][v];
+                    if (tag & 1) zf[i][v] = -zf[i][v];
+                    mx = max(mx, __float_as_uint(zf[i][v]) & 0x7fffffffu);
                 }
                 if (tag < 2) pmask |= 1u << i;
             }
         }
-        // exclusive block scan of the thread totals (exact)
+    };
+    // pass 1: the terms (kept in registers when the tile is one chunk) and max |term|
+    for (int c = 0; c < nch; c++) {
+        if (c > 0) __syncthreads();
+        load_chunk(c);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) wmax_s[warp] = mx;
+    __syncthreads();
+#pragma unroll
+    for (int w2 = 0; w2 < NW; w2++) mx = max(mx, wmax_s[w2]);
+    const bool bad = mx >= 0x7f800000u;  // a non-finite term: the product is not defined
+    const int sexp = fx_exponent(bad ? 0u : mx, E + 2);
+    long long run0[KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) run0[v] = to_fx(run0_s[v].hi, sexp) + to_fx(run0_s[v].lo, sexp);
+
+    // pass 2: exact prefix sums, recorded at the column boundaries
+    long long chC[KB], chB[KB];
+#pragma unroll
+    for (int v = 0; v < KB; v++) chC[v] = chB[v] = 0;
+    for (int c = 0; c < nch; c++) {
+        if (nch > 1) {  // the terms of chunk c are computed again
+            __syncthreads();
+            load_chunk(c);
+        }
+        long long tC[KB], tB[KB];
+#pragma unroll
+        for (int v = 0; v < KB; v++) tC[v] = tB[v] = 0;
+#pragma unroll
+        for (int i = 0; i < EPT; i++)
+#pragma unroll
+            for (int v = 0; v < KB; v++) {
+                const long long f = to_fx(zf[i][v], sexp);
+                tC[v] += f;
+                if (pmask >> i & 1) tB[v] += f;
+            }
         long long xC[KB], xB[KB], bC[KB], bB[KB];
 #pragma unroll
         for (int v = 0; v < KB; v++) {
@@ -584,6 +625,7 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
 #pragma unroll
         for (int v = 0; v < KB; v++) {
             bC[v] = bB[v] = 0;
+#pragma unroll
             for (int w2 = 0; w2 < NW; w2++) {
                 if (w2 < warp) {
                     xC[v] += wtot_s[w2][0][v];
@@ -593,9 +635,8 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
                 bB[v] += wtot_s[w2][1][v];
             }
         }
-        // record the prefixes at the column boundaries inside (lo, lo + cnt]
         if (cnt > 0) {
-            const uint32_t first = ebase + (uint32_t)(cs + lo);  // boundaries b with b > first
+            const uint32_t first = ebase + (uint32_t)((int64_t)c * CE + lo);  // boundaries b > first
             int j0 = 0, j1 = ncols + 1;
             while (j0 < j1) {  // first j with cp_s[j] > first
                 const int mid = (j0 + j1) >> 1;
@@ -614,8 +655,9 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
                 if (i < cnt) {
 #pragma unroll
                     for (int v = 0; v < KB; v++) {
-                        rc[v] += val[i][v];
-                        if (pmask >> i & 1) rb[v] += val[i][v];
+                        const long long f = to_fx(zf[i][v], sexp);
+                        rc[v] += f;
+                        if (pmask >> i & 1) rb[v] += f;
                     }
                     const uint32_t pos = first + (uint32_t)(i + 1);
                     while (j <= ncols && cp_s[j] == pos) {
@@ -634,8 +676,8 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
             chC[v] += bC[v];
             chB[v] += bB[v];
         }
-        __syncthreads();
     }
+    __syncthreads();
 
     double S[KB], R[KB], Dg[KB];
 #pragma unroll
@@ -647,16 +689,14 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
         const int64_t j = a + jl;
         Vec<KB> out;
 #pragma unroll
-        for (int v = 0; v < KB; v++) {
-            const long long t = run0_s[v] + cb_s[jl + 1][v] - bb_s[jl][v];
-            out.v[v] = bad ? __int_as_float(0x7fc00000) : from_fx(t, sexp);
-        }
+        for (int v = 0; v < KB; v++)
+            out.v[v] = bad ? __int_as_float(0x7fc00000) : from_fx(run0[v] + cb_s[jl + 1][v] - bb_s[jl][v], sexp);
         if constexpr (EPI == 0) {
             stv<KB>(y + j * ldy, out);
         } else {
             const float io = __ldg(pa.inv_outdeg + j);
             const float un = 1.0f / (float)n;
-            Vec<KB> qp = ldv<KB>(pa.q_prev + j * pa.ldq), qn, p0v;
+            Vec<KB> qp = ldv<KB>(pa.q_prev + j * pa.ldq), qn, xn, p0v;
             if (pa.p0) p0v = ldv<KB>(pa.p0 + j * pa.ldp0);
 #pragma unroll
             for (int v = 0; v < KB; v++) {
@@ -665,29 +705,16 @@ __global__ void __launch_bounds__(256) k_gather_flat(const uint32_t* __restrict_
                 const float dl = (float)pa.sc_prev[1 * KB + v];
                 const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
                 qn.v[v] = qj;
+                xn.v[v] = __fmul_rn(qj, io);
                 S[v] += (double)qj;
                 R[v] += fabs((double)qj - (double)qp.v[v]);
                 if (io == 0.0f) Dg[v] += (double)qj;
             }
             stv<KB>(pa.q_new + j * pa.ldq, qn);
+            stv<KB>(pa.x_new + j * pa.ldq, xn);
         }
     }
-    if constexpr (EPI == 1) {
-        pr_block_reduce<KB, KB>(S, R, Dg, pa, false, zmax);
-    } else {
-        // the last CTA to finish clears zmax for the next product
-        __shared__ bool last;
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            last = atomicAdd(counter, 1u) == gridDim.x - 1;
-            if (last) {
-                *zmax = 0u;
-                *counter = 0u;
-                __threadfence();
-            }
-        }
-    }
+    if constexpr (EPI == 1) pr_block_reduce<KB, KB>(S, R, Dg, pa, false);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
@@ -713,6 +740,12 @@ __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_ini
         }
         stv<V>(pa.q_new + j * pa.ldq + lane * V, pv);
         const float io = __ldg(pa.inv_outdeg + j);
+        if (pa.x_new) {
+            Vec<V> xv;
+#pragma unroll
+            for (int v = 0; v < V; v++) xv.v[v] = __fmul_rn(pv.v[v], io);
+            stv<V>(pa.x_new + j * pa.ldq + lane * V, xv);
+        }
 #pragma unroll
         for (int v = 0; v < V; v++) {
             S[v] += (double)pv.v[v];
