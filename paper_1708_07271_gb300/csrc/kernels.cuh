@@ -436,7 +436,7 @@ struct FlatShape {
     static constexpr int EPT = 8 / KB;      // entries per thread and chunk
     static constexpr int CE = NT * EPT;     // entries per chunk
     static constexpr int T = 512 / KB;      // columns per CTA
-    static constexpr int CPT = T / NT;      // columns per thread in the output phase
+    static constexpr int CPT = (T + NT - 1) / NT;  // columns per thread in the output phase
 };
 
 // Scale exponent s with maxabs * terms * 2^s <= 2^62 (maxabs given as float
