@@ -300,7 +300,7 @@ def run_bv(args):
     peak, peak_kind = measured_peaks()
     dom = max(trace.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_launches, dom_ms) = dom
-    dom_bytes = {"push_gather": bytemodel.push_gather(L, k), "push_chain": bytemodel.push_chain(L, k)}[dom_name]
+    dom_bytes = bytemodel.KERNELS[dom_name](L, k)
     dom_avg_s = dom_ms / dom_launches * 1e-3
     achieved = dom_bytes / dom_avg_s / 1e9
     traffic = profile_traffic(dom_name, kernel_source_digest())

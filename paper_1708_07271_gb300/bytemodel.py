@@ -6,11 +6,15 @@ gathered elements (served by L1/L2 when ids are local) are not counted, so
 DRAM traffic measured by ncu above these figures means re-reads.
 
 Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
-  push_chain   n (meta) + 4kn (x) + 4kn (z)
+  push_chain   4n (descendant masks) + 4kn (x) + 4kn (z)
   push_gather  4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
                + 4*carry_entries + 4kn (z) + 4kn (y)
   pull         n (meta) + 4(n+1) (row offsets) + 4*words + 4kn (x) + 4kn (y)
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
+  push_fused   4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
+               + 4*carry_entries + 4n (descendant masks) + 4kn (x) + 4kn (y)
+  pr_fused     push_fused - 4kn (y not stored) + 4n (1/outdeg) + 4kn (q_prev)
+               + 8kn (q_new, next input) [+ 4kn (p0) when teleport vectors are given]
   pr_chain     push_chain + 4n (1/outdeg)
   pr_gather    push_gather - 4kn (y not stored) + 4n (1/outdeg) + 4kn (q_prev)
                + 4kn (q_new) [+ 4kn (p0) when teleport vectors are given]
@@ -20,7 +24,7 @@ from __future__ import annotations
 
 def push_chain(L: dict, k: int) -> int:
     n = L["n"]
-    return n + 8 * k * n
+    return 4 * n + 8 * k * n
 
 
 def push_gather(L: dict, k: int) -> int:
@@ -48,3 +52,17 @@ def pr_gather(L: dict, k: int, with_p0: bool) -> int:
 
 def xA_total(L: dict, k: int) -> int:
     return push_chain(L, k) + push_gather(L, k)
+
+
+def push_fused(L: dict, k: int) -> int:
+    n = L["n"]
+    return (4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"] + 4 * n
+            + 8 * k * n)
+
+
+def pr_fused(L: dict, k: int, with_p0: bool) -> int:
+    n = L["n"]
+    return push_fused(L, k) - 4 * k * n + 4 * n + 12 * k * n + (4 * k * n if with_p0 else 0)
+
+
+KERNELS = {"push_fused": push_fused, "push_gather": push_gather, "push_chain": push_chain, "pull": pull}
