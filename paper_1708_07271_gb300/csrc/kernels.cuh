@@ -548,21 +548,54 @@ __global__ void __launch_bounds__(256) k_xA_fused(const uint32_t* __restrict__ c
         for (int e = tid; e < ce; e += NT) ent_s[e + e / EPT] = __ldg(tent + ebase + cs + e);
         __syncthreads();
         cnt = ce - lo < 0 ? 0 : (ce - lo > EPT ? EPT : ce - lo);
+        // The loads are issued level by level for all EPT entries at once
+        // (entry -> source row's mask and x -> first two descendants), so
+        // their latencies overlap; rows with more descendants finish in a
+        // short loop.
+        uint32_t k[EPT], dm[EPT];
+        unsigned int neg = 0;
         pmask = 0;
 #pragma unroll
         for (int i = 0; i < EPT; i++) {
+            const uint32_t w = i < cnt ? ent_s[lo + i + tid] : 0u;
+            k[i] = id_of(w);
+            if (i < cnt && (w >> kIdBits) < 2) pmask |= 1u << i;
+            if ((w >> kIdBits) & 1) neg |= 1u << i;
+        }
+        Vec<KB> x0[EPT], x1[EPT], x2[EPT];
 #pragma unroll
-            for (int v = 0; v < KB; v++) zf[i][v] = 0.f;
-            if (i < cnt) {
-                const uint32_t w = ent_s[lo + i + tid];
-                const uint32_t tag = w >> kIdBits;
-                subtree_sum<KB>(desc, x, ldx, id_of(w), zf[i]);
+        for (int i = 0; i < EPT; i++) {
+            dm[i] = i < cnt ? __ldg(desc + k[i]) : 0u;
+            if (i < cnt) x0[i] = ldv<KB>(x + (int64_t)k[i] * ldx);
+        }
 #pragma unroll
-                for (int v = 0; v < KB; v++) {
-                    if (tag & 1) zf[i][v] = -zf[i][v];
-                    mx = max(mx, __float_as_uint(zf[i][v]) & 0x7fffffffu);
-                }
-                if (tag < 2) pmask |= 1u << i;
+        for (int i = 0; i < EPT; i++) {
+            const uint32_t m1 = dm[i], m2 = m1 & (m1 - 1);
+#pragma unroll
+            for (int v = 0; v < KB; v++) x1[i].v[v] = x2[i].v[v] = 0.f;
+            if (m1) x1[i] = ldv<KB>(x + (int64_t)(k[i] + __ffs(m1)) * ldx);
+            if (m2) x2[i] = ldv<KB>(x + (int64_t)(k[i] + __ffs(m2)) * ldx);
+        }
+#pragma unroll
+        for (int i = 0; i < EPT; i++) {
+            df acc[KB];
+#pragma unroll
+            for (int v = 0; v < KB; v++) {
+                acc[v] = {i < cnt ? x0[i].v[v] : 0.f, 0.f};
+                acc[v] = df_addf(df_addf(acc[v], x1[i].v[v]), x2[i].v[v]);
+            }
+            uint32_t m = dm[i] & (dm[i] - 1);
+            m &= m - 1;  // the first two descendants are in
+            for (; m; m &= m - 1) {
+                Vec<KB> cv = ldv<KB>(x + (int64_t)(k[i] + __ffs(m)) * ldx);
+#pragma unroll
+                for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], cv.v[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < KB; v++) {
+                const float zv = df_val(acc[v]);
+                zf[i][v] = (neg >> i & 1) ? -zv : zv;
+                mx = max(mx, __float_as_uint(zf[i][v]) & 0x7fffffffu);
             }
         }
     };
