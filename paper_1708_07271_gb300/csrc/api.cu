@@ -87,11 +87,28 @@ constexpr int kThreads = 256;
 // Rows per CTA: the halo of kHalo rows is recomputed by two CTAs, so tiles
 // stay large; shared memory grows with kb.
 static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
-static int chain_tile(int kb, const LaunchCfg& c) { return std::max(256, c.chain_tile / kb); }
 // Columns per CTA of the gather kernel (k_gather's GatherShape).
 static int gather_tile(int kb, int v, const LaunchCfg&) {
-    (void)v;
-    return std::max(128, 1024 / kb);
+    const int G = kb / v, NG = 256 / G, CPT = std::max(4, G / 2);
+    return NG * CPT;
+}
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel on the stream finishes; it waits (griddepcontrol.wait)
+// before reading that kernel's output.
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int64_t grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <class K>
@@ -146,19 +163,12 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
     k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile);
 }
 
-// One fused launch (k_xA_fused) serves kb <= 4 with full-width vector access;
-// other shapes run the chain kernel, then the per-column gather.
-static bool fused_xA(int kb, int v) { return kb <= 4 && v == kb; }
-
 template <int KB, int V>
 static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* z,
                          int64_t ldz, const PrState* pst, cudaStream_t st) {
-    const int tile = chain_tile(KB, g->cfg);
-    const size_t smem = ((size_t)(tile + kHalo) * KB * sizeof(float) + 15) / 16 * 16;
-    set_smem(k_chain<KB, V>, smem);
-    const int64_t grid = (g->n + tile - 1) / tile;
+    const int64_t grid = (g->n + ChainShape<KB, V>::TILE - 1) / ChainShape<KB, V>::TILE;
     TraceScope ts(g, pst ? "pr_chain" : "push_chain", st);
-    k_chain<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, tile, pst);
+    k_chain<KB, V><<<(unsigned)grid, ChainShape<KB, V>::NT, 0, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, pst);
 }
 
 template <int KB, int V>
@@ -167,41 +177,19 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
-    k_gather<KB, V, 0><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        z, ldz, y, ldy, g->n, pa);
+    launch_pdl(k_gather<KB, V, 0>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
+               (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz, y, ldy,
+               g->n, pa);
 }
-
-template <int KB, int V>
-static void launch_xA_fused(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy,
-                            cudaStream_t st) {
-    if constexpr (KB <= 4 && V == KB) {
-        const int64_t grid = (g->n + FlatShape<KB>::T - 1) / FlatShape<KB>::T;
-        PrArgs pa{};
-        TraceScope ts(g, "push_fused", st);
-        k_xA_fused<KB, 0><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        g->desc, x, ldx, y, ldy, g->n, pa);
-    }
-}
-
 template <int KB, int V>
 static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz, const PrArgs& pa, cudaStream_t st) {
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
-    k_gather<KB, V, 1><<<(unsigned)grid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        z, ldz, nullptr, 0, g->n, pa);
+    launch_pdl(k_gather<KB, V, 1>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
+               (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz,
+               (float*)nullptr, (int64_t)0, g->n, pa);
 }
-
-template <int KB, int V>
-static void launch_pr_fused(const bvg_dev_graph* g, const float* x, const PrArgs& pa, cudaStream_t st) {
-    if constexpr (KB <= 4 && V == KB) {
-        const int64_t grid = (g->n + FlatShape<KB>::T - 1) / FlatShape<KB>::T;
-        TraceScope ts(g, "pr_fused", st);
-        k_xA_fused<KB, 1><<<(unsigned)grid, FlatShape<KB>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
-                                                                        g->desc, x, KB, nullptr, 0, g->n, pa);
-    }
-}
-
 template <int KB, int V>
 static void launch_pr_init(const bvg_dev_graph* g, const float* p_init, int64_t ldi, const PrArgs& pa,
                            cudaStream_t st) {
@@ -457,12 +445,8 @@ extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, in
         const int kb = block_k(k - c0);
         if ((rc = ensure_z(g, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
-        if (fused_xA(kb, v)) {
-            BVG_KV_CASES(launch_xA_fused, g, x + c0, ld, y + c0, ld, st);
-        } else {
-            BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
-            BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
-        }
+        BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
+        BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
         c0 += kb;
     }
     BVG_CUDA_TRY(cudaGetLastError());
@@ -547,7 +531,6 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     {
         PrArgs pa = base;
         pa.q_new = g->s.q[0];
-        pa.x_new = fused_xA(kb, v) ? g->s.xb[0] : nullptr;
         pa.sc_new = g->s.sc[0];
         const float* start = p_init ? p_init : p0_in;
         BVG_KV_CASES(launch_pr_init, g, start, kb, pa, st);
@@ -567,13 +550,8 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         pa.q_new = g->s.q[1 - par];
         pa.sc_prev = g->s.sc[par];
         pa.sc_new = g->s.sc[1 - par];
-        if (fused_xA(kb, v)) {
-            pa.x_new = g->s.xb[1 - par];
-            BVG_KV_CASES(launch_pr_fused, g, g->s.xb[par], pa, st);
-        } else {
-            BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
-            BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
-        }
+        BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
+        BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
     };
     PrState* hst = (PrState*)g->s.host_state;
     double* hres = (double*)((char*)g->s.host_state + sizeof(PrState));

@@ -114,44 +114,64 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 // passes through k (Proposition 1 read for the left product: v_i is the sum
 // of the difference rows along its chain), i.e. x summed over the subtree of
 // k in the reference forest. desc[k] bit t marks row k + t + 1 as a
-// descendant (a chain spans at most kHalo rows), so a CTA that owns rows
-// [a, a + tile) stages x for kHalo rows past its end and each row adds its
+// descendant (a chain spans at most kHalo rows). A CTA owns ChainShape::TILE
+// rows; it stages x for its rows and kHalo rows past the end in shared
+// memory, reads the masks of its own rows into registers (all loads of a
+// thread are independent and issued together), then each row adds its
 // descendants in increasing row order into a compensated (hi, lo) sum:
 // bit-reproducible, one barrier. Optionally x is scaled per row first
-// (x_i * rowscale_i, PageRank's 1/outdeg).
+// (x_i * rowscale_i, PageRank's 1/outdeg). The kernel allows the next
+// kernel on the stream to launch early (programmatic dependent launch).
 // ---------------------------------------------------------------------------
+template <int KB, int V>
+struct ChainShape {
+    static constexpr int NT = 256;
+    static constexpr int G = KB / V;
+    static constexpr int NG = NT / G;
+    static constexpr int TILE = 4096 / KB > 1024 ? 1024 : (4096 / KB < 128 ? 128 : 4096 / KB);
+    static constexpr int RPT = TILE / NG;  // rows per group
+};
+
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc, const float* __restrict__ x,
                                                int64_t ldx, const float* __restrict__ rowscale,
-                                               float* __restrict__ z, int64_t ldz, int64_t n, int tile,
+                                               float* __restrict__ z, int64_t ldz, int64_t n,
                                                const PrState* __restrict__ st) {
+    using Sh = ChainShape<KB, V>;
+    constexpr int G = Sh::G, NG = Sh::NG, TILE = Sh::TILE, RPT = Sh::RPT;
+    asm volatile("griddepcontrol.launch_dependents;");
     if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
-    constexpr int G = KB / V;
-    extern __shared__ float4 smem_chain[];
-    float* xs = reinterpret_cast<float*>(smem_chain);  // [(tile + kHalo) * KB]
-    const int NG = blockDim.x / G;
+    __shared__ float xs[(TILE + kHalo) * KB];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const int64_t a = (int64_t)blockIdx.x * tile;
-    const int64_t hi = a + tile + kHalo < n ? a + tile + kHalo : n;
-    const int cnt = (int)(hi - a);
-    const int own = (int)((a + tile < n ? a + tile : n) - a);
+    const int64_t a = (int64_t)blockIdx.x * TILE;
+    const int cnt = (int)((a + TILE + kHalo < n ? a + TILE + kHalo : n) - a);
+    const int own = (int)((a + TILE < n ? a + TILE : n) - a);
 
+    uint32_t m[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+        const int r = g + i * NG;
+        m[i] = r < own ? __ldg(desc + a + r) : 0u;
+    }
     for (int r = g; r < cnt; r += NG) {
         Vec<V> xv = ldv<V>(x + (a + r) * ldx + lane * V);
         const float sc = rowscale ? __ldg(rowscale + a + r) : 1.0f;
 #pragma unroll
-        for (int v = 0; v < V; v++) xs[(int64_t)r * KB + lane * V + v] = __fmul_rn(xv.v[v], sc);
+        for (int v = 0; v < V; v++) xs[r * KB + lane * V + v] = __fmul_rn(xv.v[v], sc);
     }
     __syncthreads();
-    for (int r = g; r < own; r += NG) {
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+        const int r = g + i * NG;
+        if (r >= own) break;
         df acc[V];
 #pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = {xs[(int64_t)r * KB + lane * V + v], 0.f};
-        for (uint32_t m = __ldg(desc + a + r); m; m &= m - 1) {
-            const int c = r + __ffs(m);  // bit t -> row r + t + 1
+        for (int v = 0; v < V; v++) acc[v] = {xs[r * KB + lane * V + v], 0.f};
+        for (uint32_t mm = m[i]; mm; mm &= mm - 1) {
+            const int c = r + __ffs(mm);  // bit t -> row r + t + 1
             if (c >= cnt) break;
 #pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[(int64_t)c * KB + lane * V + v]);
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[c * KB + lane * V + v]);
         }
         Vec<V> out;
 #pragma unroll
@@ -178,10 +198,12 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // ---------------------------------------------------------------------------
 template <int KB, int V>
 struct GatherShape {
-    static constexpr int NT = 128;                       // threads per CTA
+    static constexpr int NT = 256;                       // threads per CTA
     static constexpr int G = KB / V;                     // lanes per column group
-    static constexpr int T = 1024 / KB > 128 ? 1024 / KB : 128;  // columns per CTA
-    static constexpr int CPT = T * G / NT;               // columns per group
+    static constexpr int NG = NT / G;                    // column groups per CTA
+    static constexpr int CPT = G / 2 > 4 ? G / 2 : 4;    // consecutive columns per group
+    static constexpr int T = NG * CPT;                   // columns per CTA (a multiple of kCarryTile)
+    static constexpr int B = 8;                          // entries loaded per batch
 };
 
 template <int KB>
@@ -267,17 +289,14 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
 }
 
 template <int KB, int V, int EPI>
-__global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                                 const uint32_t* __restrict__ carry_ptr,
                                                 const uint32_t* __restrict__ carry, const float* __restrict__ z,
                                                 int64_t ldz, float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
     using Sh = GatherShape<KB, V>;
-    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32;
+    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, B = Sh::B;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
-    if constexpr (EPI == 1) {
-        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
-    }
     __shared__ df run_s[KB];
     __shared__ df wtot_s[NW][KB];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -286,14 +305,23 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
     const int64_t end = a + T < n ? a + T : n;
     const int64_t c0 = a + (int64_t)g * CPT;
 
+    // structure loads do not depend on the previous kernel: issue them first
+    uint32_t cp[CPT + 1];
+#pragma unroll
+    for (int q = 0; q <= CPT; q++) cp[q] = __ldg(colp + (c0 + q < end ? c0 + q : end));
+    const int64_t ct = a / kCarryTile;
+    const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // z (and the PageRank state) are ready
+    if constexpr (EPI == 1) {
+        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+    }
+
     // running interval prefix at column a: sources of intervals open there
     if (warp == 0) {
         df acc[KB];
 #pragma unroll
         for (int c = 0; c < KB; c++) acc[c] = df_zero();
-        const int64_t ct = a / kCarryTile;
-        const uint32_t e1 = __ldg(carry_ptr + ct + 1);
-        for (uint32_t e = __ldg(carry_ptr + ct) + lane32; e < e1; e += 32) {
+        for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
             for (int c = 0; c < KB; c++) acc[c] = df_addf(acc[c], __ldg(zr + c));
@@ -309,39 +337,83 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
         }
     }
 
-    // per-column point sums (FP32) and interval events (compensated)
+    // per-column point sums P (FP32, few terms, in storage order) and events D
+    // (compensated: their prefix carries any error to later columns). The
+    // group's entries are contiguous; they are loaded B at a time (independent
+    // loads in flight), and a running column sum is flushed at each boundary.
     float P[CPT][V];
     df D[CPT][V];
-    df tot[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) tot[v] = df_zero();
-#pragma unroll
-    for (int q = 0; q < CPT; q++) {
+    for (int q = 0; q < CPT; q++)
 #pragma unroll
         for (int v = 0; v < V; v++) {
             P[q][v] = 0.f;
             D[q][v] = df_zero();
         }
-        const int64_t j = c0 + q;
-        if (j < end) {
-            const uint32_t e1 = __ldg(colp + j + 1);
-            for (uint32_t e = __ldg(colp + j); e < e1; e++) {
-                const uint32_t w = __ldg(tent + e);
-                Vec<V> zv = ldv<V>(z + (int64_t)id_of(w) * ldz + lane * V);
-                const uint32_t tag = w >> kIdBits;
-                if (tag < 2) {
+    float curP[V];
+    df curD[V];
 #pragma unroll
-                    for (int v = 0; v < V; v++) P[q][v] += (tag & 1) ? -zv.v[v] : zv.v[v];
-                } else {
+    for (int v = 0; v < V; v++) {
+        curP[v] = 0.f;
+        curD[v] = df_zero();
+    }
+    int q = 0;
+    uint32_t nextb = cp[1];
+    auto flush = [&]() {
 #pragma unroll
-                    for (int v = 0; v < V; v++) D[q][v] = df_addf(D[q][v], (tag & 1) ? -zv.v[v] : zv.v[v]);
+        for (int qq = 0; qq < CPT; qq++)
+            if (qq == q) {
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    P[qq][v] = curP[v];
+                    D[qq][v] = curD[v];
                 }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < V; v++) tot[v] = df_add(tot[v], D[q][v]);
+        for (int v = 0; v < V; v++) {
+            curP[v] = 0.f;
+            curD[v] = df_zero();
+        }
+        q++;
+        uint32_t nb = cp[CPT];
+#pragma unroll
+        for (int t = CPT - 1; t >= 1; t--)
+            if (q + 1 == t) nb = cp[t];
+        nextb = nb;
+    };
+    const uint32_t eend = cp[CPT];
+    for (uint32_t base = cp[0]; base < eend; base += B) {
+        uint32_t w[B];
+        Vec<V> zv[B];
+#pragma unroll
+        for (int i = 0; i < B; i++) w[i] = base + i < eend ? __ldg(tent + base + i) : 0u;
+#pragma unroll
+        for (int i = 0; i < B; i++)
+            if (base + i < eend) zv[i] = ldv<V>(z + (int64_t)id_of(w[i]) * ldz + lane * V);
+#pragma unroll
+        for (int i = 0; i < B; i++) {
+            if (base + i >= eend) break;
+            while (base + i >= nextb) flush();
+            const uint32_t tag = w[i] >> kIdBits;
+            if (tag < 2) {
+#pragma unroll
+                for (int v = 0; v < V; v++) curP[v] += (tag & 1) ? -zv[i].v[v] : zv[i].v[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; v++) curD[v] = df_addf(curD[v], (tag & 1) ? -zv[i].v[v] : zv[i].v[v]);
+            }
+        }
     }
-    // exclusive prefix of the group totals across the block (compensated)
+    flush();  // the last column that has entries; later columns stay zero
+
+    // exclusive prefix of the group totals of D across the block (compensated)
+    df tot[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        tot[v] = df_zero();
+#pragma unroll
+        for (int qq = 0; qq < CPT; qq++) tot[v] = df_add(tot[v], D[qq][v]);
+    }
     df inc[V], ex[V];
 #pragma unroll
     for (int v = 0; v < V; v++) inc[v] = tot[v];
@@ -366,7 +438,7 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
 #pragma unroll
     for (int v = 0; v < V; v++) {
         df r = run_s[lane * V + v];
-        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w][lane * V + v]);
+        for (int w2 = 0; w2 < warp; w2++) r = df_add(r, wtot_s[w2][lane * V + v]);
         run[v] = df_add(r, ex[v]);
     }
 
@@ -374,13 +446,13 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
 #pragma unroll
     for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
 #pragma unroll
-    for (int q = 0; q < CPT; q++) {
-        const int64_t j = c0 + q;
+    for (int qq = 0; qq < CPT; qq++) {
+        const int64_t j = c0 + qq;
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] = df_add(run[v], D[q][v]);
-            out.v[v] = df_val(df_addf(run[v], P[q][v]));
+            run[v] = df_add(run[v], D[qq][v]);
+            out.v[v] = df_val(df_addf(run[v], P[qq][v]));
         }
         if (j >= end) continue;
         if constexpr (EPI == 0) {
@@ -405,349 +477,6 @@ __global__ void __launch_bounds__(128) k_gather(const uint32_t* __restrict__ col
         }
     }
     if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
-}
-
-// ---------------------------------------------------------------------------
-// y = x A in ONE launch for KB <= 4 right-hand sides (push: Proposition 1 read
-// for the left product, then the scatter written as a per-column gather).
-//  - Chain step on the fly: the pushed weight of a source row k is
-//    z_k = x_k + sum of x over its descendants (desc[k] bit t = row k+t+1),
-//    added in increasing row order into a compensated (hi, lo) sum.
-//  - Scatter step: y_j = sum_k z_k A'_kj over the column-major entries of the
-//    CTA's T columns: points +-z_k (residual/dropped id j of row k) and
-//    interval events (start at j: +z_k, end before j: -z_k) whose running
-//    prefix is the interval part; the prefix starts from the intervals open
-//    at the tile start (carry list), so no grid-wide scan is needed.
-//  - Exact accumulation: every term is turned into a 64-bit fixed-point
-//    integer with a power-of-two scale chosen per CTA from its own max |z| and
-//    term count, so no partial sum overflows; integer sums are exact and
-//    associative. The entries are processed EPT consecutive ones per thread
-//    (balanced, coalesced); two exclusive prefix sums over this flat stream,
-//    C (all terms) and Bp (point terms), are recorded at every column
-//    boundary b_j = colp[j], and y_j = carry + C(b_{j+1}) - Bp(b_j): the
-//    events of columns <= j plus the points of column j, converted back to
-//    FP32 with one rounding. The result is bit-reproducible.
-// EPI = 0: store y. EPI = 1: PageRank update (see PrArgs): also writes the
-// next iterate q and its pushed input q / outdeg.
-// ---------------------------------------------------------------------------
-template <int KB>
-struct FlatShape {
-    static constexpr int NT = 256;
-    static constexpr int EPT = 8 / KB;      // entries per thread and chunk
-    static constexpr int CE = NT * EPT;     // entries per chunk
-    static constexpr int T = 512 / KB;      // columns per CTA
-    static constexpr int CPT = (T + NT - 1) / NT;  // columns per thread in the output phase
-};
-
-// Scale exponent s with maxabs * terms * 2^s <= 2^62 (maxabs given as float
-// bits); integer exponent arithmetic only.
-__device__ __forceinline__ int fx_exponent(unsigned int maxbits, long long terms) {
-    if (maxbits == 0) return 0;
-    const int e_m = (int)((maxbits >> 23) & 0xff) - 126;  // maxabs < 2^e_m
-    const int e_t = 64 - __clzll((unsigned long long)terms);  // terms < 2^e_t
-    int sexp = 62 - e_m - e_t;
-    return sexp > 100 ? 100 : (sexp < -100 ? -100 : sexp);
-}
-
-__device__ __forceinline__ float pow2f(int e) {  // 2^e for |e| <= 126
-    return __int_as_float((e + 127) << 23);
-}
-
-__device__ __forceinline__ long long to_fx(float v, int sexp) {
-    // v * 2^s is exact (a power-of-two scaling in range); one rounding to integer
-    const float s1 = pow2f(sexp / 2), s2 = pow2f(sexp - sexp / 2);
-    return __float2ll_rn(__fmul_rn(__fmul_rn(v, s1), s2));
-}
-
-__device__ __forceinline__ float from_fx(long long v, int sexp) {
-    const float s1 = pow2f(-(sexp / 2)), s2 = pow2f(-(sexp - sexp / 2));
-    return __fmul_rn(__fmul_rn(__ll2float_rn(v), s1), s2);
-}
-
-template <int KB>
-__device__ __forceinline__ void subtree_sum(const uint32_t* __restrict__ desc, const float* __restrict__ x,
-                                            int64_t ldx, uint32_t k, float (&zo)[KB]) {
-    Vec<KB> xv = ldv<KB>(x + (int64_t)k * ldx);
-    df acc[KB];
-#pragma unroll
-    for (int v = 0; v < KB; v++) acc[v] = {xv.v[v], 0.f};
-    for (uint32_t m = __ldg(desc + k); m; m &= m - 1) {
-        Vec<KB> cv = ldv<KB>(x + (int64_t)(k + __ffs(m)) * ldx);
-#pragma unroll
-        for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], cv.v[v]);
-    }
-#pragma unroll
-    for (int v = 0; v < KB; v++) zo[v] = df_val(acc[v]);
-}
-
-template <int KB, int EPI>
-__global__ void __launch_bounds__(256) k_xA_fused(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
-                                                  const uint32_t* __restrict__ carry_ptr,
-                                                  const uint32_t* __restrict__ carry, const uint32_t* __restrict__ desc,
-                                                  const float* __restrict__ x, int64_t ldx, float* __restrict__ y,
-                                                  int64_t ldy, int64_t n, PrArgs pa) {
-    using Sh = FlatShape<KB>;
-    constexpr int NT = Sh::NT, EPT = Sh::EPT, CE = Sh::CE, T = Sh::T, CPT = Sh::CPT, NW = NT / 32;
-    static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
-    if constexpr (EPI == 1) {
-        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
-    }
-    __shared__ uint32_t cp_s[T + 1];
-    __shared__ uint32_t ent_s[CE + NT];     // skewed: entry e at e + e / EPT
-    __shared__ long long cb_s[T + 1][KB];   // C at each column boundary
-    __shared__ long long bb_s[T + 1][KB];   // Bp at each column boundary
-    __shared__ df run0_s[KB];
-    __shared__ long long wtot_s[NW][2][KB];
-    __shared__ unsigned int wmax_s[NW];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t a = (int64_t)blockIdx.x * T;
-    const int ncols = (int)((a + T < n ? a + T : n) - a);
-    const int64_t ct = a / kCarryTile;
-
-    for (int i = tid; i <= ncols; i += NT) {
-        cp_s[i] = __ldg(colp + a + i);
-#pragma unroll
-        for (int v = 0; v < KB; v++) cb_s[i][v] = bb_s[i][v] = 0;
-    }
-    const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
-    unsigned int mx = 0;  // max |term| as float bits (NaN ranks above every finite value)
-    if (warp == 0) {  // running interval prefix at column a (compensated)
-        df acc[KB];
-#pragma unroll
-        for (int v = 0; v < KB; v++) acc[v] = df_zero();
-        for (uint32_t e = cr0 + lane; e < cr1; e += 32) {
-            float zc[KB];
-            subtree_sum<KB>(desc, x, ldx, __ldg(carry + e), zc);
-#pragma unroll
-            for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], zc[v]);
-        }
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
-            for (int o = 16; o > 0; o >>= 1)
-                acc[v] = df_add(acc[v], {__shfl_down_sync(0xffffffffu, acc[v].hi, o),
-                                         __shfl_down_sync(0xffffffffu, acc[v].lo, o)});
-            if (lane == 0) {
-                run0_s[v] = acc[v];
-                mx = max(mx, __float_as_uint(acc[v].hi) & 0x7fffffffu);
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t ebase = cp_s[0];
-    const int64_t E = (int64_t)cp_s[ncols] - ebase;
-    const int nch = (int)((E + CE - 1) / CE);
-    const int lo = tid * EPT;
-
-    // terms of this thread for one chunk: z of the source row, signed
-    float zf[EPT][KB];
-    unsigned int pmask = 0;
-    int cnt = 0;
-    auto load_chunk = [&](int c) {
-        const int64_t cs = (int64_t)c * CE;
-        const int ce = (int)(E - cs < CE ? E - cs : CE);
-        for (int e = tid; e < ce; e += NT) ent_s[e + e / EPT] = __ldg(tent + ebase + cs + e);
-        __syncthreads();
-        cnt = ce - lo < 0 ? 0 : (ce - lo > EPT ? EPT : ce - lo);
-        // The loads are issued level by level for all EPT entries at once
-        // (entry -> source row's mask and x -> first two descendants), so
-        // their latencies overlap; rows with more descendants finish in a
-        // short loop.
-        uint32_t k[EPT], dm[EPT];
-        unsigned int neg = 0;
-        pmask = 0;
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            const uint32_t w = i < cnt ? ent_s[lo + i + tid] : 0u;
-            k[i] = id_of(w);
-            if (i < cnt && (w >> kIdBits) < 2) pmask |= 1u << i;
-            if ((w >> kIdBits) & 1) neg |= 1u << i;
-        }
-        Vec<KB> x0[EPT], x1[EPT], x2[EPT];
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            dm[i] = i < cnt ? __ldg(desc + k[i]) : 0u;
-            if (i < cnt) x0[i] = ldv<KB>(x + (int64_t)k[i] * ldx);
-        }
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            const uint32_t m1 = dm[i], m2 = m1 & (m1 - 1);
-#pragma unroll
-            for (int v = 0; v < KB; v++) x1[i].v[v] = x2[i].v[v] = 0.f;
-            if (m1) x1[i] = ldv<KB>(x + (int64_t)(k[i] + __ffs(m1)) * ldx);
-            if (m2) x2[i] = ldv<KB>(x + (int64_t)(k[i] + __ffs(m2)) * ldx);
-        }
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            df acc[KB];
-#pragma unroll
-            for (int v = 0; v < KB; v++) {
-                acc[v] = {i < cnt ? x0[i].v[v] : 0.f, 0.f};
-                acc[v] = df_addf(df_addf(acc[v], x1[i].v[v]), x2[i].v[v]);
-            }
-            uint32_t m = dm[i] & (dm[i] - 1);
-            m &= m - 1;  // the first two descendants are in
-            for (; m; m &= m - 1) {
-                Vec<KB> cv = ldv<KB>(x + (int64_t)(k[i] + __ffs(m)) * ldx);
-#pragma unroll
-                for (int v = 0; v < KB; v++) acc[v] = df_addf(acc[v], cv.v[v]);
-            }
-#pragma unroll
-            for (int v = 0; v < KB; v++) {
-                const float zv = df_val(acc[v]);
-                zf[i][v] = (neg >> i & 1) ? -zv : zv;
-                mx = max(mx, __float_as_uint(zf[i][v]) & 0x7fffffffu);
-            }
-        }
-    };
-    // pass 1: the terms (kept in registers when the tile is one chunk) and max |term|
-    for (int c = 0; c < nch; c++) {
-        if (c > 0) __syncthreads();
-        load_chunk(c);
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) wmax_s[warp] = mx;
-    __syncthreads();
-#pragma unroll
-    for (int w2 = 0; w2 < NW; w2++) mx = max(mx, wmax_s[w2]);
-    const bool bad = mx >= 0x7f800000u;  // a non-finite term: the product is not defined
-    const int sexp = fx_exponent(bad ? 0u : mx, E + 2);
-    long long run0[KB];
-#pragma unroll
-    for (int v = 0; v < KB; v++) run0[v] = to_fx(run0_s[v].hi, sexp) + to_fx(run0_s[v].lo, sexp);
-
-    // pass 2: exact prefix sums, recorded at the column boundaries
-    long long chC[KB], chB[KB];
-#pragma unroll
-    for (int v = 0; v < KB; v++) chC[v] = chB[v] = 0;
-    for (int c = 0; c < nch; c++) {
-        if (nch > 1) {  // the terms of chunk c are computed again
-            __syncthreads();
-            load_chunk(c);
-        }
-        long long tC[KB], tB[KB];
-#pragma unroll
-        for (int v = 0; v < KB; v++) tC[v] = tB[v] = 0;
-#pragma unroll
-        for (int i = 0; i < EPT; i++)
-#pragma unroll
-            for (int v = 0; v < KB; v++) {
-                const long long f = to_fx(zf[i][v], sexp);
-                tC[v] += f;
-                if (pmask >> i & 1) tB[v] += f;
-            }
-        long long xC[KB], xB[KB], bC[KB], bB[KB];
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
-            long long ic = tC[v], ib = tB[v];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const long long oc = __shfl_up_sync(0xffffffffu, ic, d), ob = __shfl_up_sync(0xffffffffu, ib, d);
-                if (lane >= d) {
-                    ic += oc;
-                    ib += ob;
-                }
-            }
-            if (lane == 31) {
-                wtot_s[warp][0][v] = ic;
-                wtot_s[warp][1][v] = ib;
-            }
-            xC[v] = ic - tC[v];
-            xB[v] = ib - tB[v];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
-            bC[v] = bB[v] = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < NW; w2++) {
-                if (w2 < warp) {
-                    xC[v] += wtot_s[w2][0][v];
-                    xB[v] += wtot_s[w2][1][v];
-                }
-                bC[v] += wtot_s[w2][0][v];
-                bB[v] += wtot_s[w2][1][v];
-            }
-        }
-        if (cnt > 0) {
-            const uint32_t first = ebase + (uint32_t)((int64_t)c * CE + lo);  // boundaries b > first
-            int j0 = 0, j1 = ncols + 1;
-            while (j0 < j1) {  // first j with cp_s[j] > first
-                const int mid = (j0 + j1) >> 1;
-                if (cp_s[mid] > first) j1 = mid;
-                else j0 = mid + 1;
-            }
-            int j = j0;
-            long long rc[KB], rb[KB];
-#pragma unroll
-            for (int v = 0; v < KB; v++) {
-                rc[v] = chC[v] + xC[v];
-                rb[v] = chB[v] + xB[v];
-            }
-#pragma unroll
-            for (int i = 0; i < EPT; i++) {
-                if (i < cnt) {
-#pragma unroll
-                    for (int v = 0; v < KB; v++) {
-                        const long long f = to_fx(zf[i][v], sexp);
-                        rc[v] += f;
-                        if (pmask >> i & 1) rb[v] += f;
-                    }
-                    const uint32_t pos = first + (uint32_t)(i + 1);
-                    while (j <= ncols && cp_s[j] == pos) {
-#pragma unroll
-                        for (int v = 0; v < KB; v++) {
-                            cb_s[j][v] = rc[v];
-                            bb_s[j][v] = rb[v];
-                        }
-                        j++;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < KB; v++) {
-            chC[v] += bC[v];
-            chB[v] += bB[v];
-        }
-    }
-    __syncthreads();
-
-    double S[KB], R[KB], Dg[KB];
-#pragma unroll
-    for (int v = 0; v < KB; v++) S[v] = R[v] = Dg[v] = 0.0;
-#pragma unroll
-    for (int q = 0; q < CPT; q++) {
-        const int jl = q * NT + tid;  // consecutive threads, consecutive columns
-        if (jl >= ncols) continue;
-        const int64_t j = a + jl;
-        Vec<KB> out;
-#pragma unroll
-        for (int v = 0; v < KB; v++)
-            out.v[v] = bad ? __int_as_float(0x7fc00000) : from_fx(run0[v] + cb_s[jl + 1][v] - bb_s[jl][v], sexp);
-        if constexpr (EPI == 0) {
-            stv<KB>(y + j * ldy, out);
-        } else {
-            const float io = __ldg(pa.inv_outdeg + j);
-            const float un = 1.0f / (float)n;
-            Vec<KB> qp = ldv<KB>(pa.q_prev + j * pa.ldq), qn, xn, p0v;
-            if (pa.p0) p0v = ldv<KB>(pa.p0 + j * pa.ldp0);
-#pragma unroll
-            for (int v = 0; v < KB; v++) {
-                const float p0j = pa.p0 ? p0v.v[v] : un;
-                const float gj = pa.dangling_uniform ? un : p0j;
-                const float dl = (float)pa.sc_prev[1 * KB + v];
-                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
-                qn.v[v] = qj;
-                xn.v[v] = __fmul_rn(qj, io);
-                S[v] += (double)qj;
-                R[v] += fabs((double)qj - (double)qp.v[v]);
-                if (io == 0.0f) Dg[v] += (double)qj;
-            }
-            stv<KB>(pa.q_new + j * pa.ldq, qn);
-            stv<KB>(pa.x_new + j * pa.ldq, xn);
-        }
-    }
-    if constexpr (EPI == 1) pr_block_reduce<KB, KB>(S, R, Dg, pa, false);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
