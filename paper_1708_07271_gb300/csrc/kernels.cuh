@@ -164,12 +164,19 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
     for (int i = 0; i < RPT; i++) {
         const int r = g + i * NG;
         if (r >= own) break;
+        // the first two descendants as straight-line predicated adds (most
+        // rows have at most two), the rest in a short loop
+        const uint32_t m1 = m[i], m2 = m1 & (m1 - 1), m3 = m2 & (m2 - 1);
+        const int c1 = r + __ffs(m1), c2 = r + __ffs(m2);
         df acc[V];
 #pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = {xs[r * KB + lane * V + v], 0.f};
-        for (uint32_t mm = m[i]; mm; mm &= mm - 1) {
+        for (int v = 0; v < V; v++) {
+            acc[v] = {xs[r * KB + lane * V + v], 0.f};
+            acc[v] = df_addf(acc[v], m1 ? xs[c1 * KB + lane * V + v] : 0.f);
+            acc[v] = df_addf(acc[v], m2 ? xs[c2 * KB + lane * V + v] : 0.f);
+        }
+        for (uint32_t mm = m3; mm; mm &= mm - 1) {
             const int c = r + __ffs(mm);  // bit t -> row r + t + 1
-            if (c >= cnt) break;
 #pragma unroll
             for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xs[c * KB + lane * V + v]);
         }
@@ -188,12 +195,15 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // D_j -= z_k where it ends just before j. Intervals contribute the running
 // prefix I_j of D. A CTA owns T columns from a, a multiple of kCarryTile, and
 // starts I from the intervals open at a (the carry list), so no grid-wide
-// scan is needed. A group of G = KB/V lanes owns CPT consecutive columns: it
-// sums each column's point entries P_j in FP32 (a few terms in storage order;
-// an error there stays in y_j) and its events D_j in compensated (hi, lo)
-// form, since the prefix of D carries any error to every later column; the
-// prefix runs compensated within the group's columns on the fly and across
-// groups by one block scan.
+// scan is needed. A group of G = KB/V lanes owns CPT consecutive columns.
+// Each column's first S entries are loaded and summed by the same
+// straight-line predicated code in every lane (no divergence on the typical
+// column; longer columns finish in a short loop). Point terms P_j (a few
+// per column) sum in FP32 in storage order: an error there stays in y_j.
+// Interval events sum exactly in 64-bit fixed point (scale 2^s per CTA from
+// the CTA's own max |term| and term count), since the prefix of D carries any
+// error to every later column; the prefix across groups is an exact integer
+// block scan. y_j = P_j + I_j with I_j rounded once.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
@@ -203,7 +213,7 @@ struct GatherShape {
     static constexpr int NG = NT / G;                    // column groups per CTA
     static constexpr int CPT = G / 2 > 4 ? G / 2 : 4;    // consecutive columns per group
     static constexpr int T = NG * CPT;                   // columns per CTA (a multiple of kCarryTile)
-    static constexpr int B = 8;                          // entries loaded per batch
+    static constexpr int S = 4;                          // entry slots per column in straight-line code
 };
 
 template <int KB>
@@ -288,6 +298,25 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
     }
 }
 
+// Power-of-two fixed point used for the interval events: every term is
+// rounded once to an integer multiple of 2^-s; sums of such integers are
+// exact and associative.
+__device__ __forceinline__ int fx_exponent(unsigned int maxbits, long long terms) {
+    // s with maxabs * terms * 2^s <= 2^62 (maxabs given by its float bits)
+    if (maxbits == 0) return 0;
+    const int e_m = (int)((maxbits >> 23) & 0xff) - 126;      // maxabs < 2^e_m
+    const int e_t = 64 - __clzll((unsigned long long)terms);  // terms < 2^e_t
+    const int sexp = 62 - e_m - e_t;
+    return sexp > 100 ? 100 : (sexp < -100 ? -100 : sexp);
+}
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // |e| <= 126
+__device__ __forceinline__ long long to_fx(float v, int sexp) {
+    return __float2ll_rn(__fmul_rn(__fmul_rn(v, pow2f(sexp / 2)), pow2f(sexp - sexp / 2)));
+}
+__device__ __forceinline__ float from_fx(long long v, int sexp) {
+    return __fmul_rn(__fmul_rn(__ll2float_rn(v), pow2f(-(sexp / 2))), pow2f(-(sexp - sexp / 2)));
+}
+
 template <int KB, int V, int EPI>
 __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                                 const uint32_t* __restrict__ carry_ptr,
@@ -295,10 +324,12 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
                                                 int64_t ldz, float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
     using Sh = GatherShape<KB, V>;
-    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, B = Sh::B;
+    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
-    __shared__ df run_s[KB];
-    __shared__ df wtot_s[NW][KB];
+    __shared__ long long run_s[KB];
+    __shared__ long long wtot_s[NW][KB];
+    __shared__ unsigned int wmax_s[NW];
+    __shared__ uint32_t tile_beg_s, tile_end_s;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t a = (int64_t)blockIdx.x * T;
@@ -309,150 +340,155 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
     uint32_t cp[CPT + 1];
 #pragma unroll
     for (int q = 0; q <= CPT; q++) cp[q] = __ldg(colp + (c0 + q < end ? c0 + q : end));
+    if (threadIdx.x == 0) {
+        tile_beg_s = __ldg(colp + a);
+        tile_end_s = __ldg(colp + end);
+    }
     const int64_t ct = a / kCarryTile;
     const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
+    uint32_t w[CPT][S];
+#pragma unroll
+    for (int q = 0; q < CPT; q++)
+#pragma unroll
+        for (int t = 0; t < S; t++) w[q][t] = cp[q] + t < cp[q + 1] ? __ldg(tent + cp[q] + t) : 0u;
     asm volatile("griddepcontrol.wait;" ::: "memory");  // z (and the PageRank state) are ready
     if constexpr (EPI == 1) {
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
     }
 
-    // running interval prefix at column a: sources of intervals open there
-    if (warp == 0) {
-        df acc[KB];
+    // pass 1: the terms of up to S entries per column, uniformly for all
+    // columns (predicated straight-line code); point terms (+-z of residual /
+    // dropped ids, a few per column) sum in FP32 in storage order; for the
+    // interval events only max |term| is taken here
+    float P[CPT][V];
+    Vec<V> ev[CPT][S];
+    unsigned int mx = 0;
 #pragma unroll
-        for (int c = 0; c < KB; c++) acc[c] = df_zero();
+    for (int q = 0; q < CPT; q++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) P[q][v] = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; t++) {
+            const bool valid = cp[q] + t < cp[q + 1];
+            Vec<V> zv;
+#pragma unroll
+            for (int v = 0; v < V; v++) zv.v[v] = 0.f;
+            if (valid) zv = ldv<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
+            const uint32_t tag = w[q][t] >> kIdBits;
+            const bool point = valid && tag < 2;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
+                P[q][v] += point ? val : 0.f;
+                ev[q][t].v[v] = (valid && !point) ? val : 0.f;
+                mx = max(mx, __float_as_uint(ev[q][t].v[v]) & 0x7fffffffu);
+            }
+        }
+        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // rare: more than S entries
+            const uint32_t we = __ldg(tent + e);
+            Vec<V> zv = ldv<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+            const uint32_t tag = we >> kIdBits;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
+                if (tag < 2) P[q][v] += val;
+                else mx = max(mx, __float_as_uint(val) & 0x7fffffffu);
+            }
+        }
+    }
+    // carry sources (warp 0): terms of the running interval sum at column a
+    if (warp == 0) {
         for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) acc[c] = df_addf(acc[c], __ldg(zr + c));
-        }
-#pragma unroll
-        for (int c = 0; c < KB; c++)
-            for (int o = 16; o > 0; o >>= 1)
-                acc[c] = df_add(acc[c], {__shfl_down_sync(0xffffffffu, acc[c].hi, o),
-                                         __shfl_down_sync(0xffffffffu, acc[c].lo, o)});
-        if (lane32 == 0) {
-#pragma unroll
-            for (int c = 0; c < KB; c++) run_s[c] = acc[c];
+            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldg(zr + c)) & 0x7fffffffu);
         }
     }
-
-    // per-column point sums P (FP32, few terms, in storage order) and events D
-    // (compensated: their prefix carries any error to later columns). The
-    // group's entries are contiguous; they are loaded B at a time (independent
-    // loads in flight), and a running column sum is flushed at each boundary.
-    float P[CPT][V];
-    df D[CPT][V];
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane32 == 0) wmax_s[warp] = mx;
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < CPT; q++)
+    for (int w2 = 0; w2 < NW; w2++) mx = max(mx, wmax_s[w2]);
+    const bool bad = mx >= 0x7f800000u;  // a non-finite term: the product is not defined
+    // every partial sum below has at most (entries of the tile + carry sources) terms
+    const long long terms = (long long)(tile_end_s - tile_beg_s) + (cr1 - cr0) + 2;
+    const int sexp = fx_exponent(bad ? 0u : mx, terms);
+
+    // pass 2: exact event sums per column and the running interval prefix
+    long long D[CPT][V], tot[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) tot[v] = 0;
+#pragma unroll
+    for (int q = 0; q < CPT; q++) {
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            P[q][v] = 0.f;
-            D[q][v] = df_zero();
-        }
-    float curP[V];
-    df curD[V];
+            long long d = 0;
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-        curP[v] = 0.f;
-        curD[v] = df_zero();
+            for (int t = 0; t < S; t++) d += to_fx(ev[q][t].v[v], sexp);
+            D[q][v] = d;
+        }
+        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {
+            const uint32_t we = __ldg(tent + e);
+            if ((we >> kIdBits) < 2) continue;
+            Vec<V> zv = ldv<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) D[q][v] += to_fx(((we >> kIdBits) & 1) ? -zv.v[v] : zv.v[v], sexp);
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) tot[v] += D[q][v];
     }
-    int q = 0;
-    uint32_t nextb = cp[1];
-    auto flush = [&]() {
+    if (warp == 0) {
+        long long acc[KB];
 #pragma unroll
-        for (int qq = 0; qq < CPT; qq++)
-            if (qq == q) {
+        for (int c = 0; c < KB; c++) acc[c] = 0;
+        for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
+            const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-                for (int v = 0; v < V; v++) {
-                    P[qq][v] = curP[v];
-                    D[qq][v] = curD[v];
-                }
-            }
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            curP[v] = 0.f;
-            curD[v] = df_zero();
+            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldg(zr + c), sexp);
         }
-        q++;
-        uint32_t nb = cp[CPT];
 #pragma unroll
-        for (int t = CPT - 1; t >= 1; t--)
-            if (q + 1 == t) nb = cp[t];
-        nextb = nb;
-    };
-    const uint32_t eend = cp[CPT];
-    for (uint32_t base = cp[0]; base < eend; base += B) {
-        uint32_t w[B];
-        Vec<V> zv[B];
-#pragma unroll
-        for (int i = 0; i < B; i++) w[i] = base + i < eend ? __ldg(tent + base + i) : 0u;
-#pragma unroll
-        for (int i = 0; i < B; i++)
-            if (base + i < eend) zv[i] = ldv<V>(z + (int64_t)id_of(w[i]) * ldz + lane * V);
-#pragma unroll
-        for (int i = 0; i < B; i++) {
-            if (base + i >= eend) break;
-            while (base + i >= nextb) flush();
-            const uint32_t tag = w[i] >> kIdBits;
-            if (tag < 2) {
-#pragma unroll
-                for (int v = 0; v < V; v++) curP[v] += (tag & 1) ? -zv[i].v[v] : zv[i].v[v];
-            } else {
-#pragma unroll
-                for (int v = 0; v < V; v++) curD[v] = df_addf(curD[v], (tag & 1) ? -zv[i].v[v] : zv[i].v[v]);
-            }
+        for (int c = 0; c < KB; c++) {
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            if (lane32 == 0) run_s[c] = acc[c];
         }
     }
-    flush();  // the last column that has entries; later columns stay zero
-
-    // exclusive prefix of the group totals of D across the block (compensated)
-    df tot[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-        tot[v] = df_zero();
-#pragma unroll
-        for (int qq = 0; qq < CPT; qq++) tot[v] = df_add(tot[v], D[qq][v]);
-    }
-    df inc[V], ex[V];
+    // exclusive prefix of the group totals across the block (exact)
+    long long inc[V];
 #pragma unroll
     for (int v = 0; v < V; v++) inc[v] = tot[v];
 #pragma unroll
     for (int d = G; d < 32; d <<= 1)
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            df o = df_shfl_up(inc[v], d);
-            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
+            const long long o = __shfl_up_sync(0xffffffffu, inc[v], d);
+            if (lane32 >= d) inc[v] += o;
         }
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-        df o = df_shfl_up(inc[v], G);
-        ex[v] = lane32 >= G ? o : df_zero();
-    }
     if (lane32 >= 32 - G) {
 #pragma unroll
         for (int v = 0; v < V; v++) wtot_s[warp][lane * V + v] = inc[v];
     }
     __syncthreads();
-    df run[V];
+    long long run[V];
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        df r = run_s[lane * V + v];
-        for (int w2 = 0; w2 < warp; w2++) r = df_add(r, wtot_s[w2][lane * V + v]);
-        run[v] = df_add(r, ex[v]);
+        long long r = run_s[lane * V + v] + inc[v] - tot[v];
+#pragma unroll
+        for (int w2 = 0; w2 < NW; w2++)
+            if (w2 < warp) r += wtot_s[w2][lane * V + v];
+        run[v] = r;
     }
 
-    double S[V], R[V], Dg[V];
+    double Ssum[V], R[V], Dg[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
+    for (int v = 0; v < V; v++) Ssum[v] = R[v] = Dg[v] = 0.0;
 #pragma unroll
-    for (int qq = 0; qq < CPT; qq++) {
-        const int64_t j = c0 + qq;
+    for (int q = 0; q < CPT; q++) {
+        const int64_t j = c0 + q;
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] = df_add(run[v], D[qq][v]);
-            out.v[v] = df_val(df_addf(run[v], P[qq][v]));
+            run[v] += D[q][v];
+            out.v[v] = bad ? __int_as_float(0x7fc00000) : __fadd_rn(P[q][v], from_fx(run[v], sexp));
         }
         if (j >= end) continue;
         if constexpr (EPI == 0) {
@@ -469,14 +505,14 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
                 const float dl = (float)pa.sc_prev[1 * KB + lane * V + v];
                 const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
                 qn.v[v] = qj;
-                S[v] += (double)qj;
+                Ssum[v] += (double)qj;
                 R[v] += fabs((double)qj - (double)qp.v[v]);
                 if (io == 0.0f) Dg[v] += (double)qj;
             }
             stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
         }
     }
-    if constexpr (EPI == 1) pr_block_reduce<KB, V>(S, R, Dg, pa, false);
+    if constexpr (EPI == 1) pr_block_reduce<KB, V>(Ssum, R, Dg, pa, false);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
