@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // the CTA's own max |term| and term count), since the prefix of D carries any
 // error to every later column; the prefix across groups is an exact integer
 // block scan. y_j = P_j + I_j with I_j rounded once.
+// The kernel is launched so that it may start while the chain kernel is
+// still running (programmatic dependent launch): it reads only the structure
+// before griddepcontrol.wait, and reads z afterwards through L2 (ld.cg), never
+// through the read-only non-coherent path, since z changes during its lifetime.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
@@ -320,8 +324,8 @@ __device__ __forceinline__ float from_fx(long long v, int sexp) {
 template <int KB, int V, int EPI>
 __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                                 const uint32_t* __restrict__ carry_ptr,
-                                                const uint32_t* __restrict__ carry, const float* __restrict__ z,
-                                                int64_t ldz, float* __restrict__ y, int64_t ldy, int64_t n,
+                                                const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
+                                                float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
             Vec<V> zv;
 #pragma unroll
             for (int v = 0; v < V; v++) zv.v[v] = 0.f;
-            if (valid) zv = ldv<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
+            if (valid) zv = ldv_cg<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
             const uint32_t tag = w[q][t] >> kIdBits;
             const bool point = valid && tag < 2;
 #pragma unroll
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         }
         for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // rare: more than S entries
             const uint32_t we = __ldg(tent + e);
-            Vec<V> zv = ldv<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+            Vec<V> zv = ldv_cg<V>(z + (int64_t)id_of(we) * ldz + lane * V);
             const uint32_t tag = we >> kIdBits;
 #pragma unroll
             for (int v = 0; v < V; v++) {
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldg(zr + c)) & 0x7fffffffu);
+            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldcg(zr + c)) & 0x7fffffffu);
         }
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {
             const uint32_t we = __ldg(tent + e);
             if ((we >> kIdBits) < 2) continue;
-            Vec<V> zv = ldv<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+            Vec<V> zv = ldv_cg<V>(z + (int64_t)id_of(we) * ldz + lane * V);
 #pragma unroll
             for (int v = 0; v < V; v++) D[q][v] += to_fx(((we >> kIdBits) & 1) ? -zv.v[v] : zv.v[v], sexp);
         }
@@ -444,7 +448,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldg(zr + c), sexp);
+            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldcg(zr + c), sexp);
         }
 #pragma unroll
         for (int c = 0; c < KB; c++) {
