@@ -91,6 +91,24 @@ __device__ __forceinline__ Vec<V> ldv_cg(const float* p) {
     return r;
 }
 
+// Coherent load cached in L1 (ld.global.ca): for data written by the
+// previous kernel when this kernel may start before that kernel ends
+// (programmatic dependent launch) -- read only after griddepcontrol.wait.
+template <int V>
+__device__ __forceinline__ Vec<V> ldv_ca(const float* p) {
+    Vec<V> r;
+    if constexpr (V == 4) {
+        float4 t = __ldca(reinterpret_cast<const float4*>(p));
+        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else if constexpr (V == 2) {
+        float2 t = __ldca(reinterpret_cast<const float2*>(p));
+        r.v[0] = t.x; r.v[1] = t.y;
+    } else {
+        r.v[0] = __ldca(p);
+    }
+    return r;
+}
+
 template <int V>
 __device__ __forceinline__ void stv(float* p, const Vec<V>& r) {
     if constexpr (V == 4) {

@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // block scan. y_j = P_j + I_j with I_j rounded once.
 // The kernel is launched so that it may start while the chain kernel is
 // still running (programmatic dependent launch): it reads only the structure
-// before griddepcontrol.wait, and reads z afterwards through L2 (ld.cg), never
-// through the read-only non-coherent path, since z changes during its lifetime.
+// before griddepcontrol.wait, and reads z afterwards with coherent loads
+// (ld.global.ca), never through the read-only non-coherent path, since z
+// changes during the kernel's lifetime.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
 // ---------------------------------------------------------------------------
 template <int KB, int V>
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
             Vec<V> zv;
 #pragma unroll
             for (int v = 0; v < V; v++) zv.v[v] = 0.f;
-            if (valid) zv = ldv_cg<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
+            if (valid) zv = ldv_ca<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
             const uint32_t tag = w[q][t] >> kIdBits;
             const bool point = valid && tag < 2;
 #pragma unroll
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         }
         for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // rare: more than S entries
             const uint32_t we = __ldg(tent + e);
-            Vec<V> zv = ldv_cg<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+            Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
             const uint32_t tag = we >> kIdBits;
 #pragma unroll
             for (int v = 0; v < V; v++) {
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldcg(zr + c)) & 0x7fffffffu);
+            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldca(zr + c)) & 0x7fffffffu);
         }
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {
             const uint32_t we = __ldg(tent + e);
             if ((we >> kIdBits) < 2) continue;
-            Vec<V> zv = ldv_cg<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+            Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
 #pragma unroll
             for (int v = 0; v < V; v++) D[q][v] += to_fx(((we >> kIdBits) & 1) ? -zv.v[v] : zv.v[v], sexp);
         }
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
             const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldcg(zr + c), sexp);
+            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldca(zr + c), sexp);
         }
 #pragma unroll
         for (int c = 0; c < KB; c++) {
