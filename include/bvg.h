@@ -162,6 +162,26 @@ int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int
  * no atomics (deterministic). x, y: device n x k. Asynchronous. */
 int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
+/* Same product as bvg_spmv_xA, for callers that must not allocate device
+ * memory after set-up (a caller whose memory is owned by another allocator's
+ * pool, a latency-critical loop that cannot afford cudaMalloc's implicit
+ * synchronisation, an embedder that fixes the library's footprint at load
+ * time). The paper has no counterpart: this is a property of this library.
+ * It allocates nothing: the pushed weights live in a fixed 16 MiB device
+ * array (4,194,304 floats) compiled into the library, which every GPU that
+ * loads the library holds until the process exits. Requires n <= 4,194,304;
+ * right-hand sides are processed in column blocks of at most
+ * min(32, 4194304 / n); a larger n returns BVG_ERR_UNSUPPORTED. The first
+ * call on each device looks up that array's device address (host-side, with
+ * that device current) and caches it: make that first call before any stream
+ * capture. Every call on a device shares the one array and each call
+ * overwrites the part it uses before reading it, so nothing carries over;
+ * calls that may overlap on the GPU (different streams, or in flight
+ * together) race on it and must be serialised by the caller. x, y: device
+ * n x k, leading dimension ld. Asynchronous on `stream`. Errors:
+ * INVALID_ARG, UNSUPPORTED, CUDA. */
+int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+
 /* Same as bvg_spmv_xA with x and y in HOST memory (pinned or pageable):
  * copies x to device scratch, runs the product, copies y back, and
  * synchronises `stream` before returning. ld == k. */

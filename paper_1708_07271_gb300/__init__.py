@@ -34,7 +34,7 @@ EXPORTED = [
     "bvg_encode", "bvg_decode", "bvg_stats", "bvg_get_refs", "bvg_host_size", "bvg_upload", "bvg_spmv_Ax",
     "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
     "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
-    "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get",
+    "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get", "bvg_spmv_xA_noalloc",
 ]
 
 
@@ -104,6 +104,7 @@ def load(build_if_needed: bool = True):
             "bvg_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_spmv_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_spmv_xA_host": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+            "bvg_spmv_xA_noalloc": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_pagerank": ([_P, ctypes.POINTER(PrParams), _P, _P, _I32, _P, ctypes.POINTER(_I32),
                               _P, _P], ctypes.c_int),
             "bvg_dev_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
@@ -270,6 +271,17 @@ def bvg_spmv_xA(g: DevGraph, x, y, stream=None):
     if _km(y, g.n) != (k, ld):
         raise ValueError("x and y must have the same shape and strides")
     _check(load().bvg_spmv_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_spmv_xA")
+    return y
+
+
+def bvg_spmv_xA_noalloc(g: DevGraph, x, y, stream=None):
+    """y = x A using only the library's fixed device scratch (no allocation)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    if _km(y, g.n) != (k, ld):
+        raise ValueError("x and y must have the same shape and strides")
+    _check(load().bvg_spmv_xA_noalloc(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
+           "bvg_spmv_xA_noalloc")
     return y
 
 
