@@ -201,6 +201,17 @@ int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host,
 int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0, const float* p_init,
                  int32_t k, float* p_out, int32_t* iters_out, double* resid_out, void* stream);
 
+/* Launch configuration of a device graph (what bvg_autotune chooses; the
+ * results of every setting are the same up to the product tolerance). */
+typedef struct {
+    int32_t pull_tile;      /* rows per CTA of the pull kernel: power of two in [64, 2048] (default 512) */
+    int32_t pull_prefix;    /* pull interval sums from a prefix of x: -1 auto (mean interval >= 32), 0 off, 1 on */
+    int32_t prefix_min_len; /* with the prefix on, intervals at least this long use it (default 16) */
+    int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */
+} bvg_launch_config;
+int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
+int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
+
 /* Number of rows n of a device graph. */
 int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);
 

@@ -35,6 +35,7 @@ EXPORTED = [
     "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
     "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
     "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get", "bvg_spmv_xA_noalloc",
+    "bvg_get_config", "bvg_set_config",
 ]
 
 
@@ -69,6 +70,10 @@ class LayoutView(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "words", "col_entries", "carry_tiles", "carry_entries",
                                       "carry_tile_cols")] + \
                [(f, _P) for f in ("meta", "desc", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")]
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -119,6 +124,8 @@ def load(build_if_needed: bool = True):
             "bvg_trace_enable": ([_P, ctypes.c_int], ctypes.c_int),
             "bvg_dev_layout": ([_P, ctypes.POINTER(LayoutInfo)], ctypes.c_int),
             "bvg_layout_view_get": ([_P, ctypes.POINTER(LayoutView)], ctypes.c_int),
+            "bvg_get_config": ([_P, ctypes.POINTER(LaunchConfig)], ctypes.c_int),
+            "bvg_set_config": ([_P, ctypes.POINTER(LaunchConfig)], ctypes.c_int),
             "bvg_trace_read": ([_P, ctypes.POINTER(TraceEntry), _I32, ctypes.POINTER(_I32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -378,6 +385,21 @@ def bvg_dev_layout(g: DevGraph) -> dict:
     info = LayoutInfo()
     _check(load().bvg_dev_layout(g.ptr, ctypes.byref(info)), "bvg_dev_layout")
     return {f: getattr(info, f) for f, _ in LayoutInfo._fields_}
+
+
+def bvg_get_config(g: DevGraph) -> dict:
+    c = LaunchConfig()
+    _check(load().bvg_get_config(g.ptr, ctypes.byref(c)), "bvg_get_config")
+    return {f: getattr(c, f) for f, _ in LaunchConfig._fields_}
+
+
+def bvg_set_config(g: DevGraph, **changes) -> dict:
+    """Updates fields of the launch configuration; returns the new one."""
+    cur = bvg_get_config(g)
+    cur.update(changes)
+    c = LaunchConfig(**cur)
+    _check(load().bvg_set_config(g.ptr, ctypes.byref(c)), "bvg_set_config")
+    return cur
 
 
 def bvg_trace_enable(g: DevGraph, enable: bool = True):

@@ -97,7 +97,7 @@ static int gather_tile(int kb, int v, const LaunchCfg&) {
 // the previous kernel on the stream finishes; it waits (griddepcontrol.wait)
 // before reading that kernel's output.
 template <class... KArgs, class... Args>
-static void launch_pdl(void (*kernel)(KArgs...), int64_t grid, int block, cudaStream_t st, Args... args) {
+static void launch_pdl(int pdl, void (*kernel)(KArgs...), int64_t grid, int block, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
@@ -107,7 +107,7 @@ static void launch_pdl(void (*kernel)(KArgs...), int64_t grid, int block, cudaSt
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -154,13 +154,32 @@ struct TraceScope {
 
 // ----------------------------------------------------------------- launchers
 template <int KB, int V>
-static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy, cudaStream_t st) {
+static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy, bool prefix,
+                        cudaStream_t st) {
+    PrefixArgs pf{};
+    if (prefix) {
+        using Sh = PrefixShape<KB, V>;
+        const int64_t nb = (g->n + 1 + Sh::PB - 1) / Sh::PB;
+        float* lhi = g->s.pre[0];
+        float* llo = g->s.pre[1];
+        float* bhi = g->s.pre[2];
+        float* blo = g->s.pre[3];
+        {
+            TraceScope ts(g, "prefix_local", st);
+            k_prefix_local<KB, V><<<(unsigned)nb, 256, 0, st>>>(x, ldx, lhi, llo, bhi, blo, g->n);
+        }
+        {
+            TraceScope ts(g, "prefix_blocks", st);
+            k_prefix_blocks<KB><<<1, 256, 0, st>>>(bhi, blo, (int)nb);
+        }
+        pf = PrefixArgs{lhi, llo, bhi, blo, Sh::PB, g->cfg.prefix_min_len};
+    }
     const int tile = pull_tile(KB, g->cfg);
     const size_t smem = (size_t)(tile + kHalo) * KB * sizeof(df);
     set_smem(k_pull<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pull", st);
-    k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile);
+    k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile, pf);
 }
 
 template <int KB, int V>
@@ -177,7 +196,7 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
-    launch_pdl(k_gather<KB, V, 0>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
+    launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 0>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
                (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz, y, ldy,
                g->n, pa);
 }
@@ -186,7 +205,7 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
-    launch_pdl(k_gather<KB, V, 1>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
+    launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 1>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
                (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz,
                (float*)nullptr, (int64_t)0, g->n, pa);
 }
@@ -222,6 +241,28 @@ static int ensure_z(bvg_dev_graph* g, int kb) {
     return BVG_OK;
 }
 
+// Prefix scratch for kb columns: L hi/lo ((n+1) x kb) and block starts.
+static int ensure_prefix(bvg_dev_graph* g, int kb) {
+    if (g->s.pre_kcap >= kb) return BVG_OK;
+    for (float*& b : g->s.pre) {
+        if (b) cudaFree(b);
+        b = nullptr;
+    }
+    g->s.pre_kcap = 0;
+    const int64_t nb = (g->n + 1 + 7) / 8 + 1;  // enough blocks for the smallest block (8 rows x 1 group)
+    const size_t lbytes = (size_t)(g->n + 1) * kb * sizeof(float), bbytes = (size_t)nb * kb * sizeof(float);
+    int rc;
+    if ((rc = dev_alloc((void**)&g->s.pre[0], lbytes, nullptr)) || (rc = dev_alloc((void**)&g->s.pre[1], lbytes, nullptr)) ||
+        (rc = dev_alloc((void**)&g->s.pre[2], bbytes, nullptr)) || (rc = dev_alloc((void**)&g->s.pre[3], bbytes, nullptr)))
+        return rc;
+    g->s.pre_kcap = kb;
+    return BVG_OK;
+}
+
+static bool use_prefix(const bvg_dev_graph* g) {
+    return g->cfg.pull_prefix == 1 || (g->cfg.pull_prefix < 0 && g->mean_interval >= 32.0);
+}
+
 static int64_t max_grid(const bvg_dev_graph* g) {
     // largest grid of any launch that writes per-CTA partials
     int64_t best = 0;
@@ -244,12 +285,12 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
     if (rc) return rc;
     if (g->s.pr_kcap < kb) {
         drop_pr_graph(g);
-        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.xb[0], &g->s.xb[1], &g->s.p0}) {
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
             if (*b) cudaFree(*b);
             *b = nullptr;
         }
         g->s.pr_kcap = 0;
-        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.xb[0], &g->s.xb[1], &g->s.p0}) {
+        for (float** b : {&g->s.q[0], &g->s.q[1], &g->s.p0}) {
             rc = dev_alloc((void**)b, (size_t)g->n * kb * sizeof(float), nullptr);
             if (rc) return rc;
         }
@@ -300,6 +341,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->n = n;
         g->m = hg->m;
         g->nwords = (int64_t)L->ent.size();
+        g->mean_interval = hg->stats.intervals ? (double)hg->stats.interval_members / (double)hg->stats.intervals : 0.0;
         g->ntent = (int64_t)L->tent.size();
         g->ncarry = (int64_t)L->carry.size();
         if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
@@ -333,7 +375,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
     void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
-                    g->s.hy, g->s.p0, g->s.xb[0], g->s.xb[1]};
+                    g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3]};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -401,6 +443,29 @@ extern "C" int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m) {
     return BVG_OK;
 }
 
+extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
+    if (!g || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_get_config: NULL argument");
+    out->pull_tile = g->cfg.pull_tile;
+    out->pull_prefix = g->cfg.pull_prefix;
+    out->prefix_min_len = g->cfg.prefix_min_len;
+    out->gather_pdl = g->cfg.gather_pdl;
+    return BVG_OK;
+}
+
+extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
+    if (!g || !in) return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: NULL argument");
+    if (in->pull_tile < 64 || in->pull_tile > 2048 || (in->pull_tile & (in->pull_tile - 1)) ||
+        in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
+        in->gather_pdl > 1)
+        return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
+                                         "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}");
+    g->cfg.pull_tile = in->pull_tile;
+    g->cfg.pull_prefix = in->pull_prefix;
+    g->cfg.prefix_min_len = in->prefix_min_len;
+    g->cfg.gather_pdl = in->gather_pdl;
+    return BVG_OK;
+}
+
 extern "C" int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out) {
     if (!g || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_dev_layout: NULL argument");
     out->n = g->n;
@@ -422,10 +487,13 @@ extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int
     if ((rc = check_vec(g, x, "x")) || (rc = check_vec(g, y, "y"))) return rc;
     if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_Ax: x and y must not alias");
     cudaStream_t st = (cudaStream_t)stream;
+    bvg_dev_graph* gm = const_cast<bvg_dev_graph*>(g);
+    const bool prefix = use_prefix(g);
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(k - c0);
+        if (prefix && (rc = ensure_prefix(gm, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
-        BVG_KV_CASES(launch_pull, g, x + c0, ld, y + c0, ld, st);
+        BVG_KV_CASES(launch_pull, g, x + c0, ld, y + c0, ld, prefix, st);
         c0 += kb;
     }
     BVG_CUDA_TRY(cudaGetLastError());

@@ -77,11 +77,10 @@ namespace bvg {
 
 // Launch configuration of the product kernels (autotuned per graph and k).
 struct LaunchCfg {
-    int pull_tile = 512;    // rows per CTA of the pull kernel
-    int pull_threads = 256;
-    int chain_tile = 1024;  // rows per CTA of the push-chain kernel
-    int gather_tile = 1024; // columns per CTA of the push-gather kernel
-    int gather_threads = 256;
+    int pull_tile = 512;        // rows per CTA of the pull kernel
+    int pull_prefix = -1;       // interval sums of the pull from the prefix of x: -1 auto, 0 off, 1 on
+    int prefix_min_len = 16;    // with the prefix on, intervals at least this long use it
+    int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
 };
 
 struct DevScratch {
@@ -91,7 +90,8 @@ struct DevScratch {
     void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
     double* partial = nullptr;          // per-CTA FP64 partial sums
     unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction)
-    float* xb[2] = {nullptr, nullptr};  // PageRank pushed inputs q / outdeg, n x pr_kcap
+    float* pre[4] = {nullptr, nullptr, nullptr, nullptr};  // prefix of x: L hi/lo ((n+1) x kcap), B hi/lo
+    int64_t pre_kcap = 0;
     void* host_state = nullptr;         // pinned host copy of the state + residuals
     float* hx = nullptr;                // device staging for the host-buffer product
     float* hy = nullptr;
@@ -131,6 +131,7 @@ struct bvg_dev_graph {
     uint32_t* carry = nullptr;      // source rows of intervals open at a carry-tile start
     int64_t ncarry = 0;
     float* inv_outdeg = nullptr;    // 1/|v_i|, 0 for rows without successors
+    double mean_interval = 0.0;     // mean interval length (prefix policy)
     int64_t bytes = 0;
     bvg::LaunchCfg cfg;
     bvg::DevScratch s;

@@ -37,20 +37,178 @@ struct PrArgs {
 
 
 // ---------------------------------------------------------------------------
+// Prefix of x (for interval sums of the pull): P(j) = sum_{t < j} x_t, kept
+// blocked and compensated: L[j] (hi, lo) is the exclusive prefix inside a
+// block of PrefixShape::PB rows, B[b] (hi, lo) the prefix of the block
+// starts; P(j) = B[j / PB] + L[j], j = 0..n. An interval sum is then
+// P(s + len) - P(s), two differences of compensated values.
+// ---------------------------------------------------------------------------
+template <int KB, int V>
+struct PrefixShape {
+    static constexpr int G = KB / V, NG = 256 / G, RPT = 8, PB = NG * RPT;
+};
+
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_prefix_local(const float* __restrict__ x, int64_t ldx, float* __restrict__ lhi,
+                                                      float* __restrict__ llo, float* __restrict__ bhi,
+                                                      float* __restrict__ blo, int64_t n) {
+    using Sh = PrefixShape<KB, V>;
+    constexpr int G = Sh::G, RPT = Sh::RPT, PB = Sh::PB;
+    __shared__ df wtot_s[8][KB];
+    const int g = threadIdx.x / G, lane = threadIdx.x % G;
+    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b0 = (int64_t)blockIdx.x * PB, r0 = b0 + (int64_t)g * RPT;
+    df tot[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) tot[v] = df_zero();
+    float xv[RPT][V];
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+        Vec<V> t;
+#pragma unroll
+        for (int v = 0; v < V; v++) t.v[v] = 0.f;
+        if (r0 + i < n) t = ldv<V>(x + (r0 + i) * ldx + lane * V);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            xv[i][v] = t.v[v];
+            tot[v] = df_addf(tot[v], t.v[v]);
+        }
+    }
+    df inc[V], ex[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) inc[v] = tot[v];
+#pragma unroll
+    for (int d = G; d < 32; d <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            df o = df_shfl_up(inc[v], d);
+            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
+        }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        df o = df_shfl_up(inc[v], G);
+        ex[v] = lane32 >= G ? o : df_zero();
+    }
+    if (lane32 >= 32 - G)
+#pragma unroll
+        for (int v = 0; v < V; v++) wtot_s[warp][lane * V + v] = inc[v];
+    __syncthreads();
+    df run[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        df r = df_zero();
+        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w][lane * V + v]);
+        run[v] = df_add(r, ex[v]);
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; i++) {
+        if (r0 + i <= n) {
+            Vec<V> h, l;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                h.v[v] = run[v].hi;
+                l.v[v] = run[v].lo;
+            }
+            stv<V>(lhi + (r0 + i) * KB + lane * V, h);
+            stv<V>(llo + (r0 + i) * KB + lane * V, l);
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++) run[v] = df_addf(run[v], xv[i][v]);
+    }
+    if (threadIdx.x >= 256 - G) {  // the last group holds the block total
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            bhi[(int64_t)blockIdx.x * KB + lane * V + v] = run[v].hi;
+            blo[(int64_t)blockIdx.x * KB + lane * V + v] = run[v].lo;
+        }
+    }
+}
+
+// Exclusive prefix over the nb block totals (one CTA), in place: B[b].
+template <int KB>
+__global__ void __launch_bounds__(256) k_prefix_blocks(float* __restrict__ bhi, float* __restrict__ blo, int nb) {
+    __shared__ df wtot_s[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (nb + 255) / 256, b0 = threadIdx.x * per;
+    for (int c = 0; c < KB; c++) {
+        df t = df_zero();
+        for (int b = b0; b < b0 + per && b < nb; b++) t = df_add(t, {bhi[(int64_t)b * KB + c], blo[(int64_t)b * KB + c]});
+        df inc = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            df o = df_shfl_up(inc, d);
+            if (lane >= d) inc = df_add(o, inc);
+        }
+        df o = df_shfl_up(inc, 1);
+        const df ex = lane >= 1 ? o : df_zero();
+        if (lane == 31) wtot_s[warp] = inc;
+        __syncthreads();
+        df r = df_zero();
+        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w]);
+        r = df_add(r, ex);
+        for (int b = b0; b < b0 + per && b < nb; b++) {
+            const df cur = {bhi[(int64_t)b * KB + c], blo[(int64_t)b * KB + c]};
+            bhi[(int64_t)b * KB + c] = r.hi;
+            blo[(int64_t)b * KB + c] = r.lo;
+            r = df_add(r, cur);
+        }
+        __syncthreads();
+    }
+}
+
+struct PrefixArgs {
+    const float* lhi;  // (n+1) x KB
+    const float* llo;
+    const float* bhi;  // nb x KB (block starts)
+    const float* blo;
+    int block;         // PB, rows per prefix block
+    int min_len;       // intervals at least this long use the prefix
+};
+
+// ---------------------------------------------------------------------------
 // Pull: y = A x^T (Sec. 4). A CTA owns rows [a, a + tile). It first forms the
 // correction sums c_i = sum_j A'_ij x_j for rows [a - kHalo, a + tile) into
 // shared memory (dropped ids subtract, residual ids add, an interval (s, len)
-// adds x_s + ... + x_{s+len-1}), then resolves each owned row's chain
+// adds x_s + ... + x_{s+len-1}: summed directly, or from the prefix of x when
+// len >= min_len), then resolves each owned row's chain
 // y_i = c_i + y_{r_i} = c_i + c_{r_i} + c_{r_{r_i}} + ... with at most
 // max_chain links, all inside the CTA (a chain never leaves kHalo rows).
 // The sums are compensated (hi, lo) pairs; the chain is added from its root
-// outwards, i.e. in the association of the sequential algorithm.
+// outwards, i.e. in the association of the sequential algorithm. A row's
+// first S words are loaded by straight-line predicated code.
 // ---------------------------------------------------------------------------
+template <int KB, int V>
+__device__ __forceinline__ void pull_interval(df (&acc)[V], uint32_t s0, uint32_t len, const float* __restrict__ x,
+                                              int64_t ldx, int lane, const PrefixArgs& pf) {
+    if (pf.lhi && len >= (uint32_t)pf.min_len) {
+        const uint32_t e0 = s0 + len;
+        const int64_t bs = s0 / pf.block, be = e0 / pf.block;
+        Vec<V> lsh = ldv<V>(pf.lhi + (int64_t)s0 * KB + lane * V), lsl = ldv<V>(pf.llo + (int64_t)s0 * KB + lane * V);
+        Vec<V> leh = ldv<V>(pf.lhi + (int64_t)e0 * KB + lane * V), lel = ldv<V>(pf.llo + (int64_t)e0 * KB + lane * V);
+        Vec<V> bsh = ldv<V>(pf.bhi + bs * KB + lane * V), bsl = ldv<V>(pf.blo + bs * KB + lane * V);
+        Vec<V> beh = ldv<V>(pf.bhi + be * KB + lane * V), bel = ldv<V>(pf.blo + be * KB + lane * V);
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const df dB = df_add({beh.v[v], bel.v[v]}, df_neg({bsh.v[v], bsl.v[v]}));
+            const df dL = df_add({leh.v[v], lel.v[v]}, df_neg({lsh.v[v], lsl.v[v]}));
+            acc[v] = df_add(acc[v], df_add(dB, dL));
+        }
+    } else {
+        for (uint32_t t = 0; t < len; t++) {
+            Vec<V> xv = ldv<V>(x + (int64_t)(s0 + t) * ldx + lane * V);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
+        }
+    }
+}
+
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ rowp,
                                               const uint32_t* __restrict__ ent, const float* __restrict__ x,
-                                              int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n, int tile) {
+                                              int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n, int tile,
+                                              PrefixArgs pf) {
     constexpr int G = KB / V;
+    constexpr int S = 4;
     extern __shared__ float4 smem_pull[];
     df* c = reinterpret_cast<df*>(smem_pull);  // [(tile + kHalo) * KB]
     const int NG = blockDim.x / G;
@@ -66,21 +224,37 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = df_zero();
         const uint32_t w0 = __ldg(rowp + i), w1 = __ldg(rowp + i + 1);
-        for (uint32_t w = w0; w < w1; w++) {
-            const uint32_t word = __ldg(ent + w);
+        uint32_t w[S];
+#pragma unroll
+        for (int t = 0; t < S; t++) w[t] = w0 + t < w1 ? __ldg(ent + w0 + t) : 0u;
+        Vec<V> xs[S];
+#pragma unroll
+        for (int t = 0; t < S; t++) {
+#pragma unroll
+            for (int v = 0; v < V; v++) xs[t].v[v] = 0.f;
+            if (w0 + t < w1 && tag_of(w[t]) < 2) xs[t] = ldv<V>(x + (int64_t)id_of(w[t]) * ldx + lane * V);
+        }
+#pragma unroll
+        for (int t = 0; t < S; t++) {
+            const uint32_t tag = tag_of(w[t]);
+#pragma unroll
+            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], tag == kTagMinus ? -xs[t].v[v] : xs[t].v[v]);
+            if (w0 + t < w1 && tag == kTagIvS) {
+                const uint32_t len = id_of(t + 1 < S ? w[t + 1 < S ? t + 1 : t] : __ldg(ent + w0 + t + 1));
+                pull_interval<KB, V>(acc, id_of(w[t]), len, x, ldx, lane, pf);
+            }
+        }
+        // words past the first S (a length word right after slot S-1 is skipped)
+        for (uint32_t q = w0 + S; q < w1; q++) {
+            const uint32_t word = __ldg(ent + q);
             const uint32_t tag = tag_of(word), id = id_of(word);
             if (tag == kTagPlus || tag == kTagMinus) {
                 Vec<V> xv = ldv<V>(x + (int64_t)id * ldx + lane * V);
 #pragma unroll
                 for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], tag == kTagPlus ? xv.v[v] : -xv.v[v]);
             } else if (tag == kTagIvS) {
-                const uint32_t len = id_of(__ldg(ent + w + 1));
-                w++;
-                for (uint32_t t = 0; t < len; t++) {
-                    Vec<V> xv = ldv<V>(x + (int64_t)(id + t) * ldx + lane * V);
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
-                }
+                pull_interval<KB, V>(acc, id, id_of(__ldg(ent + q + 1)), x, ldx, lane, pf);
+                q++;
             }
         }
 #pragma unroll
@@ -101,9 +275,9 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            df s = c[(int64_t)idx[len - 1] * KB + lane * V + v];
-            for (int t = len - 2; t >= 0; t--) s = df_add(c[(int64_t)idx[t] * KB + lane * V + v], s);
-            out.v[v] = df_val(s);
+            df sacc = c[(int64_t)idx[len - 1] * KB + lane * V + v];
+            for (int t = len - 2; t >= 0; t--) sacc = df_add(c[(int64_t)idx[t] * KB + lane * V + v], sacc);
+            out.v[v] = df_val(sacc);
         }
         stv<V>(y + (lo + r) * ldy + lane * V, out);
     }

@@ -261,3 +261,46 @@ def test_full_size_pagerank(web862k):
     assert rc == bvg.BVG_OK and res[0] < 1e-8, (rc, it, res)
     pstar, it_o, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-12, max_iter=2000)
     assert l1(p.cpu().numpy(), pstar) <= 1e-6
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("prefix", [0, 1])
+def test_pull_with_and_without_prefix_of_x(name, prefix):
+    """Interval sums of the pull from the device prefix of x (blocked,
+    compensated) or summed directly: both match the oracle."""
+    g, hg, dg, ref = graph(name)
+    old = bvg.bvg_get_config(dg)
+    bvg.bvg_set_config(dg, pull_prefix=prefix, prefix_min_len=4)
+    try:
+        for k in (1, 8, 33):
+            x = synth.rhs(g.n, k, synth.seed_for(1, 300 + k))
+            x64 = x.astype(np.float64)
+            xt = torch.from_numpy(x).cuda()
+            y = torch.full_like(xt, float("nan"))
+            bvg.bvg_spmv_Ax(dg, xt, y)
+            check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                        oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), f"Ax prefix={prefix} {name} k={k}")
+    finally:
+        bvg.bvg_set_config(dg, **old)
+
+
+def test_launch_config_variants_same_results():
+    g, hg, dg, ref = graph("tiny_web")
+    xt = torch.from_numpy(synth.rhs(g.n, 2, 77)).cuda()
+    base_xa, base_ax = torch.empty_like(xt), torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, base_xa)
+    bvg.bvg_spmv_Ax(dg, xt, base_ax)
+    old = bvg.bvg_get_config(dg)
+    try:
+        for cfg in ({"gather_pdl": 0}, {"pull_tile": 128}, {"pull_tile": 1024}):
+            bvg.bvg_set_config(dg, **cfg)
+            y = torch.empty_like(xt)
+            bvg.bvg_spmv_xA(dg, xt, y)
+            assert torch.equal(y, base_xa), cfg  # the push result does not depend on these settings
+            bvg.bvg_spmv_Ax(dg, xt, y)
+            assert torch.equal(y, base_ax), cfg
+            bvg.bvg_set_config(dg, **old)
+    finally:
+        bvg.bvg_set_config(dg, **old)
+    with pytest.raises(bvg.BvgError):
+        bvg.bvg_set_config(dg, pull_tile=100)
