@@ -201,6 +201,65 @@ int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host,
 int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0, const float* p_init,
                  int32_t k, float* p_out, int32_t* iters_out, double* resid_out, void* stream);
 
+/* ---------------------------------------------------- learned warm start */
+
+/* The paper has no learned part: Eq. (1) converges to the same p from any
+ * starting iterate, and this section only predicts a better start. A small
+ * network 6 -> 64 -> 64 -> 1 (ReLU; weights rounded to BF16, FP32
+ * accumulation, the 64 x 64 layer on tensor cores) maps node features to
+ * yhat_i ~ n p_i; the start is p_init = max(yhat, 0.05) / sum(max(yhat, 0.05))
+ * (n p*_i >= alpha under uniform teleport, so the floor only guards
+ * against negative or NaN predictions).
+ * Parameters: 4673 FP32 values laid out W1[64][6], b1[64], W2[64][64],
+ * b2[64], w3[64], b3 (row-major, output index first). The handle owns them,
+ * the Adam moments and a BF16 copy of the weights, on the device current at
+ * bvg_mlp_create; every call must run with that device current. Calls on
+ * one handle are serialised by the caller. */
+
+/* New network with He-style initial weights drawn from `seed` (splitmix64 +
+ * Box-Muller), zero biases. Errors: INVALID_ARG, OOM, CUDA. */
+int bvg_mlp_create(uint64_t seed, bvg_mlp** out);
+/* Number of parameters (4673). */
+int bvg_mlp_param_count(void);
+/* Copies count (= 4673) host floats into the network, resets Adam, rounds
+ * the BF16 copy. Synchronises the device. */
+int bvg_mlp_set_params(bvg_mlp* net, const float* host, int64_t count);
+/* Copies the FP32 parameters to host memory. Synchronises the device. */
+int bvg_mlp_get_params(const bvg_mlp* net, float* host, int64_t count);
+/* Node features of g into feat (device, n x 8 floats, 16-byte aligned):
+ * log1p(in-degree), log1p(out-degree), reference-chain depth (Sec. 3.1),
+ * fraction of the out-neighbours stored in intervals of the difference row
+ * (Sec. 3.2), log1p(mean out-degree of the out-neighbours), log1p(weighted
+ * in-degree sum_{j -> i} 1/outdeg(j)), 0, 0. The degrees come from two
+ * compressed products: (1, 1/outdeg) A with k = 2, and A outdeg^T.
+ * May grow the graph's scratch. Asynchronous on `stream`. */
+int bvg_features(const bvg_dev_graph* g, float* feat, void* stream);
+/* yhat (device, n floats) for features feat (device n x 8, 16-byte aligned).
+ * Asynchronous on `stream`. */
+int bvg_mlp_predict(const bvg_mlp* net, const float* feat, int64_t n, float* yhat, void* stream);
+/* Mean squared error of yhat against target (device, n floats) and its
+ * gradient with respect to the FP32 parameters (rounding steps pass
+ * gradients straight through). *loss (may be NULL) gets the loss; grad_host
+ * (may be NULL, else 4673 host floats) the gradient, which also stays in the
+ * handle for bvg_mlp_adam. Synchronises `stream`. */
+int bvg_mlp_grad(bvg_mlp* net, const float* feat, const float* target, int64_t n, double* loss,
+                 float* grad_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+ * the gradient of the last bvg_mlp_grad, then re-rounds the BF16 weights. */
+int bvg_mlp_adam(bvg_mlp* net, float lr, void* stream);
+/* Trains on `count` graphs with known PageRank vectors p_star[i] (device,
+ * n_i floats): targets n p*, `epochs` passes over the nodes
+ * in chunks of `batch` (>= 128) nodes, one Adam step per chunk. *loss (may
+ * be NULL) gets the mean loss of the last pass. Allocates temporaries for
+ * the features and frees them before returning. Synchronises `stream`. */
+int bvg_warmstart_train(bvg_mlp* net, const bvg_dev_graph* const* gs, const float* const* p_star, int32_t count,
+                        int32_t epochs, float lr, int64_t batch, double* loss, void* stream);
+/* p_init (device, n floats) = max(yhat, 0.05) normalised to sum 1 (FP64
+ * sum) for g, a starting iterate for bvg_pagerank (uniform 1/n where the sum
+ * is not finite). May grow the graph's scratch. Asynchronous on `stream`. */
+int bvg_warmstart_predict(const bvg_mlp* net, const bvg_dev_graph* g, float* p_init, void* stream);
+void bvg_free_mlp(bvg_mlp* net);
+
 /* Launch configuration of a device graph (what bvg_autotune chooses; the
  * results of every setting are the same up to the product tolerance). */
 typedef struct {

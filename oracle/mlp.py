@@ -11,7 +11,8 @@ Parameter vector layout (4673 FP32 values):
 Forward, as computed on the GPU (quantize=True):
   a1 = bf16(W1) f + b1;  h1 = relu(a1);  h1q = bf16(h1)
   a2 = bf16(W2) h1q + b2; h2 = relu(a2);  yhat = bf16(w3) . h2 + b3
-Loss (mean squared error over N nodes): L = sum_i (yhat_i - t_i)^2 / N.
+Loss (mean squared error over N nodes): L = sum_i (yhat_i - t_i)^2 / N,
+with the target t_i = n p*_i (the PageRank vector scaled to mean 1).
 Backward: the rounding steps pass gradients through unchanged.
 With quantize=False every step is exact FP64 (used for the finite-difference
 pin of the backward formulas).
@@ -92,7 +93,9 @@ def features(row_ptr, col, ref, depth, min_interval=4):
     """Node features, FP64, by definition:
     log1p(in-degree), log1p(out-degree), reference-chain depth, fraction of the
     row's successors that its difference row stores as intervals, log1p(mean
-    out-degree of the successors), log(n)."""
+    out-degree of the successors), log1p(weighted in-degree), where the
+    weighted in-degree of i is sum over edges j -> i of 1/outdeg(j) (the
+    share of uniform mass one step of Eq. 1 without teleport brings to i)."""
     rp = np.asarray(row_ptr, np.int64)
     ci = np.asarray(col, np.int64)
     n = len(rp) - 1
@@ -122,5 +125,7 @@ def features(row_ptr, col, ref, depth, min_interval=4):
     f[:, 2] = np.asarray(depth, np.float64)
     f[:, 3] = ivfrac
     f[:, 4] = np.log1p(mean_nbr)
-    f[:, 5] = np.log(n)
+    src = np.repeat(np.arange(n), np.diff(rp))
+    wdeg = np.bincount(ci, weights=1.0 / outdeg[src], minlength=n) if len(ci) else np.zeros(n)
+    f[:, 5] = np.log1p(wdeg)
     return f

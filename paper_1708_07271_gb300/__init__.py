@@ -35,7 +35,9 @@ EXPORTED = [
     "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
     "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
     "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get", "bvg_spmv_xA_noalloc",
-    "bvg_get_config", "bvg_set_config",
+    "bvg_get_config", "bvg_set_config", "bvg_mlp_create", "bvg_mlp_param_count", "bvg_mlp_set_params",
+    "bvg_mlp_get_params", "bvg_features", "bvg_mlp_predict", "bvg_mlp_grad", "bvg_mlp_adam", "bvg_warmstart_train",
+    "bvg_warmstart_predict", "bvg_free_mlp",
 ]
 
 
@@ -127,6 +129,18 @@ def load(build_if_needed: bool = True):
             "bvg_get_config": ([_P, ctypes.POINTER(LaunchConfig)], ctypes.c_int),
             "bvg_set_config": ([_P, ctypes.POINTER(LaunchConfig)], ctypes.c_int),
             "bvg_trace_read": ([_P, ctypes.POINTER(TraceEntry), _I32, ctypes.POINTER(_I32)], ctypes.c_int),
+            "bvg_mlp_create": ([ctypes.c_uint64, ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_mlp_param_count": ([], ctypes.c_int),
+            "bvg_mlp_set_params": ([_P, _P, _I64], ctypes.c_int),
+            "bvg_mlp_get_params": ([_P, _P, _I64], ctypes.c_int),
+            "bvg_features": ([_P, _P, _P], ctypes.c_int),
+            "bvg_mlp_predict": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+            "bvg_mlp_grad": ([_P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P, _P], ctypes.c_int),
+            "bvg_mlp_adam": ([_P, ctypes.c_float, _P], ctypes.c_int),
+            "bvg_warmstart_train": ([_P, _P, _P, _I32, _I32, ctypes.c_float, _I64, ctypes.POINTER(ctypes.c_double),
+                                     _P], ctypes.c_int),
+            "bvg_warmstart_predict": ([_P, _P, _P, _P], ctypes.c_int),
+            "bvg_free_mlp": ([_P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -183,6 +197,18 @@ class CsrGraph:
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
             _lib.bvg_free_csr(self.ptr)
+            self.ptr = None
+
+
+class Mlp:
+    """Owns a bvg_mlp* (the warm-start network)."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_mlp(self.ptr)
             self.ptr = None
 
 
@@ -416,3 +442,97 @@ def bvg_trace_read(g: DevGraph) -> dict:
 
 def bvg_status_string(status: int) -> str:
     return load().bvg_status_string(status).decode()
+
+
+# ------------------------------------------------------------ learned warm start
+
+def bvg_mlp_create(seed: int = 0) -> Mlp:
+    out = _P()
+    _check(load().bvg_mlp_create(int(seed) & (2**64 - 1), ctypes.byref(out)), "bvg_mlp_create")
+    return Mlp(out)
+
+
+def bvg_mlp_set_params(net: Mlp, theta):
+    a = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load().bvg_mlp_set_params(net.ptr, a.ctypes.data, a.size), "bvg_mlp_set_params")
+
+
+def bvg_mlp_get_params(net: Mlp):
+    lib = load()
+    a = np.zeros(lib.bvg_mlp_param_count(), np.float32)
+    _check(lib.bvg_mlp_get_params(net.ptr, a.ctypes.data, a.size), "bvg_mlp_get_params")
+    return a
+
+
+def bvg_features(g: DevGraph, out=None, stream=None):
+    """Node features (n x 8 float32 CUDA tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty((g.n, 8), dtype=torch.float32, device="cuda")
+    _fp32_cuda(out)
+    if tuple(out.shape) != (g.n, 8) or not out.is_contiguous():
+        raise ValueError("features: out must be a contiguous n x 8 tensor")
+    _check(load().bvg_features(g.ptr, out.data_ptr(), _stream(stream)), "bvg_features")
+    return out
+
+
+def _feat_ok(feat):
+    _fp32_cuda(feat)
+    if feat.dim() != 2 or feat.shape[1] != 8 or not feat.is_contiguous():
+        raise ValueError("features must be a contiguous n x 8 float32 CUDA tensor")
+
+
+def bvg_mlp_predict(net: Mlp, feat, out=None, stream=None):
+    import torch
+    _feat_ok(feat)
+    n = feat.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _fp32_cuda(out)
+    _check(load().bvg_mlp_predict(net.ptr, feat.data_ptr(), n, out.data_ptr(), _stream(stream)), "bvg_mlp_predict")
+    return out
+
+
+def bvg_mlp_grad(net: Mlp, feat, target, stream=None):
+    """(loss, gradient as a host float32 array) of the mean squared error."""
+    _feat_ok(feat)
+    _fp32_cuda(target)
+    n = feat.shape[0]
+    if target.shape != (n,) or not target.is_contiguous():
+        raise ValueError("target must be a contiguous vector of n floats")
+    lib = load()
+    g = np.zeros(lib.bvg_mlp_param_count(), np.float32)
+    loss = ctypes.c_double()
+    _check(lib.bvg_mlp_grad(net.ptr, feat.data_ptr(), target.data_ptr(), n, ctypes.byref(loss), g.ctypes.data,
+                            _stream(stream)), "bvg_mlp_grad")
+    return loss.value, g
+
+
+def bvg_mlp_adam(net: Mlp, lr: float, stream=None):
+    _check(load().bvg_mlp_adam(net.ptr, lr, _stream(stream)), "bvg_mlp_adam")
+
+
+def bvg_warmstart_train(net: Mlp, graphs, p_stars, epochs=20, lr=3e-3, batch=65536, stream=None) -> float:
+    """Trains the network on graphs with known PageRank vectors; returns the last pass's mean loss."""
+    if len(graphs) != len(p_stars) or not graphs:
+        raise ValueError("need one PageRank vector per graph")
+    for g, p in zip(graphs, p_stars):
+        _fp32_cuda(p)
+        if p.shape != (g.n,) or not p.is_contiguous():
+            raise ValueError("PageRank vectors must be contiguous with n entries")
+    gs = (_P * len(graphs))(*[g.ptr for g in graphs])
+    ps = (_P * len(graphs))(*[p.data_ptr() for p in p_stars])
+    loss = ctypes.c_double()
+    _check(load().bvg_warmstart_train(net.ptr, gs, ps, len(graphs), epochs, lr, batch, ctypes.byref(loss),
+                                      _stream(stream)), "bvg_warmstart_train")
+    return loss.value
+
+
+def bvg_warmstart_predict(net: Mlp, g: DevGraph, out=None, stream=None):
+    """Starting iterate for bvg_pagerank predicted by the network (n floats, sum 1)."""
+    import torch
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    _fp32_cuda(out)
+    _check(load().bvg_warmstart_predict(net.ptr, g.ptr, out.data_ptr(), _stream(stream)), "bvg_warmstart_predict")
+    return out

@@ -56,4 +56,7 @@ def test_features_on_worked_example():
     np.testing.assert_array_equal(f[:, 2], depth)
     np.testing.assert_array_equal(f[:, 3], [1, 0, 0, 0, 0, 0, 0, 0])  # only row 0 stores an interval
     np.testing.assert_allclose(f[:, 4], np.log1p(mean_nbr))
-    np.testing.assert_allclose(f[:, 5], np.log(8))
+    # weighted in-degree sum_{j -> i} 1/outdeg(j), by hand; it sums to the 7 non-dangling rows
+    wdeg = [8 / 15, 3 / 2, 9 / 20, 59 / 60, 59 / 60, 59 / 60, 5 / 6, 11 / 15]
+    assert abs(sum(wdeg) - 7) < 1e-12
+    np.testing.assert_allclose(f[:, 5], np.log1p(wdeg))
