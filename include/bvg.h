@@ -201,6 +201,31 @@ int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host,
 int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0, const float* p_init,
                  int32_t k, float* p_out, int32_t* iters_out, double* resid_out, void* stream);
 
+/* ------------------------------------------------------ multi-graph batch */
+
+/* A batch of device graphs whose products run in one grid: the chain step
+ * of every graph in one kernel, the gather of every graph in a second one
+ * (Proposition 1 applied to each graph independently), replayed from a
+ * CUDA graph. The batch refers to the graphs' device layouts (no copy): the
+ * graphs must outlive it. Graphs with n = 0 are accepted and skipped.
+ * `stream` is unused (creation does no device work). Errors: INVALID_ARG,
+ * OOM, CUDA. */
+int bvg_batch_create(const bvg_dev_graph* const* gs, int32_t count, void* stream, bvg_batch** out);
+/* Number of graphs, total rows and total edges of a batch. */
+int bvg_batch_size(const bvg_batch* b, int32_t* count, int64_t* total_n, int64_t* total_m);
+/* y_i = x_i A_i for every graph i: xs[i], ys[i] (host arrays of `count`
+ * DEVICE pointers) are row-major n_i x k with leading dimension k, 4-byte
+ * aligned (16-byte alignment and k % 4 == 0 enable 128-bit accesses). The
+ * pointer table is staged through pinned memory and copied on `stream`
+ * ahead of the launches; the result of graph i is bit-identical to
+ * bvg_spmv_xA on the same graph with the same buffers. Calls on one batch
+ * are ordered among themselves even across streams (a later call waits for
+ * the earlier one); the first call with a larger k allocates. Asynchronous.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* const* ys, int32_t k, void* stream);
+/* Waits for the batch's last call, then frees it (not the graphs). */
+void bvg_free_batch(bvg_batch* b);
+
 /* ---------------------------------------------------- learned warm start */
 
 /* The paper has no learned part: Eq. (1) converges to the same p from any
@@ -267,9 +292,43 @@ typedef struct {
     int32_t pull_prefix;    /* pull interval sums from a prefix of x: -1 auto (mean interval >= 32), 0 off, 1 on */
     int32_t prefix_min_len; /* with the prefix on, intervals at least this long use it (default 16) */
     int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */
+    int32_t col_block;      /* widest column block of a product: power of two in [1, 32] (default 32) */
 } bvg_launch_config;
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
+
+/* Autotuner. Times the products of g with k right-hand sides under each
+ * candidate launch configuration (CUDA events on `stream`, median of 7 after
+ * 2 warm-up calls, warm caches): first the push (x A) over the widest column
+ * block (the largest power of two <= min(k, 32) and up to three halvings)
+ * times gather overlap on/off, then the pull (A x^T) over rows per CTA
+ * {128, 256, 512, 1024} times prefix off / on from interval length 8 or 32.
+ * It applies the fastest choice to g (bvg_get_config shows it). With
+ * cache_path != NULL it first looks the choice up in that JSON file under
+ * the key "<device name>/sm<count>/<layout fingerprint>/k<k>" and, after a
+ * search, stores it there (read-modify-write through a temporary file and a
+ * rename; a missing or corrupt file starts a new cache). Allocates two
+ * scratch n x k buffers for the search and frees them. Synchronises
+ * `stream`. The results of every configuration agree up to the product
+ * tolerance. Errors: INVALID_ARG, OOM, CUDA. */
+int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path, void* stream);
+typedef struct {
+    int32_t from_cache;      /* 1: the last bvg_autotune took the configuration from the cache */
+    int32_t candidates;      /* configurations timed by the last bvg_autotune */
+    double push_us_default;  /* x A before tuning, and with the chosen configuration (us) */
+    double push_us_best;
+    double pull_us_default;  /* A x^T likewise */
+    double pull_us_best;
+} bvg_autotune_info;
+int bvg_autotune_info_get(const bvg_dev_graph* g, bvg_autotune_info* out);
+/* The cache key bvg_autotune uses for g and k (NUL-terminated, into buf of cap bytes). */
+int bvg_autotune_key(const bvg_dev_graph* g, int32_t k, char* buf, int32_t cap);
+/* Host-only access to the cache file (no GPU needed): *found = 1 and *out
+ * set when `key` is present; a missing or unreadable file gives *found = 0. */
+int bvg_autotune_cache_lookup(const char* path, const char* key, bvg_launch_config* out, int32_t* found);
+/* Inserts or replaces `key` (with the timings it was chosen by, in us). */
+int bvg_autotune_cache_store(const char* path, const char* key, const bvg_launch_config* cfg, double push_us,
+                             double pull_us);
 
 /* Number of rows n of a device graph. */
 int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);

@@ -37,7 +37,9 @@ EXPORTED = [
     "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get", "bvg_spmv_xA_noalloc",
     "bvg_get_config", "bvg_set_config", "bvg_mlp_create", "bvg_mlp_param_count", "bvg_mlp_set_params",
     "bvg_mlp_get_params", "bvg_features", "bvg_mlp_predict", "bvg_mlp_grad", "bvg_mlp_adam", "bvg_warmstart_train",
-    "bvg_warmstart_predict", "bvg_free_mlp",
+    "bvg_warmstart_predict", "bvg_free_mlp", "bvg_batch_create", "bvg_batch_size", "bvg_batch_spmv_xA",
+    "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
+    "bvg_autotune_cache_store",
 ]
 
 
@@ -75,7 +77,14 @@ class LayoutView(ctypes.Structure):
 
 
 class LaunchConfig(ctypes.Structure):
-    _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32)]
+    _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
+                ("col_block", _I32)]
+
+
+class AutotuneInfo(ctypes.Structure):
+    _fields_ = [("from_cache", _I32), ("candidates", _I32), ("push_us_default", ctypes.c_double),
+                ("push_us_best", ctypes.c_double), ("pull_us_default", ctypes.c_double),
+                ("pull_us_best", ctypes.c_double)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -141,6 +150,17 @@ def load(build_if_needed: bool = True):
                                      _P], ctypes.c_int),
             "bvg_warmstart_predict": ([_P, _P, _P, _P], ctypes.c_int),
             "bvg_free_mlp": ([_P], None),
+            "bvg_batch_create": ([_P, _I32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_batch_size": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_batch_spmv_xA": ([_P, _P, _P, _I32, _P], ctypes.c_int),
+            "bvg_free_batch": ([_P], None),
+            "bvg_autotune": ([_P, _I32, ctypes.c_char_p, _P], ctypes.c_int),
+            "bvg_autotune_info_get": ([_P, ctypes.POINTER(AutotuneInfo)], ctypes.c_int),
+            "bvg_autotune_key": ([_P, _I32, ctypes.c_char_p, _I32], ctypes.c_int),
+            "bvg_autotune_cache_lookup": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(LaunchConfig),
+                                           ctypes.POINTER(_I32)], ctypes.c_int),
+            "bvg_autotune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(LaunchConfig),
+                                          ctypes.c_double, ctypes.c_double], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -197,6 +217,19 @@ class CsrGraph:
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
             _lib.bvg_free_csr(self.ptr)
+            self.ptr = None
+
+
+class Batch:
+    """Owns a bvg_batch* and keeps its graphs alive."""
+
+    def __init__(self, ptr, graphs):
+        self.ptr, self.graphs = ptr, list(graphs)
+        self.sizes = [g.n for g in graphs]
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_batch(self.ptr)
             self.ptr = None
 
 
@@ -270,9 +303,11 @@ def bvg_upload(hg: HostGraph, stream=None) -> DevGraph:
 def _km(t, n):
     """(k, ld) of a row-major n x k tensor (1-D means k = 1)."""
     if t.dim() == 1:
-        if t.shape[0] != n or t.stride(0) != 1:
+        if t.shape[0] != n or (t.stride(0) != 1 and n > 0):
             raise ValueError("vector must be contiguous with n entries")
         return 1, 1
+    if t.dim() == 2 and t.shape[0] == n == 0:  # no rows: any strides
+        return t.shape[1], t.shape[1]
     if t.dim() != 2 or t.shape[0] != n or t.stride(1) != 1:
         raise ValueError("expected a row-major n x k tensor")
     return t.shape[1], t.stride(0)
@@ -536,3 +571,74 @@ def bvg_warmstart_predict(net: Mlp, g: DevGraph, out=None, stream=None):
     _fp32_cuda(out)
     _check(load().bvg_warmstart_predict(net.ptr, g.ptr, out.data_ptr(), _stream(stream)), "bvg_warmstart_predict")
     return out
+
+
+# ------------------------------------------------------------ multi-graph batch
+
+def bvg_batch_create(graphs, stream=None) -> Batch:
+    graphs = list(graphs)
+    arr = (_P * len(graphs))(*[g.ptr for g in graphs])
+    out = _P()
+    _check(load().bvg_batch_create(arr, len(graphs), _stream(stream), ctypes.byref(out)), "bvg_batch_create")
+    return Batch(out, graphs)
+
+
+def bvg_batch_size(b: Batch):
+    c, n, m = _I32(), _I64(), _I64()
+    _check(load().bvg_batch_size(b.ptr, ctypes.byref(c), ctypes.byref(n), ctypes.byref(m)), "bvg_batch_size")
+    return c.value, n.value, m.value
+
+
+def bvg_batch_spmv_xA(b: Batch, xs, ys, stream=None):
+    """ys[i] = xs[i] A_i for every graph of the batch (float32 CUDA tensors, n_i or n_i x k, contiguous)."""
+    if len(xs) != len(b.graphs) or len(ys) != len(b.graphs):
+        raise ValueError("one x and one y per graph")
+    k = None
+    for g, x, y in zip(b.graphs, xs, ys):
+        _fp32_cuda(x, y)
+        kx, ldx = _km(x, g.n)
+        if _km(y, g.n) != (kx, ldx) or ldx != kx:
+            raise ValueError("x and y must be contiguous n x k with the same shape")
+        if k is None:
+            k = kx
+        elif k != kx:
+            raise ValueError("every graph of a batch takes the same k")
+    xa = (_P * len(xs))(*[x.data_ptr() for x in xs])
+    ya = (_P * len(ys))(*[y.data_ptr() for y in ys])
+    _check(load().bvg_batch_spmv_xA(b.ptr, xa, ya, k, _stream(stream)), "bvg_batch_spmv_xA")
+    return ys
+
+
+# ------------------------------------------------------------------ autotune
+
+def bvg_autotune(g: DevGraph, k: int = 1, cache_path=None, stream=None) -> dict:
+    """Times the launch configurations, applies the fastest; returns the config and the timings."""
+    path = None if cache_path is None else os.fsencode(cache_path)
+    lib = load()
+    _check(lib.bvg_autotune(g.ptr, k, path, _stream(stream)), "bvg_autotune")
+    info = AutotuneInfo()
+    _check(lib.bvg_autotune_info_get(g.ptr, ctypes.byref(info)), "bvg_autotune_info_get")
+    out = bvg_get_config(g)
+    out.update({f: getattr(info, f) for f, _ in AutotuneInfo._fields_})
+    return out
+
+
+def bvg_autotune_key(g: DevGraph, k: int = 1) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(load().bvg_autotune_key(g.ptr, k, buf, 512), "bvg_autotune_key")
+    return buf.value.decode()
+
+
+def bvg_autotune_cache_lookup(path, key: str):
+    """Launch configuration cached under key, or None."""
+    c = LaunchConfig()
+    found = _I32()
+    _check(load().bvg_autotune_cache_lookup(os.fsencode(path), key.encode(), ctypes.byref(c),
+                                                 ctypes.byref(found)), "bvg_autotune_cache_lookup")
+    return {f: getattr(c, f) for f, _ in LaunchConfig._fields_} if found.value else None
+
+
+def bvg_autotune_cache_store(path, key: str, config: dict, push_us: float = 0.0, pull_us: float = 0.0):
+    c = LaunchConfig(**{f: int(config[f]) for f, _ in LaunchConfig._fields_})
+    _check(load().bvg_autotune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c), push_us, pull_us),
+           "bvg_autotune_cache_store")

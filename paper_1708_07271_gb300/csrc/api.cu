@@ -323,6 +323,23 @@ static int check_vec(const bvg_dev_graph* g, const void* p, const char* what) {
 }  // namespace bvg
 
 // =================================================================== upload
+// FNV-1a over the layout's 32-bit words (and its sizes): equal layouts give
+// equal keys in the autotune cache.
+static uint64_t layout_fingerprint(const HostLayout& L, int64_t n, int64_t m) {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    auto mix = [&](uint64_t w) {
+        h ^= w;
+        h *= 0x100000001b3ULL;
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)m);
+    for (const std::vector<uint32_t>* v : {&L.desc, &L.rowp, &L.ent, &L.colp, &L.tent, &L.carry_ptr, &L.carry}) {
+        mix(v->size());
+        for (uint32_t w : *v) mix(w);
+    }
+    return h;
+}
+
 extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph** out) {
     if (!hg || !out) return fail(BVG_ERR_INVALID_ARG, "bvg_upload: NULL argument");
     *out = nullptr;
@@ -344,6 +361,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->mean_interval = hg->stats.intervals ? (double)hg->stats.interval_members / (double)hg->stats.intervals : 0.0;
         g->ntent = (int64_t)L->tent.size();
         g->ncarry = (int64_t)L->carry.size();
+        g->fingerprint = layout_fingerprint(*L, n, hg->m);
         if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
             (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
@@ -450,6 +468,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
     out->pull_prefix = g->cfg.pull_prefix;
     out->prefix_min_len = g->cfg.prefix_min_len;
     out->gather_pdl = g->cfg.gather_pdl;
+    out->col_block = g->cfg.col_block;
     return BVG_OK;
 }
 
@@ -457,13 +476,16 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     if (!g || !in) return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: NULL argument");
     if (in->pull_tile < 64 || in->pull_tile > 2048 || (in->pull_tile & (in->pull_tile - 1)) ||
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
-        in->gather_pdl > 1)
+        in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)))
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
-                                         "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}");
+                                         "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
+                                         "of two in [1, 32]");
+    if (in->gather_pdl != g->cfg.gather_pdl) drop_pr_graph(g);  // the PageRank graph was captured with the old launch
     g->cfg.pull_tile = in->pull_tile;
     g->cfg.pull_prefix = in->pull_prefix;
     g->cfg.prefix_min_len = in->prefix_min_len;
     g->cfg.gather_pdl = in->gather_pdl;
+    g->cfg.col_block = in->col_block;
     return BVG_OK;
 }
 
@@ -491,7 +513,7 @@ extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int
     bvg_dev_graph* gm = const_cast<bvg_dev_graph*>(g);
     const bool prefix = use_prefix(g);
     for (int64_t c0 = 0; c0 < k; ) {
-        const int kb = block_k(k - c0);
+        const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
         if (prefix && (rc = ensure_prefix(gm, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
         BVG_KV_CASES(launch_pull, g, x + c0, ld, y + c0, ld, prefix, st);
@@ -511,7 +533,7 @@ extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, in
     if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: x and y must not alias");
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t c0 = 0; c0 < k; ) {
-        const int kb = block_k(k - c0);
+        const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
         if ((rc = ensure_z(g, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
         BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);

@@ -81,6 +81,13 @@ struct LaunchCfg {
     int pull_prefix = -1;       // interval sums of the pull from the prefix of x: -1 auto, 0 off, 1 on
     int prefix_min_len = 16;    // with the prefix on, intervals at least this long use it
     int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
+    int col_block = 32;         // widest column block of a product (power of two <= 32)
+};
+
+struct TuneInfo {
+    int from_cache = 0;
+    int candidates = 0;
+    double push_us_default = 0, push_us_best = 0, pull_us_default = 0, pull_us_best = 0;
 };
 
 struct DevScratch {
@@ -139,6 +146,8 @@ struct bvg_dev_graph {
     double mean_interval = 0.0;     // mean interval length (prefix policy)
     int64_t bytes = 0;
     bvg::LaunchCfg cfg;
+    uint64_t fingerprint = 0;  // hash of the layout (autotune cache key)
+    bvg::TuneInfo tune;
     bvg::DevScratch s;
     bvg::Tracer* tracer = nullptr;
 };

@@ -306,18 +306,18 @@ struct ChainShape {
     static constexpr int RPT = TILE / NG;  // rows per group
 };
 
+// One tile of the chain step (rows [blk * TILE, blk * TILE + TILE) of a graph
+// with n rows); shared by the one-graph and the multi-graph kernels.
 template <int KB, int V>
-__global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc, const float* __restrict__ x,
-                                               int64_t ldx, const float* __restrict__ rowscale,
-                                               float* __restrict__ z, int64_t ldz, int64_t n,
-                                               const PrState* __restrict__ st) {
+__device__ __forceinline__ void chain_tile(int64_t blk, const uint32_t* __restrict__ desc,
+                                           const float* __restrict__ x, int64_t ldx,
+                                           const float* __restrict__ rowscale, float* __restrict__ z, int64_t ldz,
+                                           int64_t n) {
     using Sh = ChainShape<KB, V>;
     constexpr int G = Sh::G, NG = Sh::NG, TILE = Sh::TILE, RPT = Sh::RPT;
-    asm volatile("griddepcontrol.launch_dependents;");
-    if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
     __shared__ float xs[(TILE + kHalo) * KB];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const int64_t a = (int64_t)blockIdx.x * TILE;
+    const int64_t a = blk * TILE;
     const int cnt = (int)((a + TILE + kHalo < n ? a + TILE + kHalo : n) - a);
     const int own = (int)((a + TILE < n ? a + TILE : n) - a);
 
@@ -359,6 +359,16 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
         for (int v = 0; v < V; v++) out.v[v] = df_val(acc[v]);
         stv<V>(z + (a + r) * ldz + lane * V, out);
     }
+}
+
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc, const float* __restrict__ x,
+                                               int64_t ldx, const float* __restrict__ rowscale,
+                                               float* __restrict__ z, int64_t ldz, int64_t n,
+                                               const PrState* __restrict__ st) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (st && (__ldcg(&st->done) || __ldcg(&st->iter) >= __ldcg(&st->max_iter))) return;  // PageRank finished
+    chain_tile<KB, V>(blockIdx.x, desc, x, ldx, rowscale, z, ldz, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,12 +506,14 @@ __device__ __forceinline__ float from_fx(long long v, int sexp) {
     return __fmul_rn(__fmul_rn(__ll2float_rn(v), pow2f(-(sexp / 2))), pow2f(-(sexp - sexp / 2)));
 }
 
+// One tile of the gather (columns [blk * T, blk * T + T)); shared by the
+// one-graph and the multi-graph kernels.
 template <int KB, int V, int EPI>
-__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
-                                                const uint32_t* __restrict__ carry_ptr,
-                                                const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
-                                                float* __restrict__ y, int64_t ldy, int64_t n,
-                                                PrArgs pa) {
+__device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restrict__ colp,
+                                            const uint32_t* __restrict__ tent,
+                                            const uint32_t* __restrict__ carry_ptr,
+                                            const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
+                                            float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
@@ -511,7 +523,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
     __shared__ uint32_t tile_beg_s, tile_end_s;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t a = (int64_t)blockIdx.x * T;
+    const int64_t a = blk * T;
     const int64_t end = a + T < n ? a + T : n;
     const int64_t c0 = a + (int64_t)g * CPT;
 
@@ -692,6 +704,15 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ col
         }
     }
     if constexpr (EPI == 1) pr_block_reduce<KB, V>(Ssum, R, Dg, pa, false);
+}
+
+template <int KB, int V, int EPI>
+__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                                const uint32_t* __restrict__ carry_ptr,
+                                                const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
+                                                float* __restrict__ y, int64_t ldy, int64_t n,
+                                                PrArgs pa) {
+    gather_tile<KB, V, EPI>(blockIdx.x, colp, tent, carry_ptr, carry, z, ldz, y, ldy, n, pa);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
