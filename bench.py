@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-graph batch leg")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     return ap.parse_args()
 
 
@@ -224,6 +226,79 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- extra legs
+def batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard):
+    """64 copying-model graphs, n log-uniform in [1e3, 1e6], k = 1: one
+    batched product (two launches from one CUDA graph) against the same
+    products one graph at a time. Under torchrun the graphs are split across
+    ranks (longest first by edges); the figure is all edges over the max time."""
+    sizes = synth.multi_graph_sizes(count=64, lo=1e3, hi=1e6, seed=synth.seed_for(3, 7))
+    specs = [synth.web_small(int(n), synth.seed_for(3, 100 + i)) for i, n in enumerate(sizes)]
+    est_edges = [int(n) * 20 for n in sizes]  # the generator's mean degree, for the split
+    mine = shard.assign_graphs(est_edges, world)[rank]
+    gs = [synth.copying_model(specs[i]) for i in mine]
+    dgs = [bvg.bvg_upload(bvg.bvg_encode(g.row_ptr, g.col)) for g in gs]
+    b = bvg.bvg_batch_create(dgs)
+    xs = [torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(3, 200 + i))).cuda().reshape(-1)
+          for i, g in zip(mine, gs)]
+    ys = [torch.empty_like(x) for x in xs]
+    m_local = sum(g.m for g in gs)
+
+    def seq():
+        for d, x, y in zip(dgs, xs, ys):
+            bvg.bvg_spmv_xA(d, x, y)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        bvg.bvg_batch_spmv_xA(b, xs, ys)
+        seq()
+    t_b = float(np.sum(timed(lambda: bvg.bvg_batch_spmv_xA(b, xs, ys), args.steps)))
+    t_s = float(np.sum(timed(seq, args.steps)))
+    tb, m_all = shard.reduce_timing(t_b, m_local * args.steps, device="cuda")
+    ts, _ = shard.reduce_timing(t_s, 0.0, device="cuda")
+    return {"graphs": len(sizes), "n_total": int(sum(int(v) for v in sizes)),
+            "m_total": int(shard.reduce_timing(0.0, m_local, device="cuda")[1]),
+            "gedges_s": m_all / (tb * 1e-3) / 1e9, "ms_per_step": tb / args.steps,
+            "one_graph_at_a_time_ms_per_step": ts / args.steps, "speedup_vs_one_at_a_time": ts / tb,
+            "launches_per_step": 2, "split": f"graphs split over {world} rank(s), longest first"}
+
+
+def warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it):
+    """The learned warm start on the bench graph: the network is trained on
+    PageRank vectors that bvg_pagerank computes on eight generated graphs
+    (n log-uniform in [1e5, 3e5]), then PageRank on the bench graph starts
+    from its prediction. Time includes the features and the prediction."""
+    sizes = synth.multi_graph_sizes(count=8, lo=1e5, hi=3e5, seed=synth.seed_for(4, 7))
+    train, pstars = [], []
+    for i, n in enumerate(sizes):
+        gt = synth.copying_model(synth.web_small(int(n), synth.seed_for(4, 100 + i)))
+        d = bvg.bvg_upload(bvg.bvg_encode(gt.row_ptr, gt.col))
+        p, _, _, _ = bvg.bvg_pagerank(d, tol=1e-10, max_iter=1000)
+        train.append(d)
+        pstars.append(p)
+    net = bvg.bvg_mlp_create(7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = bvg.bvg_warmstart_train(net, train, pstars, epochs=10, lr=3e-3, batch=16384)
+    train_s = time.perf_counter() - t0
+    p = torch.empty(g.n, device="cuda")
+    p_init = torch.empty(g.n, device="cuda")
+    bvg.bvg_warmstart_predict(net, dg, out=p_init)
+    bvg.bvg_pagerank(dg, p_init=p_init, tol=1e-8, max_iter=1000, out=p)
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bvg.bvg_warmstart_predict(net, dg, out=p_init)
+        _, it, res, rc = bvg.bvg_pagerank(dg, p_init=p_init, tol=1e-8, max_iter=1000, out=p)
+        runs.append((time.perf_counter() - t0, it, float(res[0]), rc))
+    runs.sort()
+    s, it, res, rc = runs[len(runs) // 2]
+    return {"seconds": s, "iterations": it, "l1_resid": res, "status": rc, "uniform_seconds": pr_s,
+            "uniform_iterations": pr_it, "train_seconds": train_s, "train_loss": loss,
+            "train_graphs": len(sizes), "train_nodes": int(sum(int(v) for v in sizes))}
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_bv(args):
     import torch
@@ -243,12 +318,10 @@ def run_bv(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_1708_07271_gb300 import shard
+
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.reduce_timing(v, 0.0, device="cuda")[0]
 
     k = args.k
     g = synth.copying_model(workload_spec())
@@ -359,6 +432,9 @@ def run_bv(args):
     pr_runs.sort()
     pr_s, pr_it, pr_res, pr_rc = pr_runs[len(pr_runs) // 2]
 
+    batch = None if args.no_batch else batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard)
+    warm = None if args.no_warmstart else warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times = cpu_oracle_run(g, cpu_oracle_prepare(g, k), args.cpu_seconds)
@@ -379,6 +455,7 @@ def run_bv(args):
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
+            "batch": batch, "warm_start": warm,
             "compression": {"m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
                             "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"],
                             "structure_MB": L["structure_bytes"] / 1e6},

@@ -230,8 +230,11 @@ static void launch_pr_final(const bvg_dev_graph* g, const PrState* pst, float* o
 }
 
 // Grows the z scratch to n x kb floats.
+static void drop_pr_graph(bvg_dev_graph* g);
+
 static int ensure_z(bvg_dev_graph* g, int kb) {
     if (g->s.kcap >= kb) return BVG_OK;
+    drop_pr_graph(g);  // the captured PageRank updates read the old z
     if (g->s.z) cudaFree(g->s.z);
     g->s.z = nullptr;
     g->s.kcap = 0;
@@ -632,7 +635,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     constexpr int kChunk = 8;
     const int key[4] = {kb, v, dangling, p0 != nullptr};
     if (g->s.pr_exec && (memcmp(key, g->s.pr_key, sizeof(key)) || g->s.pr_key_alpha != base.alpha ||
-                         g->s.pr_key_ptr != g->s.q[0]))
+                         g->s.pr_key_ptr != g->s.q[0] || g->s.pr_key_z != g->s.z))
         drop_pr_graph(g);
     auto launch_update = [&](int par) {
         // update reading q[par], writing q[1 - par]
@@ -687,6 +690,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         memcpy(g->s.pr_key, key, sizeof(key));
         g->s.pr_key_alpha = base.alpha;
         g->s.pr_key_ptr = g->s.q[0];
+        g->s.pr_key_z = g->s.z;
     }
     for (;;) {
         while (launched < next_poll) {

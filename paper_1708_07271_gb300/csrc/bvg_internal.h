@@ -113,6 +113,7 @@ struct DevScratch {
     int pr_key[4] = {0, 0, 0, 0};       // kb, v, dangling, has p0
     float pr_key_alpha = 0.f;
     const void* pr_key_ptr = nullptr;   // q[0] when captured
+    const void* pr_key_z = nullptr;     // z when captured
     // warm-start features: degree temporaries (4 x n) and features + prediction (9 x n)
     float* feat_tmp = nullptr;
     int64_t feat_cap = 0;

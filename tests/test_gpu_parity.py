@@ -222,6 +222,22 @@ def test_pagerank_warm_start_and_not_converged():
     assert l1(p.cpu().numpy(), want) <= 1e-6
 
 
+def test_pagerank_after_scratch_growth():
+    """A wider product between two PageRank runs reallocates the pushed-weight
+    scratch; the second run must not replay updates captured with the old
+    buffer, and gives the same (deterministic) vector."""
+    g, hg, _, _ = graph("tiny_web")
+    dg = bvg.bvg_upload(hg)
+    p1, it1, _, rc1 = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500)
+    p1 = p1.clone()
+    x = torch.rand(g.n, 4, device="cuda")
+    y = torch.empty_like(x)
+    bvg.bvg_spmv_xA(dg, x, y)  # k = 4 grows the scratch
+    p2, it2, _, rc2 = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=500)
+    assert rc1 == rc2 == bvg.BVG_OK and it1 == it2
+    assert torch.equal(p1, p2)
+
+
 def test_pagerank_nan_reported():
     g, hg, dg, ref = graph("tiny_web")
     start = torch.full((g.n,), 1.0 / g.n, device="cuda")
