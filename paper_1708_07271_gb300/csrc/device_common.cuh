@@ -49,6 +49,10 @@ __device__ __forceinline__ df df_addf(df a, float b) {
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ float df_val(df a) { return __fadd_rn(a.hi, a.lo); }
 
+__device__ __forceinline__ df df_shfl_xor(df v, int d) {
+    return {__shfl_xor_sync(0xffffffffu, v.hi, d), __shfl_xor_sync(0xffffffffu, v.lo, d)};
+}
+
 __device__ __forceinline__ df df_shfl_up(df v, int d) {
     return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
 }

@@ -410,21 +410,24 @@ struct PrPartials {
     double S[KB], R[KB], Dg[KB];
 };
 
-// Sums the per-CTA FP64 partials (sum q, sum |q - p_prev|, dangling mass),
-// then the last CTA to finish reduces all CTAs in a fixed order and writes
-// the scalars of this update (deterministic; no spin-waits).
+// Sums the per-CTA partials (sum q, sum |q - p_prev|, dangling mass): each
+// thread's compensated FP32 sums are combined across the CTA in compensated
+// FP32 (error-free two_sum steps, fixed order), stored as one FP64 value per
+// CTA, and the last CTA to finish adds all CTAs' values in FP64 in a fixed
+// order (one warp per quantity) and writes the scalars of this update
+// (deterministic; no spin-waits).
 template <int KB, int V>
-__device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V], const PrArgs& pa, bool init) {
+__device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArgs& pa, bool init) {
     constexpr int G = KB / V;
-    __shared__ double sh_part[32][3][KB];
+    __shared__ df sh_part[32][3][KB];
     __shared__ bool sh_last;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; v++) {
         for (int o = 16; o >= G; o >>= 1) {
-            S[v] += __shfl_xor_sync(0xffffffffu, S[v], o);
-            R[v] += __shfl_xor_sync(0xffffffffu, R[v], o);
-            Dg[v] += __shfl_xor_sync(0xffffffffu, Dg[v], o);
+            S[v] = df_add(S[v], df_shfl_xor(S[v], o));
+            R[v] = df_add(R[v], df_shfl_xor(R[v], o));
+            Dg[v] = df_add(Dg[v], df_shfl_xor(Dg[v], o));
         }
     }
     if (lane32 < G) {
@@ -438,31 +441,25 @@ __device__ void pr_block_reduce(double (&S)[V], double (&R)[V], double (&Dg)[V],
     __syncthreads();
     if (threadIdx.x < 3 * KB) {
         const int f = threadIdx.x / KB, c = threadIdx.x % KB;
-        double t = 0.0;
-        for (int w = 0; w < NW; w++) t += sh_part[w][f][c];
-        pa.partial[((int64_t)blockIdx.x * 3 + f) * KB + c] = t;
+        df t = df_zero();
+        for (int w = 0; w < NW; w++) t = df_add(t, sh_part[w][f][c]);
+        pa.partial[((int64_t)blockIdx.x * 3 + f) * KB + c] = (double)t.hi + (double)t.lo;
+        __threadfence();
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) sh_last = atomicAdd(pa.counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    __shared__ double sh_red[256];
     __shared__ double sh_tot[3][KB];
-    for (int item = 0; item < 3 * KB; item++) {
+    for (int item = warp; item < 3 * KB; item += NW) {
         double t = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int b = lane32; b < (int)gridDim.x; b += 32)
             t += __ldcg(pa.partial + ((int64_t)b * 3 + item / KB) * KB + item % KB);
-        sh_red[threadIdx.x] = t;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) sh_red[threadIdx.x] += sh_red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) sh_tot[item / KB][item % KB] = sh_red[0];
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane32 == 0) sh_tot[item / KB][item % KB] = t;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         bool conv = true, bad = false;
         for (int c = 0; c < pa.k; c++) {
@@ -499,11 +496,60 @@ __device__ __forceinline__ int fx_exponent(unsigned int maxbits, long long terms
     return sexp > 100 ? 100 : (sexp < -100 ? -100 : sexp);
 }
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // |e| <= 126
+
+// round_to_nearest_even(v * 2^sexp) as a 64-bit integer, from the IEEE fields
+// of v with integer instructions only. (The 64-bit float <-> integer
+// conversion instructions run on the FP64 pipe, which this GPU provisions at
+// 2 operations per SM per cycle; these helpers keep the gather off it.)
+// Zero and subnormal v give 0: |v| < 2^-126 and sexp <= 100 put the scaled
+// value below 2^-26. The scale choice above bounds every term's shift by 38.
 __device__ __forceinline__ long long to_fx(float v, int sexp) {
-    return __float2ll_rn(__fmul_rn(__fmul_rn(v, pow2f(sexp / 2)), pow2f(sexp - sexp / 2)));
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xffu);
+    const uint32_t m = (b & 0x7fffffu) | 0x800000u;  // 24-bit significand
+    const int sh = ex - 150 + sexp;                   // v * 2^sexp = m * 2^sh
+    unsigned long long mag;
+    if (ex == 0 || ex == 255 || sh < -25) {
+        mag = 0;  // zero, subnormal, or too small to reach 1/2; non-finite terms are reported apart
+    } else if (sh >= 0) {
+        mag = (unsigned long long)m << (sh > 40 ? 40 : sh);
+    } else {
+        const int k = -sh;  // 1..25
+        const uint32_t q = m >> k, rem = m & ((1u << k) - 1u), half = 1u << (k - 1);
+        mag = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+    }
+    return (b >> 31) ? -(long long)mag : (long long)mag;
 }
+
+// round_to_nearest_even(v * 2^-sexp) as a float, by normalising the 64-bit
+// integer with integer instructions; a result below the normal range takes
+// the conversion instruction instead (never on typical inputs).
 __device__ __forceinline__ float from_fx(long long v, int sexp) {
-    return __fmul_rn(__fmul_rn(__ll2float_rn(v), pow2f(-(sexp / 2))), pow2f(-(sexp - sexp / 2)));
+    if (v == 0) return 0.f;
+    const uint32_t sign = v < 0 ? 0x80000000u : 0u;
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int nb = 64 - __clzll(a);  // significant bits, 1..64
+    uint32_t m;
+    int e2;  // |v| ~= m * 2^e2 with m < 2^25
+    if (nb <= 24) {
+        m = (uint32_t)a << (24 - nb);
+        e2 = nb - 24;
+    } else {
+        const int k = nb - 24;
+        const unsigned long long q = a >> k, rem = a & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+        m = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+        e2 = k;
+    }
+    if (m == 0x1000000u) {  // rounding carried into a new bit
+        m >>= 1;
+        e2 += 1;
+    }
+    const int be = 150 + e2 - sexp;  // biased exponent of m * 2^(e2 - sexp), m in [2^23, 2^24)
+    if (be >= 255) return __uint_as_float(sign | 0x7f800000u);
+    if (be <= 0) {
+        return __fmul_rn(__fmul_rn(__ll2float_rn(v), pow2f(-(sexp / 2))), pow2f(-(sexp - sexp / 2)));
+    }
+    return __uint_as_float(sign | ((uint32_t)be << 23) | (m & 0x7fffffu));
 }
 
 // One tile of the gather (columns [blk * T, blk * T + T)); shared by the
@@ -669,9 +715,9 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         run[v] = r;
     }
 
-    double Ssum[V], R[V], Dg[V];
+    df Ssum[V], R[V], Dg[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) Ssum[v] = R[v] = Dg[v] = 0.0;
+    for (int v = 0; v < V; v++) Ssum[v] = R[v] = Dg[v] = df_zero();
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
         const int64_t j = c0 + q;
@@ -696,9 +742,9 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                 const float dl = (float)pa.sc_prev[1 * KB + lane * V + v];
                 const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
                 qn.v[v] = qj;
-                Ssum[v] += (double)qj;
-                R[v] += fabs((double)qj - (double)qp.v[v]);
-                if (io == 0.0f) Dg[v] += (double)qj;
+                Ssum[v] = df_addf(Ssum[v], qj);
+                R[v] = df_addf(R[v], fabsf(__fsub_rn(qj, qp.v[v])));
+                if (io == 0.0f) Dg[v] = df_addf(Dg[v], qj);
             }
             stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
         }
@@ -725,9 +771,9 @@ __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_ini
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
     const int64_t end = a + tile < n ? a + tile : n;
-    double S[V], R[V], Dg[V];
+    df S[V], R[V], Dg[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = 0.0;
+    for (int v = 0; v < V; v++) S[v] = R[v] = Dg[v] = df_zero();
     const float un = 1.0f / (float)n;
     for (int64_t j = a + g; j < end; j += NG) {
         Vec<V> pv;
@@ -746,8 +792,8 @@ __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_ini
         }
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            S[v] += (double)pv.v[v];
-            if (io == 0.0f) Dg[v] += (double)pv.v[v];
+            S[v] = df_addf(S[v], pv.v[v]);
+            if (io == 0.0f) Dg[v] = df_addf(Dg[v], pv.v[v]);
         }
     }
     pr_block_reduce<KB, V>(S, R, Dg, pa, true);
