@@ -89,7 +89,7 @@ constexpr int kThreads = 256;
 static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
 // Columns per CTA of the gather kernel (k_gather's GatherShape).
 static int gather_tile(int kb, int v, const LaunchCfg&) {
-    const int G = kb / v, NG = 256 / G, CPT = std::max(4, G / 2);
+    const int G = kb / v, NG = 256 / G, CPT = std::max(2, G / 2);
     return NG * CPT;
 }
 

@@ -382,12 +382,13 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // scan is needed. A group of G = KB/V lanes owns CPT consecutive columns.
 // Each column's first S entries are loaded and summed by the same
 // straight-line predicated code in every lane (no divergence on the typical
-// column; longer columns finish in a short loop). Point terms P_j (a few
-// per column) sum in FP32 in storage order: an error there stays in y_j.
-// Interval events sum exactly in 64-bit fixed point (scale 2^s per CTA from
-// the CTA's own max |term| and term count), since the prefix of D carries any
-// error to every later column; the prefix across groups is an exact integer
-// block scan. y_j = P_j + I_j with I_j rounded once.
+// column; longer columns finish in a short loop). One pass: point terms P_j
+// (a few per column) sum in FP32 in storage order, since an error there stays
+// in y_j. Interval events and their prefix are carried as compensated
+// double-float values (two_sum steps, about 48 significant bits), because the
+// prefix carries any error to every later column of the tile. The block scan
+// runs in the same arithmetic, in a fixed order. y_j = P_j + I_j is rounded
+// once.
 // The kernel is launched so that it may start while the chain kernel is
 // still running (programmatic dependent launch): it reads only the structure
 // before griddepcontrol.wait, and reads z afterwards with coherent loads
@@ -400,9 +401,9 @@ struct GatherShape {
     static constexpr int NT = 256;                       // threads per CTA
     static constexpr int G = KB / V;                     // lanes per column group
     static constexpr int NG = NT / G;                    // column groups per CTA
-    static constexpr int CPT = G / 2 > 4 ? G / 2 : 4;    // consecutive columns per group
+    static constexpr int CPT = G / 2 > 2 ? G / 2 : 2;    // consecutive columns per group
     static constexpr int T = NG * CPT;                   // columns per CTA (a multiple of kCarryTile)
-    static constexpr int S = 4;                          // entry slots per column in straight-line code
+    static constexpr int S = 3;                          // entry slots per column in straight-line code
 };
 
 template <int KB>
@@ -484,74 +485,6 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
     }
 }
 
-// Power-of-two fixed point used for the interval events: every term is
-// rounded once to an integer multiple of 2^-s; sums of such integers are
-// exact and associative.
-__device__ __forceinline__ int fx_exponent(unsigned int maxbits, long long terms) {
-    // s with maxabs * terms * 2^s <= 2^62 (maxabs given by its float bits)
-    if (maxbits == 0) return 0;
-    const int e_m = (int)((maxbits >> 23) & 0xff) - 126;      // maxabs < 2^e_m
-    const int e_t = 64 - __clzll((unsigned long long)terms);  // terms < 2^e_t
-    const int sexp = 62 - e_m - e_t;
-    return sexp > 100 ? 100 : (sexp < -100 ? -100 : sexp);
-}
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // |e| <= 126
-
-// round_to_nearest_even(v * 2^sexp) as a 64-bit integer, from the IEEE fields
-// of v with integer instructions only. (The 64-bit float <-> integer
-// conversion instructions run on the FP64 pipe, which this GPU provisions at
-// 2 operations per SM per cycle; these helpers keep the gather off it.)
-// Zero and subnormal v give 0: |v| < 2^-126 and sexp <= 100 put the scaled
-// value below 2^-26. The scale choice above bounds every term's shift by 38.
-__device__ __forceinline__ long long to_fx(float v, int sexp) {
-    const uint32_t b = __float_as_uint(v);
-    const int ex = (int)((b >> 23) & 0xffu);
-    const uint32_t m = (b & 0x7fffffu) | 0x800000u;  // 24-bit significand
-    const int sh = ex - 150 + sexp;                   // v * 2^sexp = m * 2^sh
-    unsigned long long mag;
-    if (ex == 0 || ex == 255 || sh < -25) {
-        mag = 0;  // zero, subnormal, or too small to reach 1/2; non-finite terms are reported apart
-    } else if (sh >= 0) {
-        mag = (unsigned long long)m << (sh > 40 ? 40 : sh);
-    } else {
-        const int k = -sh;  // 1..25
-        const uint32_t q = m >> k, rem = m & ((1u << k) - 1u), half = 1u << (k - 1);
-        mag = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
-    }
-    return (b >> 31) ? -(long long)mag : (long long)mag;
-}
-
-// round_to_nearest_even(v * 2^-sexp) as a float, by normalising the 64-bit
-// integer with integer instructions; a result below the normal range takes
-// the conversion instruction instead (never on typical inputs).
-__device__ __forceinline__ float from_fx(long long v, int sexp) {
-    if (v == 0) return 0.f;
-    const uint32_t sign = v < 0 ? 0x80000000u : 0u;
-    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int nb = 64 - __clzll(a);  // significant bits, 1..64
-    uint32_t m;
-    int e2;  // |v| ~= m * 2^e2 with m < 2^25
-    if (nb <= 24) {
-        m = (uint32_t)a << (24 - nb);
-        e2 = nb - 24;
-    } else {
-        const int k = nb - 24;
-        const unsigned long long q = a >> k, rem = a & ((1ull << k) - 1ull), half = 1ull << (k - 1);
-        m = (uint32_t)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
-        e2 = k;
-    }
-    if (m == 0x1000000u) {  // rounding carried into a new bit
-        m >>= 1;
-        e2 += 1;
-    }
-    const int be = 150 + e2 - sexp;  // biased exponent of m * 2^(e2 - sexp), m in [2^23, 2^24)
-    if (be >= 255) return __uint_as_float(sign | 0x7f800000u);
-    if (be <= 0) {
-        return __fmul_rn(__fmul_rn(__ll2float_rn(v), pow2f(-(sexp / 2))), pow2f(-(sexp - sexp / 2)));
-    }
-    return __uint_as_float(sign | ((uint32_t)be << 23) | (m & 0x7fffffu));
-}
-
 // One tile of the gather (columns [blk * T, blk * T + T)); shared by the
 // one-graph and the multi-graph kernels.
 template <int KB, int V, int EPI>
@@ -563,10 +496,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
-    __shared__ long long run_s[KB];
-    __shared__ long long wtot_s[NW][KB];
-    __shared__ unsigned int wmax_s[NW];
-    __shared__ uint32_t tile_beg_s, tile_end_s;
+    __shared__ df run_s[KB];
+    __shared__ df wtot_s[NW][KB];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t a = blk * T;
@@ -577,12 +508,10 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     uint32_t cp[CPT + 1];
 #pragma unroll
     for (int q = 0; q <= CPT; q++) cp[q] = __ldg(colp + (c0 + q < end ? c0 + q : end));
-    if (threadIdx.x == 0) {
-        tile_beg_s = __ldg(colp + a);
-        tile_end_s = __ldg(colp + end);
-    }
     const int64_t ct = a / kCarryTile;
     const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
+    // carry sources of this tile (warp 0; the first 32 now, any further ones later)
+    const uint32_t csrc = (warp == 0 && cr0 + lane32 < cr1) ? __ldg(carry + cr0 + lane32) : 0u;
     uint32_t w[CPT][S];
 #pragma unroll
     for (int q = 0; q < CPT; q++)
@@ -593,17 +522,40 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
     }
 
-    // pass 1: the terms of up to S entries per column, uniformly for all
-    // columns (predicated straight-line code); point terms (+-z of residual /
-    // dropped ids, a few per column) sum in FP32 in storage order; for the
-    // interval events only max |term| is taken here
+    // running interval sum at column a: the carry sources' z (warp 0)
+    if (warp == 0) {
+        df acc[KB];
+#pragma unroll
+        for (int c = 0; c < KB; c++) acc[c] = df_zero();
+        if (cr0 + lane32 < cr1) {
+            const float* zr = z + (int64_t)csrc * ldz;
+#pragma unroll
+            for (int c = 0; c < KB; c++) acc[c] = df_addf(acc[c], __ldca(zr + c));
+        }
+        for (uint32_t e = cr0 + 32 + lane32; e < cr1; e += 32) {  // rare: more than 32 open intervals
+            const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
+#pragma unroll
+            for (int c = 0; c < KB; c++) acc[c] = df_addf(acc[c], __ldca(zr + c));
+        }
+#pragma unroll
+        for (int c = 0; c < KB; c++) {
+            for (int o = 16; o > 0; o >>= 1) acc[c] = df_add(acc[c], df_shfl_xor(acc[c], o));
+            if (lane32 == 0) run_s[c] = acc[c];
+        }
+    }
+
+    // one pass over each column's entries: points in FP32, events compensated
     float P[CPT][V];
-    Vec<V> ev[CPT][S];
-    unsigned int mx = 0;
+    df D[CPT][V], tot[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) tot[v] = df_zero();
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
 #pragma unroll
-        for (int v = 0; v < V; v++) P[q][v] = 0.f;
+        for (int v = 0; v < V; v++) {
+            P[q][v] = 0.f;
+            D[q][v] = df_zero();
+        }
 #pragma unroll
         for (int t = 0; t < S; t++) {
             const bool valid = cp[q] + t < cp[q + 1];
@@ -612,16 +564,15 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             for (int v = 0; v < V; v++) zv.v[v] = 0.f;
             if (valid) zv = ldv_ca<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
             const uint32_t tag = w[q][t] >> kIdBits;
-            const bool point = valid && tag < 2;
+            const bool point = tag < 2;
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
                 P[q][v] += point ? val : 0.f;
-                ev[q][t].v[v] = (valid && !point) ? val : 0.f;
-                mx = max(mx, __float_as_uint(ev[q][t].v[v]) & 0x7fffffffu);
+                if (!point) D[q][v] = df_addf(D[q][v], val);
             }
         }
-        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // rare: more than S entries
+        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // longer columns
             const uint32_t we = __ldg(tent + e);
             Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
             const uint32_t tag = we >> kIdBits;
@@ -629,90 +580,44 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             for (int v = 0; v < V; v++) {
                 const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
                 if (tag < 2) P[q][v] += val;
-                else mx = max(mx, __float_as_uint(val) & 0x7fffffffu);
+                else D[q][v] = df_addf(D[q][v], val);
             }
         }
-    }
-    // carry sources (warp 0): terms of the running interval sum at column a
-    if (warp == 0) {
-        for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
-            const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
 #pragma unroll
-            for (int c = 0; c < KB; c++) mx = max(mx, __float_as_uint(__ldca(zr + c)) & 0x7fffffffu);
-        }
+        for (int v = 0; v < V; v++) tot[v] = df_add(tot[v], D[q][v]);
     }
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane32 == 0) wmax_s[warp] = mx;
-    __syncthreads();
-#pragma unroll
-    for (int w2 = 0; w2 < NW; w2++) mx = max(mx, wmax_s[w2]);
-    const bool bad = mx >= 0x7f800000u;  // a non-finite term: the product is not defined
-    // every partial sum below has at most (entries of the tile + carry sources) terms
-    const long long terms = (long long)(tile_end_s - tile_beg_s) + (cr1 - cr0) + 2;
-    const int sexp = fx_exponent(bad ? 0u : mx, terms);
 
-    // pass 2: exact event sums per column and the running interval prefix
-    long long D[CPT][V], tot[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) tot[v] = 0;
-#pragma unroll
-    for (int q = 0; q < CPT; q++) {
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            long long d = 0;
-#pragma unroll
-            for (int t = 0; t < S; t++) d += to_fx(ev[q][t].v[v], sexp);
-            D[q][v] = d;
-        }
-        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {
-            const uint32_t we = __ldg(tent + e);
-            if ((we >> kIdBits) < 2) continue;
-            Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
-#pragma unroll
-            for (int v = 0; v < V; v++) D[q][v] += to_fx(((we >> kIdBits) & 1) ? -zv.v[v] : zv.v[v], sexp);
-        }
-#pragma unroll
-        for (int v = 0; v < V; v++) tot[v] += D[q][v];
-    }
-    if (warp == 0) {
-        long long acc[KB];
-#pragma unroll
-        for (int c = 0; c < KB; c++) acc[c] = 0;
-        for (uint32_t e = cr0 + lane32; e < cr1; e += 32) {
-            const float* zr = z + (int64_t)__ldg(carry + e) * ldz;
-#pragma unroll
-            for (int c = 0; c < KB; c++) acc[c] += to_fx(__ldca(zr + c), sexp);
-        }
-#pragma unroll
-        for (int c = 0; c < KB; c++) {
-            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-            if (lane32 == 0) run_s[c] = acc[c];
-        }
-    }
-    // exclusive prefix of the group totals across the block (exact)
-    long long inc[V];
+    // exclusive prefix of the group totals across the block, in a fixed order:
+    // carry, then the warps before this one, then the groups before this one
+    df inc[V];
 #pragma unroll
     for (int v = 0; v < V; v++) inc[v] = tot[v];
 #pragma unroll
     for (int d = G; d < 32; d <<= 1)
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            const long long o = __shfl_up_sync(0xffffffffu, inc[v], d);
-            if (lane32 >= d) inc[v] += o;
+            const df o = df_shfl_up(inc[v], d);
+            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
         }
     if (lane32 >= 32 - G) {
 #pragma unroll
         for (int v = 0; v < V; v++) wtot_s[warp][lane * V + v] = inc[v];
     }
-    __syncthreads();
-    long long run[V];
+    df excl[V];
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        long long r = run_s[lane * V + v] + inc[v] - tot[v];
+        const df o = df_shfl_up(inc[v], G);
+        excl[v] = lane32 >= G ? o : df_zero();
+    }
+    __syncthreads();
+    df run[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        df r = run_s[lane * V + v];
 #pragma unroll
         for (int w2 = 0; w2 < NW; w2++)
-            if (w2 < warp) r += wtot_s[w2][lane * V + v];
-        run[v] = r;
+            if (w2 < warp) r = df_add(r, wtot_s[w2][lane * V + v]);
+        run[v] = df_add(r, excl[v]);
     }
 
     df Ssum[V], R[V], Dg[V];
@@ -724,8 +629,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] += D[q][v];
-            out.v[v] = bad ? __int_as_float(0x7fc00000) : __fadd_rn(P[q][v], from_fx(run[v], sexp));
+            run[v] = df_add(run[v], D[q][v]);
+            out.v[v] = df_val(df_addf(run[v], P[q][v]));
         }
         if (j >= end) continue;
         if constexpr (EPI == 0) {
