@@ -143,6 +143,20 @@ int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out);
 
 /* -------------------------------------------------------------- device side */
 
+/* The pull's work items, on the host (no GPU needed): each row's difference
+ * row with the intervals shorter than min_len expanded into single entries
+ * (a dropped id has bit 31 set), cut into items of at most `item` entries;
+ * intervals at least min_len long kept as (start, length) pairs. Sizes first,
+ * then the arrays into caller buffers: pent[entries], istart[items + 1]
+ * (item k covers pent[istart[k], istart[k + 1])), irow[n + 1] (items of row
+ * i: [irow[i], irow[i + 1])), lrow[n + 1] and lint[2 * intervals] (start,
+ * length). bvg_upload builds the same arrays for the launch configuration's
+ * pull_item and prefix_min_len. Errors: INVALID_ARG, OOM, UNSUPPORTED. */
+int bvg_pull_items_size(const bvg_host_graph* g, int32_t item, int32_t min_len, int64_t* entries, int64_t* items,
+                        int64_t* intervals);
+int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_t min_len, uint32_t* pent, uint32_t* istart,
+                        uint32_t* irow, uint32_t* lrow, uint32_t* lint);
+
 /* Builds the device layout of `g` (row-major difference rows for A x^T, the
  * same entries grouped by column for x A, per-row reference offsets and
  * chain depths, 1/outdeg) and copies it to the current device on `stream`.
@@ -151,9 +165,11 @@ int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out);
  * by the caller (bvg_free_dev). Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_upload(const bvg_host_graph* g, void* stream, bvg_dev_graph** out);
 
-/* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j, evaluated per
- * row tile with the chains resolved in shared memory. x, y: device n x k,
- * leading dimension ld. Asynchronous. Errors: INVALID_ARG, CUDA. */
+/* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j. The row sums
+ * sum_j A'_ij x_j are formed per work item (bvg_pull_items_size), then each
+ * row tile adds its rows' partials and resolves the chains in shared memory.
+ * x, y: device n x k, leading dimension ld. Asynchronous. Errors:
+ * INVALID_ARG, OOM (first call with a wider column block), CUDA. */
 int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
 /* y = x A (push, Proposition 1 read for the left product): z_k = sum of x_i
@@ -288,11 +304,13 @@ void bvg_free_mlp(bvg_mlp* net);
 /* Launch configuration of a device graph (what bvg_autotune chooses; the
  * results of every setting are the same up to the product tolerance). */
 typedef struct {
-    int32_t pull_tile;      /* rows per CTA of the pull kernel: power of two in [64, 2048] (default 512) */
+    int32_t pull_tile;      /* rows per CTA of the pull's row pass: power of two in [64, 2048] (default 512) */
     int32_t pull_prefix;    /* pull interval sums from a prefix of x: -1 auto (mean interval >= 32), 0 off, 1 on */
-    int32_t prefix_min_len; /* with the prefix on, intervals at least this long use it (default 16) */
+    int32_t prefix_min_len; /* pull: intervals at least this long stay (start, length) and are summed from the
+                               prefix of x; shorter ones are expanded into work items (default 32) */
     int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */
     int32_t col_block;      /* widest column block of a product: power of two in [1, 32] (default 32) */
+    int32_t pull_item;      /* pull: entries per work item, 4, 8 or 16 (default 8) */
 } bvg_launch_config;
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
@@ -301,8 +319,10 @@ int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
  * candidate launch configuration (CUDA events on `stream`, median of 7 after
  * 2 warm-up calls, warm caches): first the push (x A) over the widest column
  * block (the largest power of two <= min(k, 32) and up to three halvings)
- * times gather overlap on/off, then the pull (A x^T) over rows per CTA
- * {128, 256, 512, 1024} times prefix off / on from interval length 8 or 32.
+ * times gather overlap on/off, then the pull (A x^T) over entries per work
+ * item {4, 8, 16} times rows per CTA of the row pass {256, 512} times the
+ * length from which intervals stay unexpanded (32; also 16 and "never" when
+ * the graph has intervals; rebuilding the items is part of the search).
  * It applies the fastest choice to g (bvg_get_config shows it). With
  * cache_path != NULL it first looks the choice up in that JSON file under
  * the key "<device name>/sm<count>/<layout fingerprint>/k<k>" and, after a
@@ -338,6 +358,7 @@ int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);
  * (interval sources open at each 128-column tile start), structure bytes. */
 typedef struct {
     int64_t n, m, words, col_entries, carry_tiles, carry_entries, structure_bytes;
+    int64_t pull_entries, pull_items, pull_intervals;  /* the pull's work items (see bvg_pull_items_size) */
 } bvg_layout_info;
 int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 

@@ -39,7 +39,7 @@ EXPORTED = [
     "bvg_mlp_get_params", "bvg_features", "bvg_mlp_predict", "bvg_mlp_grad", "bvg_mlp_adam", "bvg_warmstart_train",
     "bvg_warmstart_predict", "bvg_free_mlp", "bvg_batch_create", "bvg_batch_size", "bvg_batch_spmv_xA",
     "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
-    "bvg_autotune_cache_store",
+    "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill",
 ]
 
 
@@ -67,7 +67,7 @@ class GraphStats(ctypes.Structure):
 
 class LayoutInfo(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "m", "words", "col_entries", "carry_tiles", "carry_entries",
-                                      "structure_bytes")]
+                                      "structure_bytes", "pull_entries", "pull_items", "pull_intervals")]
 
 
 class LayoutView(ctypes.Structure):
@@ -78,7 +78,7 @@ class LayoutView(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
-                ("col_block", _I32)]
+                ("col_block", _I32), ("pull_item", _I32)]
 
 
 class AutotuneInfo(ctypes.Structure):
@@ -161,6 +161,9 @@ def load(build_if_needed: bool = True):
                                            ctypes.POINTER(_I32)], ctypes.c_int),
             "bvg_autotune_cache_store": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(LaunchConfig),
                                           ctypes.c_double, ctypes.c_double], ctypes.c_int),
+            "bvg_pull_items_size": ([_P, _I32, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                     ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_pull_items_fill": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -642,3 +645,21 @@ def bvg_autotune_cache_store(path, key: str, config: dict, push_us: float = 0.0,
     c = LaunchConfig(**{f: int(config[f]) for f, _ in LaunchConfig._fields_})
     _check(load().bvg_autotune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c), push_us, pull_us),
            "bvg_autotune_cache_store")
+
+
+def bvg_pull_items(hg: HostGraph, item: int = 8, min_len: int = 32) -> dict:
+    """The pull's work items for a host graph (no GPU needed)."""
+    lib = load()
+    e, k, m = _I64(), _I64(), _I64()
+    _check(lib.bvg_pull_items_size(hg.ptr, item, min_len, ctypes.byref(e), ctypes.byref(k), ctypes.byref(m)),
+           "bvg_pull_items_size")
+    n = bvg_host_size(hg)[0]
+    out = {"pent": np.zeros(max(e.value, 1), np.uint32), "istart": np.zeros(k.value + 1, np.uint32),
+           "irow": np.zeros(n + 1, np.uint32), "lrow": np.zeros(n + 1, np.uint32),
+           "lint": np.zeros(max(2 * m.value, 1), np.uint32)}
+    _check(lib.bvg_pull_items_fill(hg.ptr, item, min_len, *[out[f].ctypes.data for f in
+                                                            ("pent", "istart", "irow", "lrow", "lint")]),
+           "bvg_pull_items_fill")
+    out["pent"] = out["pent"][:e.value]
+    out["lint"] = out["lint"][:2 * m.value].reshape(-1, 2)
+    return out

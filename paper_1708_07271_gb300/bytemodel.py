@@ -9,7 +9,11 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
   push_chain   4n (descendant masks) + 4kn (x) + 4kn (z)
   push_gather  4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
                + 4*carry_entries + 4kn (z) + 4kn (y)
-  pull         n (meta) + 4(n+1) (row offsets) + 4*words + 4kn (x) + 4kn (y)
+  pull         n (meta) + 4(n+1) (item offsets per row) + 4(items+1) (item starts)
+               + 4*pull_entries (expanded entries) + 4(n+1) + 8*pull_intervals
+               (kept intervals) + 4kn (x) + 4kn (y); the items' partial sums
+               (8 bytes per item and right-hand side, written then read back)
+               are scratch that stays in L2 and are not counted
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
   push_fused   4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
                + 4*carry_entries + 4n (descendant masks) + 4kn (x) + 4kn (y)
@@ -34,7 +38,8 @@ def push_gather(L: dict, k: int) -> int:
 
 def pull(L: dict, k: int) -> int:
     n = L["n"]
-    return n + 4 * (n + 1) + 4 * L["words"] + 8 * k * n
+    return (n + 4 * (n + 1) + 4 * (L["pull_items"] + 1) + 4 * L["pull_entries"] + 4 * (n + 1)
+            + 8 * L["pull_intervals"] + 8 * k * n)
 
 
 def csr(n: int, m: int, k: int) -> int:

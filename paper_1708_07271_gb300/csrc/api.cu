@@ -172,14 +172,36 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
             TraceScope ts(g, "prefix_blocks", st);
             k_prefix_blocks<KB><<<1, 256, 0, st>>>(bhi, blo, (int)nb);
         }
-        pf = PrefixArgs{lhi, llo, bhi, blo, Sh::PB, g->cfg.prefix_min_len};
+        pf = PrefixArgs{lhi, llo, bhi, blo, Sh::PB, 0};
+    }
+    float2* part = reinterpret_cast<float2*>(g->part);
+    if (g->nitems > 0) {
+        constexpr int G = KB / V;
+        const int64_t grid = (g->nitems + 256 / G - 1) / (256 / G);
+        TraceScope ts(g, "pull_items", st);
+        switch (g->pull_built_item) {
+            case 4: k_pull_items<KB, V, 4><<<(unsigned)grid, 256, 0, st>>>(g->pent, g->istart, g->nitems, x, ldx, part); break;
+            case 16: k_pull_items<KB, V, 16><<<(unsigned)grid, 256, 0, st>>>(g->pent, g->istart, g->nitems, x, ldx, part); break;
+            default: k_pull_items<KB, V, 8><<<(unsigned)grid, 256, 0, st>>>(g->pent, g->istart, g->nitems, x, ldx, part); break;
+        }
     }
     const int tile = pull_tile(KB, g->cfg);
     const size_t smem = (size_t)(tile + kHalo) * KB * sizeof(df);
-    set_smem(k_pull<KB, V>, smem);
+    set_smem(k_pull_rows<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
-    TraceScope ts(g, "pull", st);
-    k_pull<KB, V><<<(unsigned)grid, kThreads, smem, st>>>(g->meta, g->rowp, g->ent, x, ldx, y, ldy, g->n, tile, pf);
+    TraceScope ts(g, "pull_rows", st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g->nitems > 0 ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_pull_rows<KB, V>, (const uint8_t*)g->meta, (const uint32_t*)g->irow, (const float2*)part,
+                       (const uint32_t*)g->lrow, (const uint32_t*)g->lint, x, ldx, y, ldy, g->n, tile, pf);
 }
 
 template <int KB, int V>
@@ -263,7 +285,55 @@ static int ensure_prefix(bvg_dev_graph* g, int kb) {
 }
 
 static bool use_prefix(const bvg_dev_graph* g) {
-    return g->cfg.pull_prefix == 1 || (g->cfg.pull_prefix < 0 && g->mean_interval >= 32.0);
+    return g->nlint > 0 && g->cfg.pull_prefix != 0;  // only kept (long) intervals read the prefix
+}
+
+// Partial sums of the pull items for kb columns.
+static int ensure_part(bvg_dev_graph* g, int kb) {
+    if (g->part_kcap >= kb) return BVG_OK;
+    if (g->part) cudaFree(g->part);
+    g->part = nullptr;
+    g->part_kcap = 0;
+    int rc = dev_alloc((void**)&g->part, (size_t)std::max<int64_t>(g->nitems, 1) * kb * 2 * sizeof(float), nullptr);
+    if (rc) return rc;
+    g->part_kcap = kb;
+    return BVG_OK;
+}
+
+// Builds the pull work items (see build_pull_items) from the host copy of the
+// difference rows and copies them to the device, replacing earlier arrays;
+// synchronous.
+static int build_pull_items(bvg_dev_graph* g, int item, int min_len, cudaStream_t st) {
+    PullItems P;
+    int rc0 = build_pull_items(g->host_rowp.data(), g->host_ent.data(), g->n, item, min_len, P);
+    if (rc0) return rc0;
+    std::vector<uint32_t>& pent = P.pent;
+    std::vector<uint32_t>& istart = P.istart;
+    std::vector<uint32_t>& irow = P.irow;
+    std::vector<uint32_t>& lrow = P.lrow;
+    std::vector<uint32_t>& lint = P.lint;
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));  // earlier products may still read the old arrays
+    for (uint32_t** b : {&g->pent, &g->istart, &g->irow, &g->lrow, &g->lint}) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    if (g->part) cudaFree(g->part);
+    g->part = nullptr;
+    g->part_kcap = 0;
+    g->npent = (int64_t)pent.size();
+    g->nitems = (int64_t)istart.size() - 1;
+    g->nlint = (int64_t)lint.size() / 2;
+    int rc;
+    int64_t bytes = 0;
+    if ((rc = upload_vec(&g->pent, pent, st, &bytes)) || (rc = upload_vec(&g->istart, istart, st, &bytes)) ||
+        (rc = upload_vec(&g->irow, irow, st, &bytes)) || (rc = upload_vec(&g->lrow, lrow, st, &bytes)) ||
+        (rc = upload_vec(&g->lint, lint, st, &bytes)) || (rc = ensure_part(g, 1)))
+        return rc;
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    g->pull_bytes = bytes;
+    g->pull_built_item = item;
+    g->pull_built_minlen = min_len;
+    return BVG_OK;
 }
 
 static int64_t max_grid(const bvg_dev_graph* g) {
@@ -374,6 +444,12 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
+        g->host_rowp = L->rowp;
+        g->host_ent = L->ent;
+        if ((rc = build_pull_items(g, g->cfg.pull_item, g->cfg.prefix_min_len, st))) {
+            bvg_free_dev(g);
+            return rc;
+        }
         if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, sizeof(unsigned int), nullptr))) {
             bvg_free_dev(g);
             return rc;
@@ -397,7 +473,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
-                    g->s.feat_tmp, g->s.wfeat};
+                    g->s.feat_tmp, g->s.wfeat, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -472,6 +548,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
     out->prefix_min_len = g->cfg.prefix_min_len;
     out->gather_pdl = g->cfg.gather_pdl;
     out->col_block = g->cfg.col_block;
+    out->pull_item = g->cfg.pull_item;
     return BVG_OK;
 }
 
@@ -479,16 +556,22 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     if (!g || !in) return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: NULL argument");
     if (in->pull_tile < 64 || in->pull_tile > 2048 || (in->pull_tile & (in->pull_tile - 1)) ||
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
-        in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)))
+        in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)) ||
+        (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16))
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
                                          "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
-                                         "of two in [1, 32]");
+                                         "of two in [1, 32], pull_item in {4, 8, 16}");
+    if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen) {
+        int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, nullptr);
+        if (rc) return rc;
+    }
     if (in->gather_pdl != g->cfg.gather_pdl) drop_pr_graph(g);  // the PageRank graph was captured with the old launch
     g->cfg.pull_tile = in->pull_tile;
     g->cfg.pull_prefix = in->pull_prefix;
     g->cfg.prefix_min_len = in->prefix_min_len;
     g->cfg.gather_pdl = in->gather_pdl;
     g->cfg.col_block = in->col_block;
+    g->cfg.pull_item = in->pull_item;
     return BVG_OK;
 }
 
@@ -500,7 +583,10 @@ extern "C" int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out) {
     out->col_entries = g->ntent;
     out->carry_tiles = (g->n + kCarryTile - 1) / kCarryTile;
     out->carry_entries = g->ncarry;
-    out->structure_bytes = g->bytes;
+    out->structure_bytes = g->bytes + g->pull_bytes;
+    out->pull_entries = g->npent;
+    out->pull_items = g->nitems;
+    out->pull_intervals = g->nlint;
     return BVG_OK;
 }
 
@@ -517,7 +603,7 @@ extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int
     const bool prefix = use_prefix(g);
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
-        if (prefix && (rc = ensure_prefix(gm, kb))) return rc;
+        if ((prefix && (rc = ensure_prefix(gm, kb))) || (rc = ensure_part(gm, kb))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
         BVG_KV_CASES(launch_pull, g, x + c0, ld, y + c0, ld, prefix, st);
         c0 += kb;

@@ -4,9 +4,9 @@
 //
 // The searched space: the widest column block (k right-hand sides run as
 // column blocks of at most this many), whether the push gather overlaps the
-// chain kernel (programmatic dependent launch), the pull's rows per CTA, and
-// whether (and from which interval length) the pull takes interval sums from
-// a prefix of x. Every setting gives the same products up to the product
+// chain kernel (programmatic dependent launch), the pull's entries per work
+// item and rows per CTA of its row pass, and from which length on the pull
+// keeps intervals unexpanded (summed from a prefix of x). Every setting gives the same products up to the product
 // tolerance; only the time differs. Timing runs on warm caches (the
 // configuration is chosen for repeated products, as in PageRank).
 #include <cuda_runtime.h>
@@ -95,7 +95,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                     if (!sc.eat('{')) return false;
                     std::string key;
                     CacheEntry e{};
-                    e.cfg = {512, -1, 16, 1, 32};
+                    e.cfg = {512, -1, 32, 1, 32, 8};
                     int fields = 0;
                     do {
                         std::string f;
@@ -111,10 +111,11 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                         else if (f == "prefix_min_len") e.cfg.prefix_min_len = (int32_t)v, fields++;
                         else if (f == "gather_pdl") e.cfg.gather_pdl = (int32_t)v, fields++;
                         else if (f == "col_block") e.cfg.col_block = (int32_t)v, fields++;
+                        else if (f == "pull_item") e.cfg.pull_item = (int32_t)v, fields++;
                         else if (f == "push_us") e.push_us = v;
                         else if (f == "pull_us") e.pull_us = v;
                     } while (sc.eat(','));
-                    if (!sc.eat('}') || key.empty() || fields != 5) return false;
+                    if (!sc.eat('}') || key.empty() || fields != 6) return false;
                     out[key] = e;
                 } while (sc.eat(','));
                 if (!sc.eat(']')) return false;
@@ -160,9 +161,10 @@ int write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
         char buf[512];
         std::snprintf(buf, sizeof buf,
                       "%s\n  {\"key\": \"%s\", \"pull_tile\": %d, \"pull_prefix\": %d, \"prefix_min_len\": %d, "
-                      "\"gather_pdl\": %d, \"col_block\": %d, \"push_us\": %.3f, \"pull_us\": %.3f}",
+                      "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_us\": %.3f, "
+                      "\"pull_us\": %.3f}",
                       first ? "" : ",", json_escape(kv.first).c_str(), c.pull_tile, c.pull_prefix, c.prefix_min_len,
-                      c.gather_pdl, c.col_block, kv.second.push_us, kv.second.pull_us);
+                      c.gather_pdl, c.col_block, c.pull_item, kv.second.push_us, kv.second.pull_us);
         o << buf;
         first = false;
     }
@@ -340,7 +342,8 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
             }
         }
     }
-    // pull: rows per CTA x prefix policy, with the chosen column block
+    // pull: entries per work item x rows per CTA of the row pass x which
+    // intervals stay unexpanded (summed from the prefix), with the chosen column block
     bvg_launch_config b2 = best;
     if ((rc = bvg_set_config(g, &b2)) || (rc = time_op(pull, st, t, &g->tune.pull_us_default))) {
         bvg_set_config(g, &base);
@@ -348,24 +351,27 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
         return rc;
     }
     double best_pull = 1e300;
-    std::vector<std::pair<int, int>> prefix_opts = {{0, 16}};
-    if (g->mean_interval > 0) prefix_opts.insert(prefix_opts.end(), {{1, 8}, {1, 32}});
-    for (int tile : {128, 256, 512, 1024}) {
-        for (auto po : prefix_opts) {
-            bvg_launch_config c = best;
-            c.pull_tile = tile;
-            c.pull_prefix = po.first;
-            c.prefix_min_len = po.second;
-            double us = 0;
-            if ((rc = bvg_set_config(g, &c)) || (rc = time_op(pull, st, t, &us))) {
-                bvg_set_config(g, &base);
-                release();
-                return rc;
-            }
-            g->tune.candidates++;
-            if (us < best_pull) {
-                best_pull = us;
-                b2 = c;
+    std::vector<int> minlens = {32};
+    if (g->mean_interval > 0) minlens.insert(minlens.end(), {16, 1 << 20});  // 1 << 20: expand every interval
+    for (int ml : minlens) {
+        for (int item : {4, 8, 16}) {
+            for (int tile : {256, 512}) {
+                bvg_launch_config c = best;
+                c.pull_tile = tile;
+                c.pull_item = item;
+                c.prefix_min_len = ml;
+                c.pull_prefix = -1;
+                double us = 0;
+                if ((rc = bvg_set_config(g, &c)) || (rc = time_op(pull, st, t, &us))) {
+                    bvg_set_config(g, &base);
+                    release();
+                    return rc;
+                }
+                g->tune.candidates++;
+                if (us < best_pull) {
+                    best_pull = us;
+                    b2 = c;
+                }
             }
         }
     }

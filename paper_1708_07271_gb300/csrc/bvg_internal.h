@@ -49,6 +49,12 @@ struct HostLayout {
     bool built = false;
 };
 
+// Pull work items built from row-major difference rows (see build_pull_items).
+struct PullItems {
+    std::vector<uint32_t> pent, istart, irow, lrow, lint;
+};
+int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out);
+
 }  // namespace bvg
 
 struct bvg_host_graph {
@@ -77,9 +83,10 @@ namespace bvg {
 
 // Launch configuration of the product kernels (autotuned per graph and k).
 struct LaunchCfg {
-    int pull_tile = 512;        // rows per CTA of the pull kernel
-    int pull_prefix = -1;       // interval sums of the pull from the prefix of x: -1 auto, 0 off, 1 on
-    int prefix_min_len = 16;    // with the prefix on, intervals at least this long use it
+    int pull_tile = 512;        // rows per CTA of the pull's row pass
+    int pull_prefix = -1;       // kept intervals summed from the prefix of x: -1 auto (on), 0 off, 1 on
+    int prefix_min_len = 32;    // pull: intervals at least this long stay (start, length); shorter ones are expanded
+    int pull_item = 8;          // pull: entries per work item (4, 8 or 16)
     int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
     int col_block = 32;         // widest column block of a product (power of two <= 32)
 };
@@ -144,7 +151,21 @@ struct bvg_dev_graph {
     uint32_t* carry = nullptr;      // source rows of intervals open at a carry-tile start
     int64_t ncarry = 0;
     float* inv_outdeg = nullptr;    // 1/|v_i|, 0 for rows without successors
-    double mean_interval = 0.0;     // mean interval length (prefix policy)
+    double mean_interval = 0.0;     // mean interval length
+    // pull work items: the difference rows with intervals shorter than
+    // cfg.prefix_min_len expanded into single entries, cut into items of at
+    // most cfg.pull_item entries; longer intervals kept as (start, length)
+    uint32_t* pent = nullptr;       // expanded entries: id, bit 31 set for a dropped id
+    uint32_t* istart = nullptr;     // nitems + 1: item k covers pent[istart[k], istart[k + 1])
+    uint32_t* irow = nullptr;       // n + 1: items of row i are [irow[i], irow[i + 1])
+    uint32_t* lrow = nullptr;       // n + 1: kept intervals of row i are [lrow[i], lrow[i + 1])
+    uint32_t* lint = nullptr;       // 2 per kept interval: start, length
+    int64_t npent = 0, nitems = 0, nlint = 0;
+    float* part = nullptr;          // per item partial sums, compensated (hi, lo) x part_kcap
+    int64_t part_kcap = 0;
+    int pull_built_item = 0, pull_built_minlen = 0;  // parameters the item arrays were built with
+    int64_t pull_bytes = 0;                          // device bytes of the item arrays
+    std::vector<uint32_t> host_rowp, host_ent;       // the difference rows, to rebuild the items
     int64_t bytes = 0;
     bvg::LaunchCfg cfg;
     uint64_t fingerprint = 0;  // hash of the layout (autotune cache key)

@@ -166,49 +166,77 @@ struct PrefixArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Pull: y = A x^T (Sec. 4). A CTA owns rows [a, a + tile). It first forms the
-// correction sums c_i = sum_j A'_ij x_j for rows [a - kHalo, a + tile) into
-// shared memory (dropped ids subtract, residual ids add, an interval (s, len)
-// adds x_s + ... + x_{s+len-1}: summed directly, or from the prefix of x when
-// len >= min_len), then resolves each owned row's chain
-// y_i = c_i + y_{r_i} = c_i + c_{r_i} + c_{r_{r_i}} + ... with at most
-// max_chain links, all inside the CTA (a chain never leaves kHalo rows).
-// The sums are compensated (hi, lo) pairs; the chain is added from its root
-// outwards, i.e. in the association of the sequential algorithm. A row's
-// first S words are loaded by straight-line predicated code.
+// Pull: y = A x^T (Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j, in two kernels.
+// The row sums c_i = sum_j A'_ij x_j are cut into work items of at most W
+// entries (dropped ids subtract, residual ids and the members of intervals
+// shorter than a threshold add; the rows of A' differ widely in length, so the
+// items, not the rows, are the unit of parallel work):
+//   k_pull_items: one item per group of G = KB/V lanes, W straight-line
+//     predicated slots (the same instructions for every item), its
+//     compensated (hi, lo) partial sum written out;
+//   k_pull_rows: a CTA owns rows [a, a + tile); it sums the partials of its
+//     rows and of the kHalo rows before them (plus their kept intervals,
+//     from the prefix of x or member by member) into shared memory, then
+//     resolves each owned row's chain y_i = c_i + c_{r_i} + c_{r_{r_i}} + ...
+//     (at most max_chain links, never leaving the kHalo rows), added from the
+//     root outwards: the association of the sequential algorithm.
 // ---------------------------------------------------------------------------
 template <int KB, int V>
-__device__ __forceinline__ void pull_interval(df (&acc)[V], uint32_t s0, uint32_t len, const float* __restrict__ x,
-                                              int64_t ldx, int lane, const PrefixArgs& pf) {
-    if (pf.lhi && len >= (uint32_t)pf.min_len) {
-        const uint32_t e0 = s0 + len;
-        const int64_t bs = s0 / pf.block, be = e0 / pf.block;
-        Vec<V> lsh = ldv<V>(pf.lhi + (int64_t)s0 * KB + lane * V), lsl = ldv<V>(pf.llo + (int64_t)s0 * KB + lane * V);
-        Vec<V> leh = ldv<V>(pf.lhi + (int64_t)e0 * KB + lane * V), lel = ldv<V>(pf.llo + (int64_t)e0 * KB + lane * V);
-        Vec<V> bsh = ldv<V>(pf.bhi + bs * KB + lane * V), bsl = ldv<V>(pf.blo + bs * KB + lane * V);
-        Vec<V> beh = ldv<V>(pf.bhi + be * KB + lane * V), bel = ldv<V>(pf.blo + be * KB + lane * V);
+__device__ __forceinline__ void pull_interval_prefix(df (&acc)[V], uint32_t s0, uint32_t len, int lane,
+                                                     const PrefixArgs& pf) {
+    const uint32_t e0 = s0 + len;
+    const int64_t bs = s0 / pf.block, be = e0 / pf.block;
+    Vec<V> lsh = ldv<V>(pf.lhi + (int64_t)s0 * KB + lane * V), lsl = ldv<V>(pf.llo + (int64_t)s0 * KB + lane * V);
+    Vec<V> leh = ldv<V>(pf.lhi + (int64_t)e0 * KB + lane * V), lel = ldv<V>(pf.llo + (int64_t)e0 * KB + lane * V);
+    Vec<V> bsh = ldv<V>(pf.bhi + bs * KB + lane * V), bsl = ldv<V>(pf.blo + bs * KB + lane * V);
+    Vec<V> beh = ldv<V>(pf.bhi + be * KB + lane * V), bel = ldv<V>(pf.blo + be * KB + lane * V);
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            const df dB = df_add({beh.v[v], bel.v[v]}, df_neg({bsh.v[v], bsl.v[v]}));
-            const df dL = df_add({leh.v[v], lel.v[v]}, df_neg({lsh.v[v], lsl.v[v]}));
-            acc[v] = df_add(acc[v], df_add(dB, dL));
-        }
-    } else {
-        for (uint32_t t = 0; t < len; t++) {
-            Vec<V> xv = ldv<V>(x + (int64_t)(s0 + t) * ldx + lane * V);
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
-        }
+    for (int v = 0; v < V; v++) {
+        const df dB = df_add({beh.v[v], bel.v[v]}, df_neg({bsh.v[v], bsl.v[v]}));
+        const df dL = df_add({leh.v[v], lel.v[v]}, df_neg({lsh.v[v], lsl.v[v]}));
+        acc[v] = df_add(acc[v], df_add(dB, dL));
     }
 }
 
-template <int KB, int V>
-__global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ rowp,
-                                              const uint32_t* __restrict__ ent, const float* __restrict__ x,
-                                              int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n, int tile,
-                                              PrefixArgs pf) {
+template <int KB, int V, int W>
+__global__ void __launch_bounds__(256) k_pull_items(const uint32_t* __restrict__ pent,
+                                                    const uint32_t* __restrict__ istart, int64_t nitems,
+                                                    const float* __restrict__ x, int64_t ldx,
+                                                    float2* __restrict__ part) {
     constexpr int G = KB / V;
-    constexpr int S = 4;
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int64_t k = (int64_t)blockIdx.x * (256 / G) + threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    if (k >= nitems) return;
+    const uint32_t e0 = __ldg(istart + k), e1 = __ldg(istart + k + 1);
+    uint32_t w[W];
+#pragma unroll
+    for (int t = 0; t < W; t++) w[t] = e0 + t < e1 ? __ldg(pent + e0 + t) : 0u;
+    Vec<V> xv[W];
+#pragma unroll
+    for (int t = 0; t < W; t++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) xv[t].v[v] = 0.f;
+        if (e0 + t < e1) xv[t] = ldv<V>(x + (int64_t)(w[t] & 0x7fffffffu) * ldx + lane * V);
+    }
+    df acc[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = df_zero();
+#pragma unroll
+    for (int t = 0; t < W; t++)
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], (w[t] >> 31) ? -xv[t].v[v] : xv[t].v[v]);
+#pragma unroll
+    for (int v = 0; v < V; v++) part[k * KB + lane * V + v] = make_float2(acc[v].hi, acc[v].lo);
+}
+
+template <int KB, int V>
+__global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ irow,
+                                                   const float2* part, const uint32_t* __restrict__ lrow,
+                                                   const uint32_t* __restrict__ lint, const float* __restrict__ x,
+                                                   int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n,
+                                                   int tile, PrefixArgs pf) {
+    constexpr int G = KB / V;
     extern __shared__ float4 smem_pull[];
     df* c = reinterpret_cast<df*>(smem_pull);  // [(tile + kHalo) * KB]
     const int NG = blockDim.x / G;
@@ -217,44 +245,32 @@ __global__ void __launch_bounds__(256) k_pull(const uint8_t* __restrict__ meta, 
     const int64_t lo = a > kHalo ? a - kHalo : 0;
     const int64_t hi = a + tile < n ? a + tile : n;
     const int cnt = (int)(hi - lo);
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // the items' partial sums are ready
 
     for (int r = g; r < cnt; r += NG) {
         const int64_t i = lo + r;
         df acc[V];
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = df_zero();
-        const uint32_t w0 = __ldg(rowp + i), w1 = __ldg(rowp + i + 1);
-        uint32_t w[S];
+        const uint32_t k0 = __ldg(irow + i), k1 = __ldg(irow + i + 1);
+        for (uint32_t k = k0; k < k1; k++) {
 #pragma unroll
-        for (int t = 0; t < S; t++) w[t] = w0 + t < w1 ? __ldg(ent + w0 + t) : 0u;
-        Vec<V> xs[S];
-#pragma unroll
-        for (int t = 0; t < S; t++) {
-#pragma unroll
-            for (int v = 0; v < V; v++) xs[t].v[v] = 0.f;
-            if (w0 + t < w1 && tag_of(w[t]) < 2) xs[t] = ldv<V>(x + (int64_t)id_of(w[t]) * ldx + lane * V);
-        }
-#pragma unroll
-        for (int t = 0; t < S; t++) {
-            const uint32_t tag = tag_of(w[t]);
-#pragma unroll
-            for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], tag == kTagMinus ? -xs[t].v[v] : xs[t].v[v]);
-            if (w0 + t < w1 && tag == kTagIvS) {
-                const uint32_t len = id_of(t + 1 < S ? w[t + 1 < S ? t + 1 : t] : __ldg(ent + w0 + t + 1));
-                pull_interval<KB, V>(acc, id_of(w[t]), len, x, ldx, lane, pf);
+            for (int v = 0; v < V; v++) {
+                const float2 p = __ldcg(part + (int64_t)k * KB + lane * V + v);
+                acc[v] = df_add(acc[v], {p.x, p.y});
             }
         }
-        // words past the first S (a length word right after slot S-1 is skipped)
-        for (uint32_t q = w0 + S; q < w1; q++) {
-            const uint32_t word = __ldg(ent + q);
-            const uint32_t tag = tag_of(word), id = id_of(word);
-            if (tag == kTagPlus || tag == kTagMinus) {
-                Vec<V> xv = ldv<V>(x + (int64_t)id * ldx + lane * V);
+        const uint32_t l0 = __ldg(lrow + i), l1 = __ldg(lrow + i + 1);
+        for (uint32_t q = l0; q < l1; q++) {  // kept (long) intervals
+            const uint32_t s0 = __ldg(lint + 2 * q), len = __ldg(lint + 2 * q + 1);
+            if (pf.lhi) {
+                pull_interval_prefix<KB, V>(acc, s0, len, lane, pf);
+            } else {
+                for (uint32_t t = 0; t < len; t++) {
+                    Vec<V> xv = ldv<V>(x + (int64_t)(s0 + t) * ldx + lane * V);
 #pragma unroll
-                for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], tag == kTagPlus ? xv.v[v] : -xv.v[v]);
-            } else if (tag == kTagIvS) {
-                pull_interval<KB, V>(acc, id, id_of(__ldg(ent + q + 1)), x, ldx, lane, pf);
-                q++;
+                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
+                }
             }
         }
 #pragma unroll

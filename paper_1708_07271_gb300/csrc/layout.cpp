@@ -97,6 +97,52 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
     return BVG_OK;
 }
 
+// Pull work items: per row, the difference row with the intervals shorter
+// than min_len expanded into single entries (a dropped id carries bit 31),
+// cut into items of at most `item` consecutive entries; longer intervals are
+// kept as (start, length). Rows of A' differ widely in length (exact copies
+// have none, rows without a reference have all of theirs), so the pull
+// parallelises over items of equal size, not over rows.
+int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out) {
+    if (item < 1) return fail(BVG_ERR_INVALID_ARG, "pull items: item < 1");
+    try {
+        out = PullItems{};
+        out.irow.assign(n + 1, 0);
+        out.lrow.assign(n + 1, 0);
+        out.pent.reserve((size_t)rowp[n] * 2);
+        for (int64_t i = 0; i < n; i++) {
+            const uint32_t b = (uint32_t)out.pent.size();
+            out.irow[i] = (uint32_t)out.istart.size();
+            out.lrow[i] = (uint32_t)(out.lint.size() / 2);
+            for (uint32_t q = rowp[i]; q < rowp[i + 1]; q++) {
+                const uint32_t w = ent[q], tag = w >> kIdBits, id = w & kIdMask;
+                if (tag == kTagPlus) {
+                    out.pent.push_back(id);
+                } else if (tag == kTagMinus) {
+                    out.pent.push_back(id | 0x80000000u);
+                } else {
+                    const uint32_t len = ent[++q] & kIdMask;
+                    if ((int64_t)len >= min_len) {
+                        out.lint.push_back(id);
+                        out.lint.push_back(len);
+                    } else {
+                        for (uint32_t t = 0; t < len; t++) out.pent.push_back(id + t);
+                    }
+                }
+                if (out.pent.size() >= ((size_t)1 << 32) - 1)
+                    return fail(BVG_ERR_UNSUPPORTED, "pull items: more than 2^32 - 2 expanded entries");
+            }
+            for (uint32_t e = b; e < (uint32_t)out.pent.size(); e += (uint32_t)item) out.istart.push_back(e);
+        }
+        out.irow[n] = (uint32_t)out.istart.size();
+        out.lrow[n] = (uint32_t)(out.lint.size() / 2);
+        out.istart.push_back((uint32_t)out.pent.size());
+    } catch (const std::bad_alloc&) {
+        return fail(BVG_ERR_OOM, "pull items: host allocation failed");
+    }
+    return BVG_OK;
+}
+
 int get_layout(const bvg_host_graph* hg, const HostLayout** out) {
     std::lock_guard<std::mutex> lk(hg->layout_mu);
     if (!hg->layout) {
@@ -137,5 +183,37 @@ extern "C" int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out
     out->carry_ptr = L->carry_ptr.data();
     out->carry = L->carry.data();
     out->inv_outdeg = L->inv_outdeg.data();
+    return BVG_OK;
+}
+
+extern "C" int bvg_pull_items_size(const bvg_host_graph* g, int32_t item, int32_t min_len, int64_t* entries,
+                                   int64_t* items, int64_t* intervals) {
+    if (!g || !entries || !items || !intervals || item < 1 || min_len < 1)
+        return fail(BVG_ERR_INVALID_ARG, "bvg_pull_items_size: bad argument");
+    const HostLayout* L = nullptr;
+    int rc = get_layout(g, &L);
+    if (rc) return rc;
+    PullItems P;
+    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P))) return rc;
+    *entries = (int64_t)P.pent.size();
+    *items = (int64_t)P.istart.size() - 1;
+    *intervals = (int64_t)P.lint.size() / 2;
+    return BVG_OK;
+}
+
+extern "C" int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_t min_len, uint32_t* pent,
+                                   uint32_t* istart, uint32_t* irow, uint32_t* lrow, uint32_t* lint) {
+    if (!g || !pent || !istart || !irow || !lrow || !lint || item < 1 || min_len < 1)
+        return fail(BVG_ERR_INVALID_ARG, "bvg_pull_items_fill: bad argument");
+    const HostLayout* L = nullptr;
+    int rc = get_layout(g, &L);
+    if (rc) return rc;
+    PullItems P;
+    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P))) return rc;
+    std::copy(P.pent.begin(), P.pent.end(), pent);
+    std::copy(P.istart.begin(), P.istart.end(), istart);
+    std::copy(P.irow.begin(), P.irow.end(), irow);
+    std::copy(P.lrow.begin(), P.lrow.end(), lrow);
+    std::copy(P.lint.begin(), P.lint.end(), lint);
     return BVG_OK;
 }

@@ -280,13 +280,14 @@ def test_full_size_pagerank(web862k):
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-@pytest.mark.parametrize("prefix", [0, 1])
-def test_pull_with_and_without_prefix_of_x(name, prefix):
-    """Interval sums of the pull from the device prefix of x (blocked,
-    compensated) or summed directly: both match the oracle."""
+@pytest.mark.parametrize("prefix,min_len,item", [(0, 4, 8), (1, 4, 8), (-1, 32, 4), (-1, 32, 16), (-1, 1 << 20, 8)])
+def test_pull_item_and_prefix_settings(name, prefix, min_len, item):
+    """The pull's work items of 4, 8 or 16 entries, intervals kept whole from
+    length 4 (summed from the device prefix of x, or member by member), from
+    32, or never: every setting matches the oracle."""
     g, hg, dg, ref = graph(name)
     old = bvg.bvg_get_config(dg)
-    bvg.bvg_set_config(dg, pull_prefix=prefix, prefix_min_len=4)
+    bvg.bvg_set_config(dg, pull_prefix=prefix, prefix_min_len=min_len, pull_item=item)
     try:
         for k in (1, 8, 33):
             x = synth.rhs(g.n, k, synth.seed_for(1, 300 + k))
@@ -295,7 +296,8 @@ def test_pull_with_and_without_prefix_of_x(name, prefix):
             y = torch.full_like(xt, float("nan"))
             bvg.bvg_spmv_Ax(dg, xt, y)
             check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
-                        oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), f"Ax prefix={prefix} {name} k={k}")
+                        oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True),
+                        f"Ax prefix={prefix} min_len={min_len} item={item} {name} k={k}")
     finally:
         bvg.bvg_set_config(dg, **old)
 
@@ -320,3 +322,5 @@ def test_launch_config_variants_same_results():
         bvg.bvg_set_config(dg, **old)
     with pytest.raises(bvg.BvgError):
         bvg.bvg_set_config(dg, pull_tile=100)
+    with pytest.raises(bvg.BvgError):
+        bvg.bvg_set_config(dg, pull_item=5)

@@ -80,6 +80,38 @@ def emulate_Ax(L, x):
     return y
 
 
+def emulate_Ax_items(L, P, x, item, min_len):
+    """The pull as the kernels evaluate it: per work item the sum of its
+    signed expanded entries, per row the sum of its items and kept
+    intervals, then the chains."""
+    n = L["n"]
+    x = x.astype(np.float64)
+    pent = P["pent"].astype(np.int64)
+    sign = np.where(pent >> 31, -1.0, 1.0)[:, None]
+    vals = sign * x[pent & 0x7FFFFFFF]
+    istart = P["istart"].astype(np.int64)
+    sizes = np.diff(istart)
+    assert np.all(sizes >= 1) and np.all(sizes <= item)
+    part = np.add.reduceat(vals, istart[:-1], axis=0) if len(sizes) else np.zeros((0, x.shape[1]))
+    c = np.zeros_like(x)
+    irow = P["irow"].astype(np.int64)
+    for i in np.nonzero(np.diff(irow))[0]:
+        c[i] = part[irow[i]:irow[i + 1]].sum(axis=0)
+    lrow = P["lrow"].astype(np.int64)
+    assert np.all(P["lint"][:, 1] >= min_len) if len(P["lint"]) else True
+    for i in np.nonzero(np.diff(lrow))[0]:
+        for s0, ln in P["lint"][lrow[i]:lrow[i + 1]]:
+            c[i] += x[s0:s0 + ln].sum(axis=0)
+    # every item lies inside its row's entries, rows in order
+    rows_of_items = np.repeat(np.arange(n), np.diff(irow))
+    assert len(rows_of_items) == len(sizes)
+    y = np.zeros_like(c)
+    off = (L["meta"] & 7).astype(np.int64)
+    for i in range(n):
+        y[i] = c[i] + (y[i - off[i]] if off[i] else 0.0)
+    return y
+
+
 GRAPHS = {
     "tiny_web": lambda: synth.copying_model(synth.tiny_web()),
     "ragged": lambda: synth.copying_model(synth.replace(synth.tiny_web(), n=1037, seed=77)),
@@ -115,3 +147,21 @@ def test_layout_reproduces_products(name):
             desc[r] |= 1 << (i - r - 1)
             r = ref[r]
     np.testing.assert_array_equal(L["desc"], desc)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("item,min_len", [(8, 32), (4, 4), (16, 1 << 20), (8, 100)])
+def test_pull_items_reproduce_products(name, item, min_len):
+    g = GRAPHS[name]()
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    L = bvg.bvg_layout_view_get(hg)
+    P = bvg.bvg_pull_items(hg, item, min_len)
+    x = synth.rhs(g.n, 2, 4).astype(np.float64)
+    np.testing.assert_allclose(emulate_Ax_items(L, P, x, item, min_len), oracle.csr_Ax(g.row_ptr, g.col, x),
+                               rtol=1e-9, atol=1e-9)
+    # expanded entries count: every single id plus the members of short intervals
+    ent = L["ent"].astype(np.int64)
+    tag = ent >> TAG_SHIFT
+    lens = (ent[np.nonzero(tag == 2)[0] + 1] & MASK)
+    assert len(P["pent"]) == int(np.sum(tag < 2) + lens[lens < min_len].sum())
+    assert len(P["lint"]) == int(np.sum(lens >= min_len))
