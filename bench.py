@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-graph batch leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--no-krhs", action="store_true", help="skip the k = 32 leg")
+    ap.add_argument("--config3", action="store_true",
+                    help="run the k = 32 leg on the web-like graph n = 7.4 M, 194 M edges")
     return ap.parse_args()
 
 
@@ -227,6 +230,41 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- extra legs
+def krhs_leg(args, bvg, synth, torch, flush, timed, dg, g, k=32):
+    """k = 32 right-hand sides in one product (row-major n x 32, one walk of
+    the structure): x A and A x^T, Gedges/s counted as m * k per step; and
+    personalized PageRank for 32 one-hot teleport vectors at once (seed nodes
+    drawn uniformly), to L1 < 1e-8 in every column."""
+    if args.config3:
+        g = synth.copying_model(synth.web_7m4())
+        dg = bvg.bvg_upload(bvg.bvg_encode(g.row_ptr, g.col))
+    x = torch.from_numpy(synth.rhs(g.n, k, synth.seed_for(3, 1))).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        bvg.bvg_spmv_xA(dg, x, y)
+        bvg.bvg_spmv_Ax(dg, x, y)
+    push = timed(lambda: bvg.bvg_spmv_xA(dg, x, y), args.steps)
+    pull = timed(lambda: bvg.bvg_spmv_Ax(dg, x, y), args.steps)
+    seeds = synth.nodes(k, g.n, synth.seed_for(3, 2))
+    p0 = torch.zeros((g.n, k), dtype=torch.float32, device="cuda")
+    p0[torch.from_numpy(seeds.astype(np.int64)).cuda(), torch.arange(k, device="cuda")] = 1.0
+    out = torch.empty_like(p0)
+    bvg.bvg_pagerank(dg, p0=p0, tol=1e-8, max_iter=1000, out=out)
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, res, rc = bvg.bvg_pagerank(dg, p0=p0, tol=1e-8, max_iter=1000, out=out)
+        runs.append((time.perf_counter() - t0, it, float(np.max(res)), rc))
+    runs.sort()
+    s_, it, res, rc = runs[len(runs) // 2]
+    gd = lambda ms: g.m * k * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
+    return {"k": k, "graph": workload_name(g), "xA_gedges_s": gd(push), "xA_ms_per_step": float(np.mean(push)),
+            "Ax_gedges_s": gd(pull), "Ax_ms_per_step": float(np.mean(pull)),
+            "ppr": {"vectors": k, "seconds": s_, "iterations": it, "max_l1_resid": res, "status": rc,
+                    "teleport": "one-hot seed nodes"}}
+
+
 def batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard):
     """64 copying-model graphs, n log-uniform in [1e3, 1e6], k = 1: one
     batched product (two launches from one CUDA graph) against the same
@@ -432,6 +470,7 @@ def run_bv(args):
     pr_runs.sort()
     pr_s, pr_it, pr_res, pr_rc = pr_runs[len(pr_runs) // 2]
 
+    krhs = None if args.no_krhs else krhs_leg(args, bvg, synth, torch, flush, timed, dg, g)
     batch = None if args.no_batch else batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard)
     warm = None if args.no_warmstart else warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it)
 
@@ -455,7 +494,7 @@ def run_bv(args):
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
-            "batch": batch, "warm_start": warm,
+            "k_rhs": krhs, "batch": batch, "warm_start": warm,
             "compression": {"m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
                             "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"],
                             "structure_MB": L["structure_bytes"] / 1e6},

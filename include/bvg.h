@@ -305,7 +305,9 @@ void bvg_free_mlp(bvg_mlp* net);
  * results of every setting are the same up to the product tolerance). */
 typedef struct {
     int32_t pull_tile;      /* rows per CTA of the pull's row pass: power of two in [64, 2048] (default 512) */
-    int32_t pull_prefix;    /* pull interval sums from a prefix of x: -1 auto (mean interval >= 32), 0 off, 1 on */
+    int32_t pull_prefix;    /* pull: intervals of at least prefix_min_len ids: -1 kept whole (and summed from
+                               the prefix of x) only when their members outnumber 2n, else expanded (default);
+                               0 kept whole and summed member by member; 1 kept whole, summed from the prefix */
     int32_t prefix_min_len; /* pull: intervals at least this long stay (start, length) and are summed from the
                                prefix of x; shorter ones are expanded into work items (default 32) */
     int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */

@@ -89,7 +89,7 @@ constexpr int kThreads = 256;
 static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
 // Columns per CTA of the gather kernel (k_gather's GatherShape).
 static int gather_tile(int kb, int v, const LaunchCfg&) {
-    const int G = kb / v, NG = 256 / G, CPT = std::max(2, G / 2);
+    const int G = kb / v, NT = G >= 8 ? 512 : 256, NG = NT / G, CPT = std::max(2, 128 / NG);
     return NG * CPT;
 }
 
@@ -303,9 +303,9 @@ static int ensure_part(bvg_dev_graph* g, int kb) {
 // Builds the pull work items (see build_pull_items) from the host copy of the
 // difference rows and copies them to the device, replacing earlier arrays;
 // synchronous.
-static int build_pull_items(bvg_dev_graph* g, int item, int min_len, cudaStream_t st) {
+static int build_pull_items(bvg_dev_graph* g, int item, int min_len, int prefix_mode, cudaStream_t st) {
     PullItems P;
-    int rc0 = build_pull_items(g->host_rowp.data(), g->host_ent.data(), g->n, item, min_len, P);
+    int rc0 = build_pull_items(g->host_rowp.data(), g->host_ent.data(), g->n, item, min_len, P, prefix_mode < 0);
     if (rc0) return rc0;
     std::vector<uint32_t>& pent = P.pent;
     std::vector<uint32_t>& istart = P.istart;
@@ -333,6 +333,7 @@ static int build_pull_items(bvg_dev_graph* g, int item, int min_len, cudaStream_
     g->pull_bytes = bytes;
     g->pull_built_item = item;
     g->pull_built_minlen = min_len;
+    g->pull_built_auto = prefix_mode < 0 ? 1 : 0;
     return BVG_OK;
 }
 
@@ -446,7 +447,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         }
         g->host_rowp = L->rowp;
         g->host_ent = L->ent;
-        if ((rc = build_pull_items(g, g->cfg.pull_item, g->cfg.prefix_min_len, st))) {
+        if ((rc = build_pull_items(g, g->cfg.pull_item, g->cfg.prefix_min_len, g->cfg.pull_prefix, st))) {
             bvg_free_dev(g);
             return rc;
         }
@@ -561,8 +562,9 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
                                          "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
                                          "of two in [1, 32], pull_item in {4, 8, 16}");
-    if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen) {
-        int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, nullptr);
+    if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen ||
+        (in->pull_prefix < 0 ? 1 : 0) != g->pull_built_auto) {
+        int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, in->pull_prefix, nullptr);
         if (rc) return rc;
     }
     if (in->gather_pdl != g->cfg.gather_pdl) drop_pr_graph(g);  // the PageRank graph was captured with the old launch

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_chain_batch(const BatchEntry* __restric
 }
 
 template <int KB, int V>
-__global__ void __launch_bounds__(256) k_gather_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
+__global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
                                                       int64_t c0) {
     const BatchEntry e = tab[find_graph<false>(tab, count, blockIdx.x)];
     PrArgs pa{};

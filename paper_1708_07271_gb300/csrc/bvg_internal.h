@@ -53,7 +53,8 @@ struct HostLayout {
 struct PullItems {
     std::vector<uint32_t> pent, istart, irow, lrow, lint;
 };
-int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out);
+int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out,
+                     bool only_if_worth);
 
 }  // namespace bvg
 
@@ -84,7 +85,8 @@ namespace bvg {
 // Launch configuration of the product kernels (autotuned per graph and k).
 struct LaunchCfg {
     int pull_tile = 512;        // rows per CTA of the pull's row pass
-    int pull_prefix = -1;       // kept intervals summed from the prefix of x: -1 auto (on), 0 off, 1 on
+    int pull_prefix = -1;       // kept intervals: -1 keep only when worth a prefix (then use it), 0 keep and sum
+                                // member by member, 1 keep and use the prefix of x
     int prefix_min_len = 32;    // pull: intervals at least this long stay (start, length); shorter ones are expanded
     int pull_item = 8;          // pull: entries per work item (4, 8 or 16)
     int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
@@ -163,7 +165,7 @@ struct bvg_dev_graph {
     int64_t npent = 0, nitems = 0, nlint = 0;
     float* part = nullptr;          // per item partial sums, compensated (hi, lo) x part_kcap
     int64_t part_kcap = 0;
-    int pull_built_item = 0, pull_built_minlen = 0;  // parameters the item arrays were built with
+    int pull_built_item = 0, pull_built_minlen = 0, pull_built_auto = -1;  // parameters the items were built with
     int64_t pull_bytes = 0;                          // device bytes of the item arrays
     std::vector<uint32_t> host_rowp, host_ent;       // the difference rows, to rebuild the items
     int64_t bytes = 0;

@@ -414,10 +414,10 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // ---------------------------------------------------------------------------
 template <int KB, int V>
 struct GatherShape {
-    static constexpr int NT = 256;                       // threads per CTA
     static constexpr int G = KB / V;                     // lanes per column group
+    static constexpr int NT = G >= 8 ? 512 : 256;        // threads per CTA (wide blocks: more, smaller groups)
     static constexpr int NG = NT / G;                    // column groups per CTA
-    static constexpr int CPT = G / 2 > 2 ? G / 2 : 2;    // consecutive columns per group
+    static constexpr int CPT = 128 / NG > 2 ? 128 / NG : 2;  // consecutive columns per group
     static constexpr int T = NG * CPT;                   // columns per CTA (a multiple of kCarryTile)
     static constexpr int S = 3;                          // entry slots per column in straight-line code
 };
@@ -512,8 +512,10 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
+    static_assert(NW * KB <= NT, "one thread per (warp, right-hand side) forms the warp prefixes");
     __shared__ df run_s[KB];
     __shared__ df wtot_s[NW][KB];
+    __shared__ df wpre_s[NW][KB];
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t a = blk * T;
@@ -538,8 +540,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
     }
 
-    // running interval sum at column a: the carry sources' z (warp 0)
-    if (warp == 0) {
+    // running interval sum at column a: the carry sources' z, one thread per
+    // right-hand side for a wide column block, the lanes of warp 0 otherwise
+    if constexpr (KB >= 8) {
+        if (threadIdx.x < KB) {
+            df acc = df_zero();
+            for (uint32_t e = cr0; e < cr1; e++) {
+                const uint32_t src = __ldg(carry + e);
+                acc = df_addf(acc, __ldca(z + (int64_t)src * ldz + threadIdx.x));
+            }
+            run_s[threadIdx.x] = acc;
+        }
+    } else if (warp == 0) {
         df acc[KB];
 #pragma unroll
         for (int c = 0; c < KB; c++) acc[c] = df_zero();
@@ -626,15 +638,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         excl[v] = lane32 >= G ? o : df_zero();
     }
     __syncthreads();
+    // each warp's starting prefix, once per (warp, right-hand side): the carry,
+    // then the totals of the warps before it, in order
+    if (threadIdx.x < NW * KB) {
+        const int w = threadIdx.x / KB, c = threadIdx.x % KB;
+        df r = run_s[c];
+        for (int w2 = 0; w2 < w; w2++) r = df_add(r, wtot_s[w2][c]);
+        wpre_s[w][c] = r;
+    }
+    __syncthreads();
     df run[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-        df r = run_s[lane * V + v];
-#pragma unroll
-        for (int w2 = 0; w2 < NW; w2++)
-            if (w2 < warp) r = df_add(r, wtot_s[w2][lane * V + v]);
-        run[v] = df_add(r, excl[v]);
-    }
+    for (int v = 0; v < V; v++) run[v] = df_add(wpre_s[warp][lane * V + v], excl[v]);
 
     df Ssum[V], R[V], Dg[V];
 #pragma unroll
@@ -674,7 +689,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 }
 
 template <int KB, int V, int EPI>
-__global__ void __launch_bounds__(256) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+__global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                                 const uint32_t* __restrict__ carry_ptr,
                                                 const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                                 float* __restrict__ y, int64_t ldy, int64_t n,

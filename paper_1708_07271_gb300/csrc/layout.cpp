@@ -14,6 +14,7 @@
 // lies before the tile and whose end event (if any) lies at or after a;
 // summing their z gives the running sum at a without a grid-wide scan.
 #include <algorithm>
+#include <climits>
 #include <new>
 
 #include "bvg_internal.h"
@@ -103,8 +104,21 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
 // kept as (start, length). Rows of A' differ widely in length (exact copies
 // have none, rows without a reference have all of theirs), so the pull
 // parallelises over items of equal size, not over rows.
-int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out) {
+int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out,
+                     bool only_if_worth) {
     if (item < 1) return fail(BVG_ERR_INVALID_ARG, "pull items: item < 1");
+    if (only_if_worth) {
+        // the prefix of x costs O(n) per product: keep intervals whole only
+        // when their members outnumber 2n, else expand every one
+        int64_t members = 0;
+        for (int64_t q = 0; q < (int64_t)rowp[n]; q++)
+            if ((ent[q] >> kIdBits) == kTagIvS) {
+                const int64_t len = ent[q + 1] & kIdMask;
+                if (len >= min_len) members += len;
+                q++;
+            }
+        if (members <= 2 * n) min_len = INT32_MAX;
+    }
     try {
         out = PullItems{};
         out.irow.assign(n + 1, 0);
@@ -194,7 +208,7 @@ extern "C" int bvg_pull_items_size(const bvg_host_graph* g, int32_t item, int32_
     int rc = get_layout(g, &L);
     if (rc) return rc;
     PullItems P;
-    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P))) return rc;
+    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P, false))) return rc;
     *entries = (int64_t)P.pent.size();
     *items = (int64_t)P.istart.size() - 1;
     *intervals = (int64_t)P.lint.size() / 2;
@@ -209,7 +223,7 @@ extern "C" int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_
     int rc = get_layout(g, &L);
     if (rc) return rc;
     PullItems P;
-    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P))) return rc;
+    if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), g->n, item, min_len, P, false))) return rc;
     std::copy(P.pent.begin(), P.pent.end(), pent);
     std::copy(P.istart.begin(), P.istart.end(), istart);
     std::copy(P.irow.begin(), P.irow.end(), irow);
