@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-krhs", action="store_true", help="skip the k = 32 leg")
     ap.add_argument("--config3", action="store_true",
                     help="run the k = 32 leg on the web-like graph n = 7.4 M, 194 M edges")
+    ap.add_argument("--no-variants", action="store_true", help="skip the A^T-pull and social-graph legs")
+    ap.add_argument("--config5", action="store_true",
+                    help="run the BV-vs-CSR crossover on the social graph n = 5.4 M and the web graph n = 22.7 M "
+                         "(k = 8)")
     return ap.parse_args()
 
 
@@ -230,6 +234,68 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- extra legs
+def transpose_csr(row_ptr, col, n):
+    """CSR of A^T (rows sorted, no duplicates) from the CSR of A."""
+    rp = np.asarray(row_ptr, np.int64)
+    ci = np.asarray(col, np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    order = np.lexsort((src, ci))
+    tp = np.zeros(n + 1, np.int64)
+    tp[1:] = np.cumsum(np.bincount(ci, minlength=n))
+    return tp, src[order].astype(np.int32)
+
+
+def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
+    """Two comparisons on the bench graph and a social-shaped one:
+    x A as the pull on an encoding of A^T (the paper's own choice for its
+    PageRank) against the push on A's encoding; and BV against CSR on a graph
+    with power-law out-degree and random ids (weak locality, little
+    compression), where the paper expects the compressed product to lose."""
+    x = torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
+    y = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    tp, tc = transpose_csr(g.row_ptr, g.col, g.n)
+    hgT = bvg.bvg_encode(tp, tc)
+    stT = bvg.bvg_stats(hgT)
+    dgT = bvg.bvg_upload(hgT)
+
+    def warm_timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        return timed(fn, args.steps)
+
+    push = warm_timed(lambda: bvg.bvg_spmv_xA(dg, x, y))
+    pullT = warm_timed(lambda: bvg.bvg_spmv_Ax(dgT, x, y2))
+    torch.cuda.synchronize()
+    rel = float(((y - y2).abs().max() / y.abs().max()).item())
+    gd = lambda m, ms: m * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
+    out = {"xA_push_on_A_gedges_s": gd(g.m, push), "xA_pull_on_AT_gedges_s": gd(g.m, pullT),
+           "AT_m_over_words": stT["m"] / max(1, stT["words"]), "max_rel_diff_push_vs_pull": rel}
+
+    def crossover(spec, k):
+        gs = synth.copying_model(spec)
+        hs = bvg.bvg_encode(gs.row_ptr, gs.col)
+        st = bvg.bvg_stats(hs)
+        ds = bvg.bvg_upload(hs)
+        cs = bvg.bvg_csr_upload(gs.row_ptr, gs.col)
+        xs = torch.from_numpy(synth.rhs(gs.n, k, synth.seed_for(5, 1))).cuda()
+        if k == 1:
+            xs = xs.reshape(-1)
+        ys = torch.empty_like(xs)
+        r = {"n": gs.n, "m": gs.m, "k": k, "m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
+             "m_over_words": st["m"] / max(1, st["words"])}
+        for name, fn in (("bv_xA", lambda: bvg.bvg_spmv_xA(ds, xs, ys)), ("csr_xA", lambda: bvg.bvg_csr_spmv_xA(cs, xs, ys)),
+                         ("bv_Ax", lambda: bvg.bvg_spmv_Ax(ds, xs, ys)), ("csr_Ax", lambda: bvg.bvg_csr_spmv_Ax(cs, xs, ys))):
+            r[name + "_gedges_s"] = gd(gs.m * k, warm_timed(fn))
+        return r
+
+    out["social"] = crossover(synth.replace(synth.social_5m4(), n=g.n), 1)
+    if args.config5:
+        out["social_5m4"] = crossover(synth.social_5m4(), 1)
+        out["web_22m7_k8"] = crossover(synth.web_22m7(), 8)
+    return out
+
+
 def krhs_leg(args, bvg, synth, torch, flush, timed, dg, g, k=32):
     """k = 32 right-hand sides in one product (row-major n x 32, one walk of
     the structure): x A and A x^T, Gedges/s counted as m * k per step; and
@@ -470,6 +536,7 @@ def run_bv(args):
     pr_runs.sort()
     pr_s, pr_it, pr_res, pr_rc = pr_runs[len(pr_runs) // 2]
 
+    variants = None if args.no_variants else variants_leg(args, bvg, synth, torch, timed, dg, g, cg)
     krhs = None if args.no_krhs else krhs_leg(args, bvg, synth, torch, flush, timed, dg, g)
     batch = None if args.no_batch else batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard)
     warm = None if args.no_warmstart else warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it)
@@ -494,7 +561,7 @@ def run_bv(args):
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
-            "k_rhs": krhs, "batch": batch, "warm_start": warm,
+            "k_rhs": krhs, "batch": batch, "warm_start": warm, "variants": variants,
             "compression": {"m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
                             "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"],
                             "structure_MB": L["structure_bytes"] / 1e6},
