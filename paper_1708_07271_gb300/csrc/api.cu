@@ -380,6 +380,8 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
         int64_t cap = max_grid(g) * 3 * 32;
         rc = dev_alloc((void**)&g->s.partial, (size_t)cap * sizeof(double), nullptr);
         if (rc) return rc;
+        rc = dev_alloc((void**)&g->s.gpartial, (size_t)(max_grid(g) / kPrGroup + 1) * 3 * 32 * sizeof(double), nullptr);
+        if (rc) return rc;
         g->s.partial_cap = cap;
         BVG_CUDA_TRY(cudaMallocHost((void**)&g->s.host_state, sizeof(PrState) + 64 * sizeof(double)));
     }
@@ -451,11 +453,12 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
-        if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, sizeof(unsigned int), nullptr))) {
+        const size_t ncount = (size_t)(1 + max_grid(g) / kPrGroup + 1);  // global + one per group of CTAs
+        if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, ncount * sizeof(unsigned int), nullptr))) {
             bvg_free_dev(g);
             return rc;
         }
-        BVG_CUDA_TRY(cudaMemsetAsync(g->s.counter, 0, sizeof(unsigned int), st));
+        BVG_CUDA_TRY(cudaMemsetAsync(g->s.counter, 0, ncount * sizeof(unsigned int), st));
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
             bvg_free_dev(g);
@@ -474,7 +477,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
-                    g->s.feat_tmp, g->s.wfeat, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part};
+                    g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -706,6 +709,8 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     base.st = pst;
     base.partial = g->s.partial;
     base.counter = g->s.counter;
+    base.gcounter = g->s.counter + 1;
+    base.gpartial = g->s.gpartial;
     base.alpha = (float)(1.0 - damping);
     base.dangling_uniform = dangling;
     base.k = k;

@@ -105,7 +105,8 @@ struct DevScratch {
     double* sc[2] = {nullptr, nullptr}; // PageRank scalars per parity: [3][32] (1/S, dangling, resid)
     void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
     double* partial = nullptr;          // per-CTA FP64 partial sums
-    unsigned int* counter = nullptr;    // CTAs finished (last-CTA reduction)
+    double* gpartial = nullptr;         // per group of CTAs (two-level reduction)
+    unsigned int* counter = nullptr;    // [0]: groups finished; [1 + g]: CTAs of group g finished
     float* pre[4] = {nullptr, nullptr, nullptr, nullptr};  // prefix of x: L hi/lo ((n+1) x kcap), B hi/lo
     int64_t pre_kcap = 0;
     void* host_state = nullptr;         // pinned host copy of the state + residuals

@@ -29,7 +29,9 @@ struct PrArgs {
     double* sc_new;
     PrState* st;
     double* partial;           // [grid][3][KB]
-    unsigned int* counter;
+    unsigned int* counter;     // CTAs groups finished (last-group reduction)
+    double* gpartial;          // [groups][3][KB]
+    unsigned int* gcounter;    // per group of kPrGroup CTAs: CTAs finished
     float alpha;
     int dangling_uniform;
     int k;                     // right-hand sides of the solve (== KB)
@@ -429,10 +431,23 @@ struct PrPartials {
 
 // Sums the per-CTA partials (sum q, sum |q - p_prev|, dangling mass): each
 // thread's compensated FP32 sums are combined across the CTA in compensated
-// FP32 (error-free two_sum steps, fixed order), stored as one FP64 value per
-// CTA, and the last CTA to finish adds all CTAs' values in FP64 in a fixed
-// order (one warp per quantity) and writes the scalars of this update
-// (deterministic; no spin-waits).
+// FP32 (error-free two_sum steps, fixed order) and stored as one FP64 value
+// per CTA. Then two levels, each deterministic and free of spin-waits: the
+// last CTA to finish in each group of kPrGroup CTAs adds the group's values in
+// FP64 in a fixed order (one warp per quantity, lanes over the CTAs, a fixed
+// shuffle tree), and the last group to finish adds the groups' values the same
+// way and writes the scalars of this update. A single reducing CTA for the
+// whole grid would read grid x 3k values alone (5 MB for k = 32 at n = 862k).
+constexpr int kPrGroup = 64;
+
+template <int KB>
+__device__ __forceinline__ double pr_warp_sum(const double* __restrict__ base, int count, int item, int lane32) {
+    double t = 0.0;
+    for (int b = lane32; b < count; b += 32) t += __ldcg(base + ((int64_t)b * 3 + item / KB) * KB + item % KB);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
 template <int KB, int V>
 __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArgs& pa, bool init) {
     constexpr int G = KB / V;
@@ -464,16 +479,32 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
         __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) sh_last = atomicAdd(pa.counter, 1u) == gridDim.x - 1;
+    // level 1: the last CTA of this group adds the group's CTAs
+    const int grp = blockIdx.x / kPrGroup;
+    const int gsize = min(kPrGroup, (int)gridDim.x - grp * kPrGroup);
+    if (threadIdx.x == 0) sh_last = atomicAdd(pa.gcounter + grp, 1u) == (unsigned)gsize - 1u;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    const double* gbase = pa.partial + (int64_t)grp * kPrGroup * 3 * KB;
+    for (int item = warp; item < 3 * KB; item += NW) {
+        const double t = pr_warp_sum<KB>(gbase, gsize, item, lane32);
+        if (lane32 == 0) pa.gpartial[((int64_t)grp * 3 + item / KB) * KB + item % KB] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    // level 2: the last group adds the groups and writes the scalars
+    const int ngroups = ((int)gridDim.x + kPrGroup - 1) / kPrGroup;
+    if (threadIdx.x == 0) {
+        pa.gcounter[grp] = 0u;  // every CTA of the group has counted
+        sh_last = atomicAdd(pa.counter, 1u) == (unsigned)ngroups - 1u;
+    }
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
     __shared__ double sh_tot[3][KB];
     for (int item = warp; item < 3 * KB; item += NW) {
-        double t = 0.0;
-        for (int b = lane32; b < (int)gridDim.x; b += 32)
-            t += __ldcg(pa.partial + ((int64_t)b * 3 + item / KB) * KB + item % KB);
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        const double t = pr_warp_sum<KB>(pa.gpartial, ngroups, item, lane32);
         if (lane32 == 0) sh_tot[item / KB][item % KB] = t;
     }
     __syncthreads();
