@@ -669,18 +669,31 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         excl[v] = lane32 >= G ? o : df_zero();
     }
     __syncthreads();
-    // each warp's starting prefix, once per (warp, right-hand side): the carry,
-    // then the totals of the warps before it, in order
-    if (threadIdx.x < NW * KB) {
-        const int w = threadIdx.x / KB, c = threadIdx.x % KB;
-        df r = run_s[c];
-        for (int w2 = 0; w2 < w; w2++) r = df_add(r, wtot_s[w2][c]);
-        wpre_s[w][c] = r;
-    }
-    __syncthreads();
+    // this warp's starting prefix: the carry, then the totals of the warps
+    // before it, in order; for a wide column block formed once per (warp,
+    // right-hand side) in shared memory, otherwise by every thread (cheaper
+    // than a second barrier when each thread owns few right-hand sides)
     df run[V];
+    if constexpr (KB >= 8) {
+        if (threadIdx.x < NW * KB) {
+            const int w = threadIdx.x / KB, c = threadIdx.x % KB;
+            df r = run_s[c];
+            for (int w2 = 0; w2 < w; w2++) r = df_add(r, wtot_s[w2][c]);
+            wpre_s[w][c] = r;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int v = 0; v < V; v++) run[v] = df_add(wpre_s[warp][lane * V + v], excl[v]);
+        for (int v = 0; v < V; v++) run[v] = df_add(wpre_s[warp][lane * V + v], excl[v]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            df r = run_s[lane * V + v];
+#pragma unroll
+            for (int w2 = 0; w2 < NW; w2++)
+                if (w2 < warp) r = df_add(r, wtot_s[w2][lane * V + v]);
+            run[v] = df_add(r, excl[v]);
+        }
+    }
 
     df Ssum[V], R[V], Dg[V];
 #pragma unroll
