@@ -10,9 +10,13 @@
 namespace bvg {
 
 // A value carried as an unevaluated sum hi + lo of two floats. Additions use
-// the error-free transformation two_sum (Knuth), so a chain of additions
-// loses about one FP32 rounding in total instead of one per addition
-// (compensated summation).
+// the error-free transformation two_sum (Knuth) on the leading parts and add
+// the exact error terms into lo in plain FP32, without renormalising after
+// every step: the cascaded summation of Ogita, Rump and Oishi ("Sum2",
+// Accurate sum and dot product, 2005), whose result hi + lo is as accurate as
+// if computed in twice the working precision and then rounded (error at most
+// eps |s| + gamma_{n-1}^2 sum |x_i| for n terms). A chain of additions thus
+// loses about one FP32 rounding in total instead of one per addition.
 struct df {
     float hi, lo;
 };
@@ -25,25 +29,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ df df_renorm(float s, float e) {
-    float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-}
-
-// a + b for two compensated values.
+// a + b for two compensated values (cascaded: the error terms accumulate in lo).
 __device__ __forceinline__ df df_add(df a, df b) {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
+    return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
+// a + b with the result renormalised (|lo| <= ulp(hi) / 2): for long running
+// sums with cancellation (prefixes of +/- events), where the unnormalised
+// form's second-order error term (n eps)^2 sum |x| is not negligible.
+__device__ __forceinline__ df df_add_rn(df a, df b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
     e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    return df_renorm(s, e);
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 
 // a + b for a compensated value and a float.
 __device__ __forceinline__ df df_addf(df a, float b) {
     float s, e;
     two_sum(a.hi, b, s, e);
-    e = __fadd_rn(e, a.lo);
-    return df_renorm(s, e);
+    return {s, __fadd_rn(a.lo, e)};
 }
 
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }

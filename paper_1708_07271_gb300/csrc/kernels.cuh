@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_prefix_local(const float* __restrict__ 
 #pragma unroll
         for (int v = 0; v < V; v++) {
             df o = df_shfl_up(inc[v], d);
-            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
+            if (lane32 >= d) inc[v] = df_add_rn(o, inc[v]);
         }
 #pragma unroll
     for (int v = 0; v < V; v++) {
@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(256) k_prefix_local(const float* __restrict__ 
 #pragma unroll
     for (int v = 0; v < V; v++) {
         df r = df_zero();
-        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w][lane * V + v]);
-        run[v] = df_add(r, ex[v]);
+        for (int w = 0; w < warp; w++) r = df_add_rn(r, wtot_s[w][lane * V + v]);
+        run[v] = df_add_rn(r, ex[v]);
     }
 #pragma unroll
     for (int i = 0; i < RPT; i++) {
@@ -134,25 +134,25 @@ __global__ void __launch_bounds__(256) k_prefix_blocks(float* __restrict__ bhi, 
     const int per = (nb + 255) / 256, b0 = threadIdx.x * per;
     for (int c = 0; c < KB; c++) {
         df t = df_zero();
-        for (int b = b0; b < b0 + per && b < nb; b++) t = df_add(t, {bhi[(int64_t)b * KB + c], blo[(int64_t)b * KB + c]});
+        for (int b = b0; b < b0 + per && b < nb; b++) t = df_add_rn(t, {bhi[(int64_t)b * KB + c], blo[(int64_t)b * KB + c]});
         df inc = t;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             df o = df_shfl_up(inc, d);
-            if (lane >= d) inc = df_add(o, inc);
+            if (lane >= d) inc = df_add_rn(o, inc);
         }
         df o = df_shfl_up(inc, 1);
         const df ex = lane >= 1 ? o : df_zero();
         if (lane == 31) wtot_s[warp] = inc;
         __syncthreads();
         df r = df_zero();
-        for (int w = 0; w < warp; w++) r = df_add(r, wtot_s[w]);
-        r = df_add(r, ex);
+        for (int w = 0; w < warp; w++) r = df_add_rn(r, wtot_s[w]);
+        r = df_add_rn(r, ex);
         for (int b = b0; b < b0 + per && b < nb; b++) {
             const df cur = {bhi[(int64_t)b * KB + c], blo[(int64_t)b * KB + c]};
             bhi[(int64_t)b * KB + c] = r.hi;
             blo[(int64_t)b * KB + c] = r.lo;
-            r = df_add(r, cur);
+            r = df_add_rn(r, cur);
         }
         __syncthreads();
     }
@@ -194,9 +194,9 @@ __device__ __forceinline__ void pull_interval_prefix(df (&acc)[V], uint32_t s0, 
     Vec<V> beh = ldv<V>(pf.bhi + be * KB + lane * V), bel = ldv<V>(pf.blo + be * KB + lane * V);
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        const df dB = df_add({beh.v[v], bel.v[v]}, df_neg({bsh.v[v], bsl.v[v]}));
-        const df dL = df_add({leh.v[v], lel.v[v]}, df_neg({lsh.v[v], lsl.v[v]}));
-        acc[v] = df_add(acc[v], df_add(dB, dL));
+        const df dB = df_add_rn({beh.v[v], bel.v[v]}, df_neg({bsh.v[v], bsl.v[v]}));
+        const df dL = df_add_rn({leh.v[v], lel.v[v]}, df_neg({lsh.v[v], lsl.v[v]}));
+        acc[v] = df_add_rn(acc[v], df_add_rn(dB, dL));
     }
 }
 
@@ -400,9 +400,10 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // scan is needed. A group of G = KB/V lanes owns CPT consecutive columns.
 // Each column's first S entries are loaded and summed by the same
 // straight-line predicated code in every lane (no divergence on the typical
-// column; longer columns finish in a short loop). One pass: point terms P_j
-// (a few per column) sum in FP32 in storage order, since an error there stays
-// in y_j. Interval events and their prefix are carried as compensated
+// column; longer columns finish in a short loop). One pass: the point terms
+// of a column's first S entries sum in FP32 in storage order (an error there
+// stays in y_j, and S is small); points past them (long columns: the hubs of a
+// power-law graph) sum compensated. Interval events and their prefix are carried as compensated
 // double-float values (two_sum steps, about 48 significant bits), because the
 // prefix carries any error to every later column of the tile. The block scan
 // runs in the same arithmetic, in a fixed order. y_j = P_j + I_j is rounded
@@ -598,13 +599,15 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         }
 #pragma unroll
         for (int c = 0; c < KB; c++) {
-            for (int o = 16; o > 0; o >>= 1) acc[c] = df_add(acc[c], df_shfl_xor(acc[c], o));
+            for (int o = 16; o > 0; o >>= 1) acc[c] = df_add_rn(acc[c], df_shfl_xor(acc[c], o));
             if (lane32 == 0) run_s[c] = acc[c];
         }
     }
 
-    // one pass over each column's entries: points in FP32, events compensated
-    float P[CPT][V];
+    // one pass over each column's entries: the first S points in FP32, points
+    // past them (long columns: hubs of a power-law graph reach hundreds) and
+    // all events compensated
+    float P[CPT][V], Pe[CPT][V];  // Pe: the error terms of the compensated point sum of long columns
     df D[CPT][V], tot[V];
 #pragma unroll
     for (int v = 0; v < V; v++) tot[v] = df_zero();
@@ -613,6 +616,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
         for (int v = 0; v < V; v++) {
             P[q][v] = 0.f;
+            Pe[q][v] = 0.f;
             D[q][v] = df_zero();
         }
 #pragma unroll
@@ -638,12 +642,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
-                if (tag < 2) P[q][v] += val;
-                else D[q][v] = df_addf(D[q][v], val);
+                if (tag < 2) {
+                    float s_, e_;
+                    two_sum(P[q][v], val, s_, e_);  // the point sum continues compensated
+                    P[q][v] = s_;
+                    Pe[q][v] = __fadd_rn(Pe[q][v], e_);
+                } else {
+                    D[q][v] = df_addf(D[q][v], val);
+                }
             }
         }
 #pragma unroll
-        for (int v = 0; v < V; v++) tot[v] = df_add(tot[v], D[q][v]);
+        for (int v = 0; v < V; v++) tot[v] = df_add_rn(tot[v], D[q][v]);
     }
 
     // exclusive prefix of the group totals across the block, in a fixed order:
@@ -656,7 +666,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
         for (int v = 0; v < V; v++) {
             const df o = df_shfl_up(inc[v], d);
-            if (lane32 >= d) inc[v] = df_add(o, inc[v]);
+            if (lane32 >= d) inc[v] = df_add_rn(o, inc[v]);
         }
     if (lane32 >= 32 - G) {
 #pragma unroll
@@ -678,20 +688,20 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         if (threadIdx.x < NW * KB) {
             const int w = threadIdx.x / KB, c = threadIdx.x % KB;
             df r = run_s[c];
-            for (int w2 = 0; w2 < w; w2++) r = df_add(r, wtot_s[w2][c]);
+            for (int w2 = 0; w2 < w; w2++) r = df_add_rn(r, wtot_s[w2][c]);
             wpre_s[w][c] = r;
         }
         __syncthreads();
 #pragma unroll
-        for (int v = 0; v < V; v++) run[v] = df_add(wpre_s[warp][lane * V + v], excl[v]);
+        for (int v = 0; v < V; v++) run[v] = df_add_rn(wpre_s[warp][lane * V + v], excl[v]);
     } else {
 #pragma unroll
         for (int v = 0; v < V; v++) {
             df r = run_s[lane * V + v];
 #pragma unroll
             for (int w2 = 0; w2 < NW; w2++)
-                if (w2 < warp) r = df_add(r, wtot_s[w2][lane * V + v]);
-            run[v] = df_add(r, excl[v]);
+                if (w2 < warp) r = df_add_rn(r, wtot_s[w2][lane * V + v]);
+            run[v] = df_add_rn(r, excl[v]);
         }
     }
 
@@ -704,8 +714,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] = df_add(run[v], D[q][v]);
-            out.v[v] = df_val(df_addf(run[v], P[q][v]));
+            run[v] = df_add_rn(run[v], D[q][v]);
+            out.v[v] = df_val(df_addf(df_addf(run[v], P[q][v]), Pe[q][v]));
         }
         if (j >= end) continue;
         if constexpr (EPI == 0) {
