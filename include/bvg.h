@@ -126,7 +126,10 @@ int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
  * column), 1 (-1), 2 (an interval of that row starts here), 3 (an interval
  * of that row ended just before this column). carry[carry_ptr[t] ..
  * carry_ptr[t+1]) lists the rows of intervals [s, e) with
- * s < t * carry_tile_cols <= e. meta[i] = (i - r_i, or 0) | depth_i << 3. */
+ * s < t * carry_tile_cols <= e. meta[i] = (i - r_i, or 0) | depth_i << 3.
+ * Tail items: column j's entries past its first 3 in runs of at most 4,
+ * items [titem_ptr[j], titem_ptr[j+1]), each item = start index into the
+ * column-major entries | (count - 1) << 30. */
 typedef struct {
     int64_t n, words, col_entries, carry_tiles, carry_entries, carry_tile_cols;
     const uint8_t* meta;
@@ -138,6 +141,9 @@ typedef struct {
     const uint32_t* carry_ptr;
     const uint32_t* carry;
     const float* inv_outdeg;
+    int64_t tail_items;
+    const uint32_t* titem_ptr;
+    const uint32_t* titem;
 } bvg_layout_view;
 int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out);
 
@@ -361,6 +367,7 @@ int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);
 typedef struct {
     int64_t n, m, words, col_entries, carry_tiles, carry_entries, structure_bytes;
     int64_t pull_entries, pull_items, pull_intervals;  /* the pull's work items (see bvg_pull_items_size) */
+    int64_t tail_items;                                /* the push gather's tail items (bvg_layout_view) */
 } bvg_layout_info;
 int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 

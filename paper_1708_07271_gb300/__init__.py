@@ -67,13 +67,15 @@ class GraphStats(ctypes.Structure):
 
 class LayoutInfo(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "m", "words", "col_entries", "carry_tiles", "carry_entries",
-                                      "structure_bytes", "pull_entries", "pull_items", "pull_intervals")]
+                                      "structure_bytes", "pull_entries", "pull_items", "pull_intervals",
+                                      "tail_items")]
 
 
 class LayoutView(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "words", "col_entries", "carry_tiles", "carry_entries",
                                       "carry_tile_cols")] + \
-               [(f, _P) for f in ("meta", "desc", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")]
+               [(f, _P) for f in ("meta", "desc", "rowp", "ent", "colp", "tent", "carry_ptr", "carry", "inv_outdeg")] + \
+               [("tail_items", _I64), ("titem_ptr", _P), ("titem", _P)]
 
 
 class LaunchConfig(ctypes.Structure):
@@ -442,6 +444,8 @@ def bvg_layout_view_get(hg: HostGraph) -> dict:
         "carry_ptr": arr(v.carry_ptr, v.carry_tiles + 1, ctypes.c_uint32, np.uint32),
         "carry": arr(v.carry, v.carry_entries, ctypes.c_uint32, np.uint32),
         "inv_outdeg": arr(v.inv_outdeg, n, ctypes.c_float, np.float32),
+        "titem_ptr": arr(v.titem_ptr, n + 1, ctypes.c_uint32, np.uint32),
+        "titem": arr(v.titem, v.tail_items, ctypes.c_uint32, np.uint32),
     }
 
 

@@ -7,8 +7,8 @@ DRAM traffic measured by ncu above these figures means re-reads.
 
 Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
   push_chain   4n (descendant masks) + 4kn (x) + 4kn (z)
-  push_gather  4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
-               + 4*carry_entries + 4kn (z) + 4kn (y)
+  push_gather  4(n+1) (column offsets) + 4*col_entries + 4(n+1) + 4*tail_items
+               (tail items) + 4*(carry_tiles+1) + 4*carry_entries + 4kn (z) + 4kn (y)
   pull         n (meta) + 4(n+1) (item offsets per row) + 4(items+1) (item starts)
                + 4*pull_entries (expanded entries) + 4(n+1) + 8*pull_intervals
                (kept intervals) + 4kn (x) + 4kn (y); the items' partial sums
@@ -33,7 +33,8 @@ def push_chain(L: dict, k: int) -> int:
 
 def push_gather(L: dict, k: int) -> int:
     n = L["n"]
-    return 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"] + 8 * k * n
+    return (4 * (n + 1) + 4 * L["col_entries"] + 4 * (n + 1) + 4 * L.get("tail_items", 0)
+            + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"] + 8 * k * n)
 
 
 def pull(L: dict, k: int) -> int:

@@ -219,7 +219,8 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
     PrArgs pa{};
     TraceScope ts(g, "push_gather", st);
     launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 0>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
-               (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz, y, ldy,
+               (const uint32_t*)g->tent, (const uint32_t*)g->titem_ptr, (const uint32_t*)g->titem,
+               (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz, y, ldy,
                g->n, pa);
 }
 template <int KB, int V>
@@ -228,7 +229,8 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_gather", st);
     launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 1>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
-               (const uint32_t*)g->tent, (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz,
+               (const uint32_t*)g->tent, (const uint32_t*)g->titem_ptr, (const uint32_t*)g->titem,
+               (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz,
                (float*)nullptr, (int64_t)0, g->n, pa);
 }
 template <int KB, int V>
@@ -436,11 +438,14 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->nwords = (int64_t)L->ent.size();
         g->mean_interval = hg->stats.intervals ? (double)hg->stats.interval_members / (double)hg->stats.intervals : 0.0;
         g->ntent = (int64_t)L->tent.size();
+        g->ntitem = (int64_t)L->titem.size();
         g->ncarry = (int64_t)L->carry.size();
         g->fingerprint = layout_fingerprint(*L, n, hg->m);
         if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
             (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
+            (rc = upload_vec(&g->titem_ptr, L->titem_ptr, st, &g->bytes)) ||
+            (rc = upload_vec(&g->titem, L->titem, st, &g->bytes)) ||
             (rc = upload_vec(&g->carry_ptr, L->carry_ptr, st, &g->bytes)) ||
             (rc = upload_vec(&g->carry, L->carry, st, &g->bytes)) ||
             (rc = upload_vec(&g->inv_outdeg, L->inv_outdeg, st, &g->bytes))) {
@@ -474,7 +479,8 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
 
 extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
-    void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->carry_ptr, g->carry, g->inv_outdeg, g->s.z,
+    void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->titem_ptr, g->titem, g->carry_ptr, g->carry,
+                    g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part};
@@ -592,6 +598,7 @@ extern "C" int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out) {
     out->pull_entries = g->npent;
     out->pull_items = g->nitems;
     out->pull_intervals = g->nlint;
+    out->tail_items = g->ntitem;
     return BVG_OK;
 }
 

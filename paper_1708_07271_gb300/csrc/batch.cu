@@ -23,6 +23,8 @@ struct BatchEntry {
     const uint32_t* desc;
     const uint32_t* colp;
     const uint32_t* tent;
+    const uint32_t* titem_ptr;
+    const uint32_t* titem;
     const uint32_t* carry_ptr;
     const uint32_t* carry;
     const float* x;
@@ -59,7 +61,8 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const B
                                                       int64_t c0) {
     const BatchEntry e = tab[find_graph<false>(tab, count, blockIdx.x)];
     PrArgs pa{};
-    gather_tile<KB, V, 0>((int64_t)blockIdx.x - e.gather_tile0, e.colp, e.tent, e.carry_ptr, e.carry, e.z, KB,
+    gather_tile<KB, V, 0>((int64_t)blockIdx.x - e.gather_tile0, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr,
+                          e.carry, e.z, KB,
                           e.y + c0, ld, e.n, pa);
 }
 
@@ -299,6 +302,8 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
             e.desc = g->desc;
             e.colp = g->colp;
             e.tent = g->tent;
+            e.titem_ptr = g->titem_ptr;
+            e.titem = g->titem;
             e.carry_ptr = g->carry_ptr;
             e.carry = g->carry;
             e.x = xs[b->slot[i]];

@@ -35,6 +35,12 @@ constexpr int64_t kMaxN = (int64_t)1 << kIdBits;
 //   kTagIvS    an interval of row k starts at j  (D_j += z_k)
 //   kTagIvL    an interval of row k ends before j (D_j -= z_k)
 constexpr uint32_t kTagPlus = 0, kTagMinus = 1, kTagIvS = 2, kTagIvL = 3;
+// Push gather: the first kGatherSlots entries of a column are read by every
+// column's own straight-line code; the rest form tail items of at most
+// kTailItem consecutive entries (start index | (count - 1) << 30), handed out
+// to the CTA's threads evenly.
+constexpr int kGatherSlots = 3;
+constexpr int kTailItem = 4;
 inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
 
 void set_error(const char* fmt, ...);
@@ -45,6 +51,7 @@ struct HostLayout {
     std::vector<uint8_t> meta;
     std::vector<uint32_t> desc;
     std::vector<uint32_t> rowp, ent, colp, tent, carry_ptr, carry;
+    std::vector<uint32_t> titem_ptr, titem;  // tail items of the column-major entries
     std::vector<float> inv_outdeg;
     bool built = false;
 };
@@ -150,6 +157,9 @@ struct bvg_dev_graph {
     uint32_t* colp = nullptr;  // n+1
     uint32_t* tent = nullptr;
     int64_t ntent = 0;
+    uint32_t* titem_ptr = nullptr;  // n + 1: tail items of column j are [titem_ptr[j], titem_ptr[j + 1])
+    uint32_t* titem = nullptr;      // start in tent | (count - 1) << 30
+    int64_t ntitem = 0;
     uint32_t* carry_ptr = nullptr;  // ceil(n / kCarryTile) + 1
     uint32_t* carry = nullptr;      // source rows of intervals open at a carry-tile start
     int64_t ncarry = 0;

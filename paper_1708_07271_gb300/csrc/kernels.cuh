@@ -400,10 +400,12 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // scan is needed. A group of G = KB/V lanes owns CPT consecutive columns.
 // Each column's first S entries are loaded and summed by the same
 // straight-line predicated code in every lane (no divergence on the typical
-// column; longer columns finish in a short loop). One pass: the point terms
-// of a column's first S entries sum in FP32 in storage order (an error there
-// stays in y_j, and S is small); points past them (long columns: the hubs of a
-// power-law graph) sum compensated. Interval events and their prefix are carried as compensated
+// column; the entries past them form tail items of at most kTailItem
+// entries, handed to the CTA's lane groups evenly, one per group per round,
+// so no lane walks a long column while the rest of its warp waits. The point
+// terms of a column's first S entries sum in FP32 in storage order (an error
+// there stays in y_j, and S is small); the tail items' points (long columns:
+// the hubs of a power-law graph) sum compensated. Interval events and their prefix are carried as compensated
 // double-float values (two_sum steps, about 48 significant bits), because the
 // prefix carries any error to every later column of the tile. The block scan
 // runs in the same arithmetic, in a fixed order. y_j = P_j + I_j is rounded
@@ -422,7 +424,7 @@ struct GatherShape {
     static constexpr int NG = NT / G;                    // column groups per CTA
     static constexpr int CPT = 128 / NG > 2 ? 128 / NG : 2;  // consecutive columns per group
     static constexpr int T = NG * CPT;                   // columns per CTA (a multiple of kCarryTile)
-    static constexpr int S = 3;                          // entry slots per column in straight-line code
+    static constexpr int S = kGatherSlots;               // entry slots per column in straight-line code
 };
 
 template <int KB>
@@ -538,6 +540,8 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
 template <int KB, int V, int EPI>
 __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restrict__ colp,
                                             const uint32_t* __restrict__ tent,
+                                            const uint32_t* __restrict__ titem_ptr,
+                                            const uint32_t* __restrict__ titem,
                                             const uint32_t* __restrict__ carry_ptr,
                                             const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                             float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
@@ -555,9 +559,13 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     const int64_t c0 = a + (int64_t)g * CPT;
 
     // structure loads do not depend on the previous kernel: issue them first
-    uint32_t cp[CPT + 1];
+    uint32_t cp[CPT + 1], ip[CPT + 1];
 #pragma unroll
-    for (int q = 0; q <= CPT; q++) cp[q] = __ldg(colp + (c0 + q < end ? c0 + q : end));
+    for (int q = 0; q <= CPT; q++) {
+        cp[q] = __ldg(colp + (c0 + q < end ? c0 + q : end));
+        ip[q] = __ldg(titem_ptr + (c0 + q < end ? c0 + q : end));
+    }
+    const uint32_t it0 = __ldg(titem_ptr + a), it1 = __ldg(titem_ptr + end);  // the tile's tail items
     const int64_t ct = a / kCarryTile;
     const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
     // carry sources of this tile (warp 0; the first 32 now, any further ones later)
@@ -635,26 +643,111 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                 if (!point) D[q][v] = df_addf(D[q][v], val);
             }
         }
-        for (uint32_t e = cp[q] + S; e < cp[q + 1]; e++) {  // longer columns
-            const uint32_t we = __ldg(tent + e);
-            Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
-            const uint32_t tag = we >> kIdBits;
+    }
+
+    // tail items (entries past a column's first S). With one lane per column
+    // group the items are shared out: one item per group per round, its point
+    // and event partial sums in shared memory, then each column adds the
+    // items of the round that are its own, in order. With several lanes per
+    // group (wide column blocks) each group reads its own columns' items in
+    // order instead (no extra barriers, fewer registers).
+    if constexpr (G > 1) {
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
-                if (tag < 2) {
-                    float s_, e_;
-                    two_sum(P[q][v], val, s_, e_);  // the point sum continues compensated
-                    P[q][v] = s_;
-                    Pe[q][v] = __fadd_rn(Pe[q][v], e_);
-                } else {
-                    D[q][v] = df_addf(D[q][v], val);
+        for (int q = 0; q < CPT; q++) {
+            for (uint32_t k = ip[q]; k < ip[q + 1]; k++) {
+                const uint32_t wi = __ldg(titem + k);
+                const uint32_t e0 = wi & 0x3fffffffu, cnt = (wi >> 30) + 1u;
+                uint32_t we[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) we[t] = (uint32_t)t < cnt ? __ldg(tent + e0 + t) : 0u;
+                Vec<V> zc[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+#pragma unroll
+                    for (int v = 0; v < V; v++) zc[t].v[v] = 0.f;
+                    if ((uint32_t)t < cnt) zc[t] = ldv_ca<V>(z + (int64_t)id_of(we[t]) * ldz + lane * V);
+                }
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+                    if ((uint32_t)t >= cnt) break;
+                    const uint32_t tag = we[t] >> kIdBits;
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        const float val = (tag & 1) ? -zc[t].v[v] : zc[t].v[v];
+                        if (tag < 2) {
+                            float s_, e_;
+                            two_sum(P[q][v], val, s_, e_);  // the point sum continues compensated
+                            P[q][v] = s_;
+                            Pe[q][v] = __fadd_rn(Pe[q][v], e_);
+                        } else {
+                            D[q][v] = df_addf(D[q][v], val);
+                        }
+                    }
                 }
             }
         }
+    } else {
+        constexpr int NGR = NT / G;  // items per round
+        __shared__ df tail_pt[NGR][KB], tail_ev[NGR][KB];
+        for (uint32_t r0 = it0; r0 < it1; r0 += NGR) {  // the same trip count in every thread
+            const uint32_t i = r0 + (uint32_t)g;
+            if (i < it1) {
+                const uint32_t wi = __ldg(titem + i);
+                const uint32_t e0 = wi & 0x3fffffffu, cnt = (wi >> 30) + 1u;
+                uint32_t we[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) we[t] = (uint32_t)t < cnt ? __ldg(tent + e0 + t) : 0u;
+                Vec<V> zc[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+#pragma unroll
+                    for (int v = 0; v < V; v++) zc[t].v[v] = 0.f;
+                    if ((uint32_t)t < cnt) zc[t] = ldv_ca<V>(z + (int64_t)id_of(we[t]) * ldz + lane * V);
+                }
+                df pt[V], ev[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) pt[v] = ev[v] = df_zero();
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+                    const uint32_t tag = we[t] >> kIdBits;
+                    const bool point = tag < 2;
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        const float val = (tag & 1) ? -zc[t].v[v] : zc[t].v[v];
+                        pt[v] = df_addf(pt[v], point ? val : 0.f);
+                        ev[v] = df_addf(ev[v], point ? 0.f : val);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    tail_pt[g][lane * V + v] = pt[v];
+                    tail_ev[g][lane * V + v] = ev[v];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < CPT; q++) {
+                const uint32_t b = ip[q] > r0 ? ip[q] : r0;
+                const uint32_t e = ip[q + 1] < r0 + NGR ? ip[q + 1] : r0 + NGR;
+                for (uint32_t k = b; k < e; k++) {
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        const df tp = tail_pt[k - r0][lane * V + v];
+                        float s_, e_;
+                        two_sum(P[q][v], tp.hi, s_, e_);  // the point sum continues compensated
+                        P[q][v] = s_;
+                        Pe[q][v] = __fadd_rn(Pe[q][v], __fadd_rn(e_, tp.lo));
+                        D[q][v] = df_add_rn(D[q][v], tail_ev[k - r0][lane * V + v]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; q++)
 #pragma unroll
         for (int v = 0; v < V; v++) tot[v] = df_add_rn(tot[v], D[q][v]);
-    }
 
     // exclusive prefix of the group totals across the block, in a fixed order:
     // carry, then the warps before this one, then the groups before this one
@@ -744,11 +837,13 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 
 template <int KB, int V, int EPI>
 __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                                const uint32_t* __restrict__ titem_ptr,
+                                                const uint32_t* __restrict__ titem,
                                                 const uint32_t* __restrict__ carry_ptr,
                                                 const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                                 float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
-    gather_tile<KB, V, EPI>(blockIdx.x, colp, tent, carry_ptr, carry, z, ldz, y, ldy, n, pa);
+    gather_tile<KB, V, EPI>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, z, ldz, y, ldy, n, pa);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the

@@ -13,6 +13,9 @@
 // starting at a, the rows k of intervals with s < a <= e, whose start event
 // lies before the tile and whose end event (if any) lies at or after a;
 // summing their z gives the running sum at a without a grid-wide scan.
+// Tail items: each column's entries past the first kGatherSlots, cut into
+// runs of at most kTailItem entries (the gather hands them to its threads
+// evenly instead of letting one thread walk a long column).
 #include <algorithm>
 #include <climits>
 #include <new>
@@ -66,6 +69,8 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
                 return fail(BVG_ERR_UNSUPPORTED, "layout: more than 2^32 column entries");
             L.colp[j + 1] += L.colp[j];
         }
+        if ((int64_t)L.colp[n] >= ((int64_t)1 << 30))
+            return fail(BVG_ERR_UNSUPPORTED, "layout: more than 2^30 column entries");
         L.tent.assign(L.colp[n], 0);
         std::vector<uint32_t> fillp(L.colp.begin(), L.colp.end() - 1);
         const int64_t ntiles = (n + kCarryTile - 1) / kCarryTile;
@@ -91,6 +96,17 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
                 for (int64_t ct = s0 / kCarryTile + 1; ct <= e / kCarryTile && ct < ntiles; ct++)
                     L.carry[cfill[ct]++] = (uint32_t)i;
             }
+        // tail items: each column's entries past the first kGatherSlots, in
+        // runs of at most kTailItem
+        L.titem_ptr.assign(n + 1, 0);
+        for (int64_t j = 0; j < n; j++) {
+            L.titem_ptr[j] = (uint32_t)L.titem.size();
+            for (int64_t e = (int64_t)L.colp[j] + kGatherSlots; e < (int64_t)L.colp[j + 1]; e += kTailItem) {
+                const int64_t cnt = std::min<int64_t>(kTailItem, (int64_t)L.colp[j + 1] - e);
+                L.titem.push_back((uint32_t)e | (uint32_t)(cnt - 1) << 30);
+            }
+        }
+        L.titem_ptr[n] = (uint32_t)L.titem.size();
     } catch (const std::bad_alloc&) {
         return fail(BVG_ERR_OOM, "layout: host allocation failed");
     }
@@ -197,6 +213,9 @@ extern "C" int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out
     out->carry_ptr = L->carry_ptr.data();
     out->carry = L->carry.data();
     out->inv_outdeg = L->inv_outdeg.data();
+    out->tail_items = (int64_t)L->titem.size();
+    out->titem_ptr = L->titem_ptr.data();
+    out->titem = L->titem.data();
     return BVG_OK;
 }
 

@@ -67,7 +67,8 @@ void launch_pair(const bvg_dev_graph* g, const float* x, int64_t ld, float* z, f
     k_chain<KB, V><<<(unsigned)cgrid, ChainShape<KB, V>::NT, 0, st>>>(g->desc, x, ld, nullptr, z, KB, g->n, nullptr);
     const int64_t ggrid = (g->n + GatherShape<KB, V>::T - 1) / GatherShape<KB, V>::T;
     PrArgs pa{};
-    k_gather<KB, V, 0><<<(unsigned)ggrid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->carry_ptr, g->carry,
+    k_gather<KB, V, 0><<<(unsigned)ggrid, GatherShape<KB, V>::NT, 0, st>>>(g->colp, g->tent, g->titem_ptr, g->titem,
+                                                                         g->carry_ptr, g->carry,
                                                                          z, KB, y, ld, g->n, pa);
 }
 

@@ -165,3 +165,23 @@ def test_pull_items_reproduce_products(name, item, min_len):
     lens = (ent[np.nonzero(tag == 2)[0] + 1] & MASK)
     assert len(P["pent"]) == int(np.sum(tag < 2) + lens[lens < min_len].sum())
     assert len(P["lint"]) == int(np.sum(lens >= min_len))
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_tail_items_cover_the_long_columns(name):
+    """The push gather reads a column's first 3 entries itself and its other
+    entries through tail items of at most 4: the items must cover exactly
+    those entries, column by column, in order."""
+    g = GRAPHS[name]()
+    L = bvg.bvg_layout_view_get(bvg.bvg_encode(g.row_ptr, g.col))
+    colp = L["colp"].astype(np.int64)
+    tp = L["titem_ptr"].astype(np.int64)
+    items = L["titem"].astype(np.int64)
+    assert tp[0] == 0 and tp[-1] == len(items) and np.all(np.diff(tp) >= 0)
+    start = items & ((1 << 30) - 1)
+    cnt = (items >> 30) + 1
+    for j in np.nonzero(np.diff(colp) > 3)[0][:2000]:
+        covered = np.concatenate([np.arange(s, s + c) for s, c in zip(start[tp[j]:tp[j + 1]], cnt[tp[j]:tp[j + 1]])])
+        np.testing.assert_array_equal(covered, np.arange(colp[j] + 3, colp[j + 1]))
+    short = np.diff(colp) <= 3
+    assert np.all(np.diff(tp)[short] == 0)
