@@ -233,12 +233,60 @@ __global__ void __launch_bounds__(256) k_pull_items(const uint32_t* __restrict__
 }
 
 template <int KB, int V>
+__device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k0, uint32_t k1, const float2* part,
+                                             const uint32_t* __restrict__ lrow, const uint32_t* __restrict__ lint,
+                                             const float* __restrict__ x, int64_t ldx, int lane,
+                                             const PrefixArgs& pf) {
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = df_zero();
+    for (uint32_t k = k0; k < k1; k++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const float2 p = __ldcg(part + (int64_t)k * KB + lane * V + v);
+            acc[v] = df_add(acc[v], {p.x, p.y});
+        }
+    }
+    const uint32_t l0 = __ldg(lrow + i), l1 = __ldg(lrow + i + 1);
+    for (uint32_t q = l0; q < l1; q++) {  // kept (long) intervals
+        const uint32_t s0 = __ldg(lint + 2 * q), len = __ldg(lint + 2 * q + 1);
+        if (pf.lhi) {
+            pull_interval_prefix<KB, V>(acc, s0, len, lane, pf);
+        } else {
+            for (uint32_t t = 0; t < len; t++) {
+                Vec<V> xv = ldv<V>(x + (int64_t)(s0 + t) * ldx + lane * V);
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
+            }
+        }
+    }
+}
+
+// The reference chain of tile row r (indices into the tile's c): r, r's
+// reference, ..., at most kMaxChain links, never leaving the kHalo rows.
+__device__ __forceinline__ int pull_chain_of(const uint8_t* __restrict__ meta, int64_t lo, int r,
+                                             int (&idx)[kMaxChain + 1]) {
+    int len = 0, cur = r;
+    idx[len++] = cur;
+    for (int t = 0; t < kMaxChain; t++) {
+        const int off = __ldg(meta + lo + cur) & 7;
+        if (off == 0 || cur - off < 0) break;
+        cur -= off;
+        idx[len++] = cur;
+    }
+    return len;
+}
+
+template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ irow,
                                                    const float2* part, const uint32_t* __restrict__ lrow,
                                                    const uint32_t* __restrict__ lint, const float* __restrict__ x,
                                                    int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n,
                                                    int tile, PrefixArgs pf) {
     constexpr int G = KB / V;
+    // rows per group whose structure is read before the wait (one-lane groups;
+    // for wider groups the extra registers cost more than the overlap gains)
+    constexpr int PF = G == 1 ? 2 : 0;
+    constexpr int PFA = PF > 0 ? PF : 1;
     extern __shared__ float4 smem_pull[];
     df* c = reinterpret_cast<df*>(smem_pull);  // [(tile + kHalo) * KB]
     const int NG = blockDim.x / G;
@@ -247,57 +295,59 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
     const int64_t lo = a > kHalo ? a - kHalo : 0;
     const int64_t hi = a + tile < n ? a + tile : n;
     const int cnt = (int)(hi - lo);
+    const int own0 = (int)(a - lo);
+
+    // structure first: it does not depend on the item pass, which may still be
+    // running (programmatic dependent launch). The item ranges of the group's
+    // first PF rows and the chains of the first PF rows it outputs.
+    uint32_t kr[PFA][2];
+    int idx[PFA][kMaxChain + 1], clen[PFA];
+#pragma unroll
+    for (int j = 0; j < PF; j++) {
+        const int r = g + j * NG;
+        kr[j][0] = r < cnt ? __ldg(irow + lo + r) : 0u;
+        kr[j][1] = r < cnt ? __ldg(irow + lo + r + 1) : 0u;
+        const int ro = own0 + g + j * NG;
+        clen[j] = ro < cnt ? pull_chain_of(meta, lo, ro, idx[j]) : 0;
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the items' partial sums are ready
 
-    for (int r = g; r < cnt; r += NG) {
-        const int64_t i = lo + r;
+#pragma unroll
+    for (int j = 0; j < PF; j++) {
+        const int r = g + j * NG;
+        if (r < cnt) {
+            df acc[V];
+            pull_row_sum<KB, V>(acc, lo + r, kr[j][0], kr[j][1], part, lrow, lint, x, ldx, lane, pf);
+#pragma unroll
+            for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
+        }
+    }
+    for (int r = g + PF * NG; r < cnt; r += NG) {
         df acc[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = df_zero();
-        const uint32_t k0 = __ldg(irow + i), k1 = __ldg(irow + i + 1);
-        for (uint32_t k = k0; k < k1; k++) {
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float2 p = __ldcg(part + (int64_t)k * KB + lane * V + v);
-                acc[v] = df_add(acc[v], {p.x, p.y});
-            }
-        }
-        const uint32_t l0 = __ldg(lrow + i), l1 = __ldg(lrow + i + 1);
-        for (uint32_t q = l0; q < l1; q++) {  // kept (long) intervals
-            const uint32_t s0 = __ldg(lint + 2 * q), len = __ldg(lint + 2 * q + 1);
-            if (pf.lhi) {
-                pull_interval_prefix<KB, V>(acc, s0, len, lane, pf);
-            } else {
-                for (uint32_t t = 0; t < len; t++) {
-                    Vec<V> xv = ldv<V>(x + (int64_t)(s0 + t) * ldx + lane * V);
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], xv.v[v]);
-                }
-            }
-        }
+        pull_row_sum<KB, V>(acc, lo + r, __ldg(irow + lo + r), __ldg(irow + lo + r + 1), part, lrow, lint, x, ldx,
+                            lane, pf);
 #pragma unroll
         for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
     }
     __syncthreads();
 
-    for (int r = (int)(a - lo) + g; r < cnt; r += NG) {
-        int idx[kMaxChain + 1];
-        int len = 0, cur = r;
-        idx[len++] = cur;
-        for (int t = 0; t < kMaxChain; t++) {
-            const int off = __ldg(meta + lo + cur) & 7;
-            if (off == 0 || cur - off < 0) break;
-            cur -= off;
-            idx[len++] = cur;
-        }
+    auto emit = [&](int r, const int (&ix)[kMaxChain + 1], int len) {
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            df sacc = c[(int64_t)idx[len - 1] * KB + lane * V + v];
-            for (int t = len - 2; t >= 0; t--) sacc = df_add(c[(int64_t)idx[t] * KB + lane * V + v], sacc);
+            df sacc = c[(int64_t)ix[len - 1] * KB + lane * V + v];
+            for (int t = len - 2; t >= 0; t--) sacc = df_add(c[(int64_t)ix[t] * KB + lane * V + v], sacc);
             out.v[v] = df_val(sacc);
         }
         stv<V>(y + (lo + r) * ldy + lane * V, out);
+    };
+#pragma unroll
+    for (int j = 0; j < PF; j++)
+        if (clen[j] > 0) emit(own0 + g + j * NG, idx[j], clen[j]);
+    for (int r = own0 + g + PF * NG; r < cnt; r += NG) {
+        int ix[kMaxChain + 1];
+        const int len = pull_chain_of(meta, lo, r, ix);
+        emit(r, ix, len);
     }
 }
 
