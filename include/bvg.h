@@ -163,6 +163,21 @@ int bvg_pull_items_size(const bvg_host_graph* g, int32_t item, int32_t min_len, 
 int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_t min_len, uint32_t* pent, uint32_t* istart,
                         uint32_t* irow, uint32_t* lrow, uint32_t* lint);
 
+/* The push's point columns, on the host (no GPU needed): for every column j,
+ * the source rows k of the nonzeros of column j of A' (Proposition 1's
+ * difference matrix), in increasing k, as 32-bit words: tag (two high bits)
+ * 0 for +1 (a residual id or a member of an interval of row k), 1 for -1 (a
+ * dropped id), over the 30-bit row k. Every interval member is listed, so
+ * y_j = sum of +-z_k over column j alone (no running interval sum).
+ * colp[n + 1]: column j is ent[colp[j], colp[j + 1]). Tail items: the
+ * entries of column j past its first 4, in runs of at most 4, items
+ * [titem_ptr[j], titem_ptr[j + 1]), each item = start index | (count - 1)
+ * << 30. Sizes first, then the arrays into caller buffers. The x A product
+ * builds the same arrays on the device the first time a launch uses them.
+ * Errors: INVALID_ARG, OOM, UNSUPPORTED (2^30 entries or more). */
+int bvg_point_cols_size(const bvg_host_graph* g, int64_t* entries, int64_t* tail_items);
+int bvg_point_cols_fill(const bvg_host_graph* g, uint32_t* colp, uint32_t* ent, uint32_t* titem_ptr, uint32_t* titem);
+
 /* Builds the device layout of `g` (row-major difference rows for A x^T, the
  * same entries grouped by column for x A, per-row reference offsets and
  * chain depths, 1/outdeg) and copies it to the current device on `stream`.
@@ -181,7 +196,13 @@ int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int
 /* y = x A (push, Proposition 1 read for the left product): z_k = sum of x_i
  * over rows whose chain passes through k (x pushed down the reference chains
  * in reverse level order), then y = sum_k z_k a'_k, gathered per column with
- * no atomics (deterministic). x, y: device n x k. Asynchronous. */
+ * no atomics (deterministic). The gather reads either the event columns
+ * (intervals as start / end events and a running sum across columns,
+ * bvg_layout_view) or the point columns (bvg_point_cols_size), as the launch
+ * configuration's push_points says; the point columns are built and copied
+ * to the device (synchronising `stream`) the first time a launch uses them,
+ * and if they cannot be built (2^30 entries or more) the event columns
+ * serve. x, y: device n x k. Asynchronous. Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
 /* Same product as bvg_spmv_xA, for callers that must not allocate device
@@ -240,10 +261,13 @@ int bvg_batch_size(const bvg_batch* b, int32_t* count, int64_t* total_n, int64_t
  * aligned (16-byte alignment and k % 4 == 0 enable 128-bit accesses). The
  * pointer table is staged through pinned memory and copied on `stream`
  * ahead of the launches; the result of graph i is bit-identical to
- * bvg_spmv_xA on the same graph with the same buffers. Calls on one batch
- * are ordered among themselves even across streams (a later call waits for
- * the earlier one); the first call with a larger k allocates. Asynchronous.
- * Errors: INVALID_ARG, OOM, CUDA. */
+ * bvg_spmv_xA on the same graph with the same buffers and launch
+ * configuration (each graph's gather reads its event or point columns as its
+ * configuration says; point columns not built yet are built first, which
+ * synchronises `stream`). Calls on one batch are ordered among themselves
+ * even across streams (a later call waits for the earlier one); the first
+ * call with a larger k allocates. Asynchronous. Errors: INVALID_ARG, OOM,
+ * CUDA. */
 int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* const* ys, int32_t k, void* stream);
 /* Waits for the batch's last call, then frees it (not the graphs). */
 void bvg_free_batch(bvg_batch* b);
@@ -319,6 +343,8 @@ typedef struct {
     int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */
     int32_t col_block;      /* widest column block of a product: power of two in [1, 32] (default 32) */
     int32_t pull_item;      /* pull: entries per work item, 4, 8 or 16 (default 8) */
+    int32_t push_points;    /* push gather over the point columns: -1 for column blocks of 4 or more right-hand
+                               sides (default), 0 never (event columns), 1 always */
 } bvg_launch_config;
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
@@ -327,7 +353,7 @@ int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
  * candidate launch configuration (CUDA events on `stream`, median of 7 after
  * 2 warm-up calls, warm caches): first the push (x A) over the widest column
  * block (the largest power of two <= min(k, 32) and up to three halvings)
- * times gather overlap on/off, then the pull (A x^T) over entries per work
+ * times gather overlap on/off times event or point columns, then the pull (A x^T) over entries per work
  * item {4, 8, 16} times rows per CTA of the row pass {256, 512} times the
  * length from which intervals stay unexpanded (32; also 16 and "never" when
  * the graph has intervals; rebuilding the items is part of the search).
@@ -368,6 +394,7 @@ typedef struct {
     int64_t n, m, words, col_entries, carry_tiles, carry_entries, structure_bytes;
     int64_t pull_entries, pull_items, pull_intervals;  /* the pull's work items (see bvg_pull_items_size) */
     int64_t tail_items;                                /* the push gather's tail items (bvg_layout_view) */
+    int64_t point_entries, point_tail_items;           /* the point columns (bvg_point_cols_size); 0 until built */
 } bvg_layout_info;
 int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 

@@ -39,7 +39,8 @@ EXPORTED = [
     "bvg_mlp_get_params", "bvg_features", "bvg_mlp_predict", "bvg_mlp_grad", "bvg_mlp_adam", "bvg_warmstart_train",
     "bvg_warmstart_predict", "bvg_free_mlp", "bvg_batch_create", "bvg_batch_size", "bvg_batch_spmv_xA",
     "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
-    "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill",
+    "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
+    "bvg_point_cols_fill",
 ]
 
 
@@ -68,7 +69,7 @@ class GraphStats(ctypes.Structure):
 class LayoutInfo(ctypes.Structure):
     _fields_ = [(f, _I64) for f in ("n", "m", "words", "col_entries", "carry_tiles", "carry_entries",
                                       "structure_bytes", "pull_entries", "pull_items", "pull_intervals",
-                                      "tail_items")]
+                                      "tail_items", "point_entries", "point_tail_items")]
 
 
 class LayoutView(ctypes.Structure):
@@ -80,7 +81,7 @@ class LayoutView(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
-                ("col_block", _I32), ("pull_item", _I32)]
+                ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32)]
 
 
 class AutotuneInfo(ctypes.Structure):
@@ -166,6 +167,8 @@ def load(build_if_needed: bool = True):
             "bvg_pull_items_size": ([_P, _I32, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                      ctypes.POINTER(_I64)], ctypes.c_int),
             "bvg_pull_items_fill": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
+            "bvg_point_cols_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_point_cols_fill": ([_P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -646,7 +649,8 @@ def bvg_autotune_cache_lookup(path, key: str):
 
 
 def bvg_autotune_cache_store(path, key: str, config: dict, push_us: float = 0.0, pull_us: float = 0.0):
-    c = LaunchConfig(**{f: int(config[f]) for f, _ in LaunchConfig._fields_})
+    c = LaunchConfig(**{f: int(config.get(f, -1) if f == "push_points" else config[f])
+                        for f, _ in LaunchConfig._fields_})
     _check(load().bvg_autotune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c), push_us, pull_us),
            "bvg_autotune_cache_store")
 
@@ -666,4 +670,19 @@ def bvg_pull_items(hg: HostGraph, item: int = 8, min_len: int = 32) -> dict:
            "bvg_pull_items_fill")
     out["pent"] = out["pent"][:e.value]
     out["lint"] = out["lint"][:2 * m.value].reshape(-1, 2)
+    return out
+
+
+def bvg_point_cols(hg: HostGraph) -> dict:
+    """The push's point columns for a host graph (no GPU needed)."""
+    lib = load()
+    e, t = _I64(), _I64()
+    _check(lib.bvg_point_cols_size(hg.ptr, ctypes.byref(e), ctypes.byref(t)), "bvg_point_cols_size")
+    n = bvg_host_size(hg)[0]
+    out = {"colp": np.zeros(n + 1, np.uint32), "ent": np.zeros(max(e.value, 1), np.uint32),
+           "titem_ptr": np.zeros(n + 1, np.uint32), "titem": np.zeros(max(t.value, 1), np.uint32)}
+    _check(lib.bvg_point_cols_fill(hg.ptr, *[out[f].ctypes.data for f in ("colp", "ent", "titem_ptr", "titem")]),
+           "bvg_point_cols_fill")
+    out["ent"] = out["ent"][:e.value]
+    out["titem"] = out["titem"][:t.value]
     return out

@@ -14,14 +14,14 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
                (kept intervals) + 4kn (x) + 4kn (y); the items' partial sums
                (8 bytes per item and right-hand side, written then read back)
                are scratch that stays in L2 and are not counted
+  push_gather_pt  (point columns) 4(n+1) (column offsets) + 4*point_entries
+               [+ 4(n+1) + 4*point_tail_items (tail items) when k <= 4, where one lane
+               group owns a column and the tail items are shared out] + 4kn (z) + 4kn (y)
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
-  push_fused   4(n+1) (column offsets) + 4*col_entries + 4*(carry_tiles+1)
-               + 4*carry_entries + 4n (descendant masks) + 4kn (x) + 4kn (y)
-  pr_fused     push_fused - 4kn (y not stored) + 4n (1/outdeg) + 4kn (q_prev)
-               + 8kn (q_new, next input) [+ 4kn (p0) when teleport vectors are given]
   pr_chain     push_chain + 4n (1/outdeg)
   pr_gather    push_gather - 4kn (y not stored) + 4n (1/outdeg) + 4kn (q_prev)
-               + 4kn (q_new) [+ 4kn (p0) when teleport vectors are given]
+               + 4kn (q_new) [+ 4kn (p0) when teleport vectors are given]; pr_gather_pt
+               likewise from push_gather_pt
 """
 from __future__ import annotations
 
@@ -56,19 +56,19 @@ def pr_gather(L: dict, k: int, with_p0: bool) -> int:
     return push_gather(L, k) - 4 * k * n + 4 * n + 8 * k * n + (4 * k * n if with_p0 else 0)
 
 
+def push_gather_pt(L: dict, k: int) -> int:
+    n = L["n"]
+    tail = 4 * (n + 1) + 4 * L["point_tail_items"] if k <= 4 else 0
+    return 4 * (n + 1) + 4 * L["point_entries"] + tail + 8 * k * n
+
+
+def pr_gather_pt(L: dict, k: int, with_p0: bool) -> int:
+    n = L["n"]
+    return push_gather_pt(L, k) - 4 * k * n + 4 * n + 8 * k * n + (4 * k * n if with_p0 else 0)
+
+
 def xA_total(L: dict, k: int) -> int:
     return push_chain(L, k) + push_gather(L, k)
 
 
-def push_fused(L: dict, k: int) -> int:
-    n = L["n"]
-    return (4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"] + 4 * n
-            + 8 * k * n)
-
-
-def pr_fused(L: dict, k: int, with_p0: bool) -> int:
-    n = L["n"]
-    return push_fused(L, k) - 4 * k * n + 4 * n + 12 * k * n + (4 * k * n if with_p0 else 0)
-
-
-KERNELS = {"push_fused": push_fused, "push_gather": push_gather, "push_chain": push_chain, "pull": pull}
+KERNELS = {"push_gather": push_gather, "push_gather_pt": push_gather_pt, "push_chain": push_chain, "pull": pull}

@@ -212,11 +212,29 @@ static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, co
     k_chain<KB, V><<<(unsigned)grid, ChainShape<KB, V>::NT, 0, st>>>(g->desc, x, ldx, rowscale, z, ldz, g->n, pst);
 }
 
+// Whether the gather of a kb-wide column block reads the point columns
+// (which ensure_points has built when this is true).
+bool use_points(const bvg_dev_graph* g, int kb) {
+    if (g->pcol_state != 1) return false;
+    return g->cfg.push_points == 1 || (g->cfg.push_points < 0 && kb >= 4);
+}
+bool want_points(const bvg_dev_graph* g, int kb) {
+    if (g->pcol_state < 0) return false;
+    return g->cfg.push_points == 1 || (g->cfg.push_points < 0 && kb >= 4);
+}
+
 template <int KB, int V>
 static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, float* y, int64_t ldy, cudaStream_t st) {
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
     PrArgs pa{};
+    if (use_points(g, KB)) {
+        TraceScope ts(g, "push_gather_pt", st);
+        launch_pdl(g->cfg.gather_pdl, k_gather_pt<KB, V, 0>, grid, GatherShape<KB, V>::NT, st,
+                   (const uint32_t*)g->pcolp, (const uint32_t*)g->pcent, (const uint32_t*)g->ptitem_ptr,
+                   (const uint32_t*)g->ptitem, z, ldz, y, ldy, g->n, pa);
+        return;
+    }
     TraceScope ts(g, "push_gather", st);
     launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 0>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
                (const uint32_t*)g->tent, (const uint32_t*)g->titem_ptr, (const uint32_t*)g->titem,
@@ -227,6 +245,13 @@ template <int KB, int V>
 static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz, const PrArgs& pa, cudaStream_t st) {
     const int tile = gather_tile(KB, V, g->cfg);
     const int64_t grid = (g->n + tile - 1) / tile;
+    if (use_points(g, KB)) {
+        TraceScope ts(g, "pr_gather_pt", st);
+        launch_pdl(g->cfg.gather_pdl, k_gather_pt<KB, V, 1>, grid, GatherShape<KB, V>::NT, st,
+                   (const uint32_t*)g->pcolp, (const uint32_t*)g->pcent, (const uint32_t*)g->ptitem_ptr,
+                   (const uint32_t*)g->ptitem, z, ldz, (float*)nullptr, (int64_t)0, g->n, pa);
+        return;
+    }
     TraceScope ts(g, "pr_gather", st);
     launch_pdl(g->cfg.gather_pdl, k_gather<KB, V, 1>, grid, GatherShape<KB, V>::NT, st, (const uint32_t*)g->colp,
                (const uint32_t*)g->tent, (const uint32_t*)g->titem_ptr, (const uint32_t*)g->titem,
@@ -336,6 +361,31 @@ static int build_pull_items(bvg_dev_graph* g, int item, int min_len, int prefix_
     g->pull_built_item = item;
     g->pull_built_minlen = min_len;
     g->pull_built_auto = prefix_mode < 0 ? 1 : 0;
+    return BVG_OK;
+}
+
+// Builds the point columns (see build_point_cols) from the host copy of the
+// difference rows and copies them to the device, once; synchronous. If they
+// cannot be built (2^30 entries or more) the event columns serve from then on.
+int ensure_points(bvg_dev_graph* g, void* stream) {
+    if (g->pcol_state != 0) return BVG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    PointCols P;
+    int rc = build_point_cols(g->host_rowp.data(), g->host_ent.data(), g->n, P);
+    if (rc == BVG_ERR_UNSUPPORTED) {
+        g->pcol_state = -1;
+        return BVG_OK;
+    }
+    if (rc) return rc;
+    int64_t bytes = 0;
+    if ((rc = upload_vec(&g->pcolp, P.colp, st, &bytes)) || (rc = upload_vec(&g->pcent, P.ent, st, &bytes)) ||
+        (rc = upload_vec(&g->ptitem_ptr, P.titem_ptr, st, &bytes)) || (rc = upload_vec(&g->ptitem, P.titem, st, &bytes)))
+        return rc;
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    g->npcent = (int64_t)P.ent.size();
+    g->nptitem = (int64_t)P.titem.size();
+    g->pcol_bytes = bytes;
+    g->pcol_state = 1;
     return BVG_OK;
 }
 
@@ -483,7 +533,8 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->inv_outdeg, g->s.z,
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
-                    g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part};
+                    g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -559,6 +610,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
     out->gather_pdl = g->cfg.gather_pdl;
     out->col_block = g->cfg.col_block;
     out->pull_item = g->cfg.pull_item;
+    out->push_points = g->cfg.push_points;
     return BVG_OK;
 }
 
@@ -567,22 +619,25 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     if (in->pull_tile < 64 || in->pull_tile > 2048 || (in->pull_tile & (in->pull_tile - 1)) ||
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
         in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)) ||
-        (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16))
+        (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16) || in->push_points < -1 ||
+        in->push_points > 1)
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
                                          "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
-                                         "of two in [1, 32], pull_item in {4, 8, 16}");
+                                         "of two in [1, 32], pull_item in {4, 8, 16}, push_points in {-1,0,1}");
     if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen ||
         (in->pull_prefix < 0 ? 1 : 0) != g->pull_built_auto) {
         int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, in->pull_prefix, nullptr);
         if (rc) return rc;
     }
-    if (in->gather_pdl != g->cfg.gather_pdl) drop_pr_graph(g);  // the PageRank graph was captured with the old launch
+    if (in->gather_pdl != g->cfg.gather_pdl || in->push_points != g->cfg.push_points)
+        drop_pr_graph(g);  // the PageRank graph was captured with the old launch
     g->cfg.pull_tile = in->pull_tile;
     g->cfg.pull_prefix = in->pull_prefix;
     g->cfg.prefix_min_len = in->prefix_min_len;
     g->cfg.gather_pdl = in->gather_pdl;
     g->cfg.col_block = in->col_block;
     g->cfg.pull_item = in->pull_item;
+    g->cfg.push_points = in->push_points;
     return BVG_OK;
 }
 
@@ -594,11 +649,13 @@ extern "C" int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out) {
     out->col_entries = g->ntent;
     out->carry_tiles = (g->n + kCarryTile - 1) / kCarryTile;
     out->carry_entries = g->ncarry;
-    out->structure_bytes = g->bytes + g->pull_bytes;
+    out->structure_bytes = g->bytes + g->pull_bytes + g->pcol_bytes;
     out->pull_entries = g->npent;
     out->pull_items = g->nitems;
     out->pull_intervals = g->nlint;
     out->tail_items = g->ntitem;
+    out->point_entries = g->npcent;
+    out->point_tail_items = g->nptitem;
     return BVG_OK;
 }
 
@@ -636,6 +693,7 @@ extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, in
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
         if ((rc = ensure_z(g, kb))) return rc;
+        if (want_points(g, kb) && (rc = ensure_points(g, st))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
         BVG_KV_CASES(launch_chain, g, x + c0, ld, nullptr, g->s.z, kb, nullptr, st);
         BVG_KV_CASES(launch_gather, g, g->s.z, kb, y + c0, ld, st);
@@ -698,6 +756,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     if ((rc = ensure_pr(g, k))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int kb = k;
+    if (want_points(g, kb) && (rc = ensure_points(g, st))) return rc;
     const int v = pick_v(kb, kb, 0, {p0, p_init, p_out, g->s.q[0], g->s.q[1]});
 
     PrState hs{0, 0, 0, max_iter, tol};
@@ -733,7 +792,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     // is captured once per configuration and replayed; the device state makes
     // updates past convergence or max_iter return at once.
     constexpr int kChunk = 8;
-    const int key[4] = {kb, v, dangling, p0 != nullptr};
+    const int key[5] = {kb, v, dangling, p0 != nullptr, use_points(g, kb) ? 1 : 0};
     if (g->s.pr_exec && (memcmp(key, g->s.pr_key, sizeof(key)) || g->s.pr_key_alpha != base.alpha ||
                          g->s.pr_key_ptr != g->s.q[0] || g->s.pr_key_z != g->s.z))
         drop_pr_graph(g);

@@ -95,7 +95,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                     if (!sc.eat('{')) return false;
                     std::string key;
                     CacheEntry e{};
-                    e.cfg = {512, -1, 32, 1, 32, 8};
+                    e.cfg = {512, -1, 32, 1, 32, 8, -1};
                     int fields = 0;
                     do {
                         std::string f;
@@ -112,6 +112,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                         else if (f == "gather_pdl") e.cfg.gather_pdl = (int32_t)v, fields++;
                         else if (f == "col_block") e.cfg.col_block = (int32_t)v, fields++;
                         else if (f == "pull_item") e.cfg.pull_item = (int32_t)v, fields++;
+                        else if (f == "push_points") e.cfg.push_points = (int32_t)v;  // absent in older files: -1
                         else if (f == "push_us") e.push_us = v;
                         else if (f == "pull_us") e.pull_us = v;
                     } while (sc.eat(','));
@@ -161,10 +162,10 @@ int write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
         char buf[512];
         std::snprintf(buf, sizeof buf,
                       "%s\n  {\"key\": \"%s\", \"pull_tile\": %d, \"pull_prefix\": %d, \"prefix_min_len\": %d, "
-                      "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_us\": %.3f, "
-                      "\"pull_us\": %.3f}",
+                      "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_points\": %d, "
+                      "\"push_us\": %.3f, \"pull_us\": %.3f}",
                       first ? "" : ",", json_escape(kv.first).c_str(), c.pull_tile, c.pull_prefix, c.prefix_min_len,
-                      c.gather_pdl, c.col_block, c.pull_item, kv.second.push_us, kv.second.pull_us);
+                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, kv.second.push_us, kv.second.pull_us);
         o << buf;
         first = false;
     }
@@ -317,7 +318,7 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
     auto pull = [&]() { return bvg_spmv_Ax(g, x, y, k, k, st); };
     int kpow = 1;
     while (kpow * 2 <= std::min(k, 32)) kpow *= 2;
-    // push: column block x overlap
+    // push: column block x overlap x gather over event or point columns
     bvg_launch_config best = base;
     double best_push = 1e300;
     if ((rc = time_op(push, st, t, &g->tune.push_us_default))) {
@@ -325,22 +326,24 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
         return rc;
     }
     for (int cb = kpow; cb >= std::max(1, kpow / 8); cb >>= 1) {
-        for (int pdl = 0; pdl <= 1; pdl++) {
-            bvg_launch_config c = base;
-            c.col_block = cb;
-            c.gather_pdl = pdl;
-            double us = 0;
-            if ((rc = bvg_set_config(g, &c)) || (rc = time_op(push, st, t, &us))) {
-                bvg_set_config(g, &base);
-                release();
-                return rc;
+        for (int pdl = 0; pdl <= 1; pdl++)
+            for (int pts = 0; pts <= 1; pts++) {
+                bvg_launch_config c = base;
+                c.col_block = cb;
+                c.gather_pdl = pdl;
+                c.push_points = pts;
+                double us = 0;
+                if ((rc = bvg_set_config(g, &c)) || (rc = time_op(push, st, t, &us))) {
+                    bvg_set_config(g, &base);
+                    release();
+                    return rc;
+                }
+                g->tune.candidates++;
+                if (us < best_push) {
+                    best_push = us;
+                    best = c;
+                }
             }
-            g->tune.candidates++;
-            if (us < best_push) {
-                best_push = us;
-                best = c;
-            }
-        }
     }
     // pull: entries per work item x rows per CTA of the row pass x which
     // intervals stay unexpanded (summed from the prefix), with the chosen column block

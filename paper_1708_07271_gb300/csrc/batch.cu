@@ -6,8 +6,10 @@
 // first drains, through programmatic dependent launch), and the pair is
 // replayed from a CUDA graph. Each CTA finds its graph by binary search over
 // the first-tile offsets in a device table, then runs the same per-tile code
-// as the one-graph product, so a batch result is bit-identical to the
-// one-graph result for the same column block and vector width.
+// as the one-graph product (over the graph's event or point columns, as its
+// launch configuration says for the column block), so a batch result is
+// bit-identical to the one-graph result for the same column block and vector
+// width.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -21,7 +23,7 @@ namespace bvg {
 
 struct BatchEntry {
     const uint32_t* desc;
-    const uint32_t* colp;
+    const uint32_t* colp;  // event columns, or point columns when `points`
     const uint32_t* tent;
     const uint32_t* titem_ptr;
     const uint32_t* titem;
@@ -33,6 +35,7 @@ struct BatchEntry {
     int64_t n;
     int64_t chain_tile0;   // first chain tile of this graph in the grid
     int64_t gather_tile0;  // first gather tile of this graph in the grid
+    int points;            // 1: the gather reads point columns (no carry lists)
 };
 
 // Largest i with tab[i].tile0 <= blk (graphs with no rows are not in the table).
@@ -61,9 +64,13 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const B
                                                       int64_t c0) {
     const BatchEntry e = tab[find_graph<false>(tab, count, blockIdx.x)];
     PrArgs pa{};
-    gather_tile<KB, V, 0>((int64_t)blockIdx.x - e.gather_tile0, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr,
-                          e.carry, e.z, KB,
-                          e.y + c0, ld, e.n, pa);
+    const int64_t blk = (int64_t)blockIdx.x - e.gather_tile0;
+    if (e.points)
+        gather_tile<KB, V, 0, false>(blk, e.colp, e.tent, e.titem_ptr, e.titem, nullptr, nullptr, e.z, KB, e.y + c0, ld,
+                                     e.n, pa);
+    else
+        gather_tile<KB, V, 0, true>(blk, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr, e.carry, e.z, KB, e.y + c0,
+                                    ld, e.n, pa);
 }
 
 }  // namespace bvg
@@ -268,6 +275,12 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
     }
     int rc;
     if ((rc = ensure_tables(b, nb))) return rc;
+    // point columns a graph's configuration asks for (built once, synchronous)
+    for (int bi = 0; bi < nb; bi++)
+        for (int i = 0; i < cnt; i++)
+            if (want_points(b->graphs[i], blocks[bi]) &&
+                (rc = ensure_points(const_cast<bvg_dev_graph*>(b->graphs[i]), stream)))
+                return rc;
     const int zk = blocks[0];  // the widest column block
     if (b->zk < zk) {
         if (b->z) {
@@ -300,10 +313,11 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
             const bvg_dev_graph* g = b->graphs[i];
             BatchEntry& e = h[(size_t)bi * cnt + i];
             e.desc = g->desc;
-            e.colp = g->colp;
-            e.tent = g->tent;
-            e.titem_ptr = g->titem_ptr;
-            e.titem = g->titem;
+            e.points = use_points(g, kb) ? 1 : 0;
+            e.colp = e.points ? g->pcolp : g->colp;
+            e.tent = e.points ? g->pcent : g->tent;
+            e.titem_ptr = e.points ? g->ptitem_ptr : g->titem_ptr;
+            e.titem = e.points ? g->ptitem : g->titem;
             e.carry_ptr = g->carry_ptr;
             e.carry = g->carry;
             e.x = xs[b->slot[i]];

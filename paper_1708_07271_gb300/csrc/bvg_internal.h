@@ -41,6 +41,8 @@ constexpr uint32_t kTagPlus = 0, kTagMinus = 1, kTagIvS = 2, kTagIvL = 3;
 // to the CTA's threads evenly.
 constexpr int kGatherSlots = 3;
 constexpr int kTailItem = 4;
+// Point columns (see build_point_cols): straight-line slots per column.
+constexpr int kPointSlots = 4;
 inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
 
 void set_error(const char* fmt, ...);
@@ -62,6 +64,12 @@ struct PullItems {
 };
 int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int item, int min_len, PullItems& out,
                      bool only_if_worth);
+
+// Point columns built from row-major difference rows (see build_point_cols).
+struct PointCols {
+    std::vector<uint32_t> colp, ent, titem_ptr, titem;
+};
+int build_point_cols(const uint32_t* rowp, const uint32_t* ent, int64_t n, PointCols& out);
 
 }  // namespace bvg
 
@@ -98,6 +106,7 @@ struct LaunchCfg {
     int pull_item = 8;          // pull: entries per work item (4, 8 or 16)
     int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
     int col_block = 32;         // widest column block of a product (power of two <= 32)
+    int push_points = -1;       // x A gather over point columns: -1 for column blocks of at least 4, 0 never, 1 always
 };
 
 struct TuneInfo {
@@ -127,7 +136,7 @@ struct DevScratch {
     // CUDA graph of a chunk of PageRank updates, and what it was built for
     void* pr_exec = nullptr;            // cudaGraphExec_t
     void* cap_stream = nullptr;         // private stream the update graph is captured on
-    int pr_key[4] = {0, 0, 0, 0};       // kb, v, dangling, has p0
+    int pr_key[5] = {0, 0, 0, 0, 0};    // kb, v, dangling, has p0, point columns
     float pr_key_alpha = 0.f;
     const void* pr_key_ptr = nullptr;   // q[0] when captured
     const void* pr_key_z = nullptr;     // z when captured
@@ -178,6 +187,15 @@ struct bvg_dev_graph {
     int64_t part_kcap = 0;
     int pull_built_item = 0, pull_built_minlen = 0, pull_built_auto = -1;  // parameters the items were built with
     int64_t pull_bytes = 0;                          // device bytes of the item arrays
+    // point columns (x A): column-major entries with every interval member
+    // expanded into a +z_k entry, so the gather needs no running interval sum;
+    // tail items past the first kPointSlots entries. Built on first use.
+    uint32_t* pcolp = nullptr;      // n + 1
+    uint32_t* pcent = nullptr;      // kTagPlus / kTagMinus | source row
+    uint32_t* ptitem_ptr = nullptr; // n + 1
+    uint32_t* ptitem = nullptr;     // start in pcent | (count - 1) << 30
+    int64_t npcent = 0, nptitem = 0, pcol_bytes = 0;
+    int pcol_state = 0;             // 0 not built, 1 built, -1 too many entries (the event columns serve)
     std::vector<uint32_t> host_rowp, host_ent;       // the difference rows, to rebuild the items
     int64_t bytes = 0;
     bvg::LaunchCfg cfg;
@@ -186,6 +204,15 @@ struct bvg_dev_graph {
     bvg::DevScratch s;
     bvg::Tracer* tracer = nullptr;
 };
+
+namespace bvg {
+// Point columns of a device graph (api.cu): built and copied on first use
+// (synchronises `stream`); want_points: a kb-wide column block should read
+// them; use_points: it does (they are built).
+int ensure_points(bvg_dev_graph* g, void* stream);
+bool want_points(const bvg_dev_graph* g, int kb);
+bool use_points(const bvg_dev_graph* g, int kb);
+}  // namespace bvg
 
 struct bvg_csr_graph {
     int64_t n = 0, m = 0;

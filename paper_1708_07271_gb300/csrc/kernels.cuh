@@ -466,6 +466,14 @@ __global__ void __launch_bounds__(256) k_chain(const uint32_t* __restrict__ desc
 // (ld.global.ca), never through the read-only non-coherent path, since z
 // changes during the kernel's lifetime.
 // EPI = 0: store y. EPI = 1: PageRank epilogue (see PrArgs).
+// EV = false: the same gather over point columns, where every interval member
+// is its own +z_k entry: no events, no carry list, no block scan; y_j is the
+// sum of column j's entries alone: the first kPointSlots in FP32, then runs
+// of at most kTailItem, each summed in FP32 and joined through an error-free
+// two_sum (the error stays near 3u of the column's magnitudes at any
+// length). It reads more structure (an interval of length L costs L entries,
+// not two) and executes far fewer instructions per right-hand side, which
+// wins once a column block carries several right-hand sides.
 // ---------------------------------------------------------------------------
 template <int KB, int V>
 struct GatherShape {
@@ -587,7 +595,7 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
 
 // One tile of the gather (columns [blk * T, blk * T + T)); shared by the
 // one-graph and the multi-graph kernels.
-template <int KB, int V, int EPI>
+template <int KB, int V, int EPI, bool EV>
 __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restrict__ colp,
                                             const uint32_t* __restrict__ tent,
                                             const uint32_t* __restrict__ titem_ptr,
@@ -596,7 +604,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                                             const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                             float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
     using Sh = GatherShape<KB, V>;
-    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32, S = Sh::S;
+    constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32;
+    constexpr int S = EV ? Sh::S : kPointSlots;
     static_assert(T % kCarryTile == 0, "tile must align with the carry lists");
     static_assert(NW * KB <= NT, "one thread per (warp, right-hand side) forms the warp prefixes");
     __shared__ df run_s[KB];
@@ -616,10 +625,14 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         ip[q] = __ldg(titem_ptr + (c0 + q < end ? c0 + q : end));
     }
     const uint32_t it0 = __ldg(titem_ptr + a), it1 = __ldg(titem_ptr + end);  // the tile's tail items
-    const int64_t ct = a / kCarryTile;
-    const uint32_t cr0 = __ldg(carry_ptr + ct), cr1 = __ldg(carry_ptr + ct + 1);
-    // carry sources of this tile (warp 0; the first 32 now, any further ones later)
-    const uint32_t csrc = (warp == 0 && cr0 + lane32 < cr1) ? __ldg(carry + cr0 + lane32) : 0u;
+    uint32_t cr0 = 0, cr1 = 0, csrc = 0;
+    if constexpr (EV) {
+        const int64_t ct = a / kCarryTile;
+        cr0 = __ldg(carry_ptr + ct);
+        cr1 = __ldg(carry_ptr + ct + 1);
+        // carry sources of this tile (warp 0; the first 32 now, any further ones later)
+        csrc = (warp == 0 && cr0 + lane32 < cr1) ? __ldg(carry + cr0 + lane32) : 0u;
+    }
     uint32_t w[CPT][S];
 #pragma unroll
     for (int q = 0; q < CPT; q++)
@@ -632,7 +645,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 
     // running interval sum at column a: the carry sources' z, one thread per
     // right-hand side for a wide column block, the lanes of warp 0 otherwise
-    if constexpr (KB >= 8) {
+    if constexpr (!EV) {
+    } else if constexpr (KB >= 8) {
         if (threadIdx.x < KB) {
             df acc = df_zero();
             for (uint32_t e = cr0; e < cr1; e++) {
@@ -685,12 +699,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             for (int v = 0; v < V; v++) zv.v[v] = 0.f;
             if (valid) zv = ldv_ca<V>(z + (int64_t)id_of(w[q][t]) * ldz + lane * V);
             const uint32_t tag = w[q][t] >> kIdBits;
-            const bool point = tag < 2;
+            if constexpr (EV) {
+                const bool point = tag < 2;
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
-                P[q][v] += point ? val : 0.f;
-                if (!point) D[q][v] = df_addf(D[q][v], val);
+                for (int v = 0; v < V; v++) {
+                    const float val = (tag & 1) ? -zv.v[v] : zv.v[v];
+                    P[q][v] += point ? val : 0.f;
+                    if (!point) D[q][v] = df_addf(D[q][v], val);
+                }
+            } else {
+                const float sg = (tag & 1) ? -1.f : 1.f;  // sg * z is exact: the same rounding as P -+ z
+#pragma unroll
+                for (int v = 0; v < V; v++) P[q][v] = __fmaf_rn(sg, zv.v[v], P[q][v]);
             }
         }
     }
@@ -701,7 +721,45 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     // items of the round that are its own, in order. With several lanes per
     // group (wide column blocks) each group reads its own columns' items in
     // order instead (no extra barriers, fewer registers).
-    if constexpr (G > 1) {
+    if constexpr (G > 1 && !EV) {
+        // point columns: the entries past the first S in runs of kTailItem,
+        // straight from the column (no item table); a run sums in FP32 (its
+        // error is at most 3u of its magnitudes) and joins the column's sum
+        // through one error-free two_sum, so the column's error stays near 3u
+        // of its magnitudes however long it is
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            for (uint32_t e0 = cp[q] + S; e0 < cp[q + 1]; e0 += kTailItem) {
+                const uint32_t cnt = cp[q + 1] - e0;
+                uint32_t we[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) we[t] = (uint32_t)t < cnt ? __ldg(tent + e0 + t) : 0u;
+                Vec<V> zc[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+#pragma unroll
+                    for (int v = 0; v < V; v++) zc[t].v[v] = 0.f;
+                    if ((uint32_t)t < cnt) zc[t] = ldv_ca<V>(z + (int64_t)id_of(we[t]) * ldz + lane * V);
+                }
+                float sr[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) sr[v] = 0.f;
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+                    const float sg = (we[t] >> kIdBits) & 1 ? -1.f : 1.f;  // sg * z is exact
+#pragma unroll
+                    for (int v = 0; v < V; v++) sr[v] = __fmaf_rn(sg, zc[t].v[v], sr[v]);
+                }
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    float s_, e_;
+                    two_sum(P[q][v], sr[v], s_, e_);
+                    P[q][v] = s_;
+                    Pe[q][v] = __fadd_rn(Pe[q][v], e_);
+                }
+            }
+        }
+    } else if constexpr (G > 1) {
 #pragma unroll
         for (int q = 0; q < CPT; q++) {
             for (uint32_t k = ip[q]; k < ip[q + 1]; k++) {
@@ -724,7 +782,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
                     for (int v = 0; v < V; v++) {
                         const float val = (tag & 1) ? -zc[t].v[v] : zc[t].v[v];
-                        if (tag < 2) {
+                        if (!EV || tag < 2) {
                             float s_, e_;
                             two_sum(P[q][v], val, s_, e_);  // the point sum continues compensated
                             P[q][v] = s_;
@@ -738,7 +796,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         }
     } else {
         constexpr int NGR = NT / G;  // items per round
-        __shared__ df tail_pt[NGR][KB], tail_ev[NGR][KB];
+        __shared__ df tail_pt[NGR][KB], tail_ev[NGR][EV ? KB : 1];
         for (uint32_t r0 = it0; r0 < it1; r0 += NGR) {  // the same trip count in every thread
             const uint32_t i = r0 + (uint32_t)g;
             if (i < it1) {
@@ -760,18 +818,22 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
                 for (int t = 0; t < kTailItem; t++) {
                     const uint32_t tag = we[t] >> kIdBits;
-                    const bool point = tag < 2;
+                    const bool point = !EV || tag < 2;
 #pragma unroll
                     for (int v = 0; v < V; v++) {
                         const float val = (tag & 1) ? -zc[t].v[v] : zc[t].v[v];
-                        pt[v] = df_addf(pt[v], point ? val : 0.f);
-                        ev[v] = df_addf(ev[v], point ? 0.f : val);
+                        if constexpr (EV) {
+                            pt[v] = df_addf(pt[v], point ? val : 0.f);
+                            ev[v] = df_addf(ev[v], point ? 0.f : val);
+                        } else {
+                            pt[v].hi = __fadd_rn(pt[v].hi, val);  // a run of at most kTailItem sums in FP32
+                        }
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     tail_pt[g][lane * V + v] = pt[v];
-                    tail_ev[g][lane * V + v] = ev[v];
+                    if constexpr (EV) tail_ev[g][lane * V + v] = ev[v];
                 }
             }
             __syncthreads();
@@ -787,13 +849,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                         two_sum(P[q][v], tp.hi, s_, e_);  // the point sum continues compensated
                         P[q][v] = s_;
                         Pe[q][v] = __fadd_rn(Pe[q][v], __fadd_rn(e_, tp.lo));
-                        D[q][v] = df_add_rn(D[q][v], tail_ev[k - r0][lane * V + v]);
+                        if constexpr (EV) D[q][v] = df_add_rn(D[q][v], tail_ev[k - r0][lane * V + v]);
                     }
                 }
             }
             __syncthreads();
         }
     }
+    // exclusive prefix of the group totals across the block (event columns only)
+    df run[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) run[v] = df_zero();
+    if constexpr (EV) {
 #pragma unroll
     for (int q = 0; q < CPT; q++)
 #pragma unroll
@@ -826,7 +893,6 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     // before it, in order; for a wide column block formed once per (warp,
     // right-hand side) in shared memory, otherwise by every thread (cheaper
     // than a second barrier when each thread owns few right-hand sides)
-    df run[V];
     if constexpr (KB >= 8) {
         if (threadIdx.x < NW * KB) {
             const int w = threadIdx.x / KB, c = threadIdx.x % KB;
@@ -847,6 +913,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             run[v] = df_add_rn(r, excl[v]);
         }
     }
+    }  // EV
 
     df Ssum[V], R[V], Dg[V];
 #pragma unroll
@@ -857,8 +924,12 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            run[v] = df_add_rn(run[v], D[q][v]);
-            out.v[v] = df_val(df_addf(df_addf(run[v], P[q][v]), Pe[q][v]));
+            if constexpr (EV) {
+                run[v] = df_add_rn(run[v], D[q][v]);
+                out.v[v] = df_val(df_addf(df_addf(run[v], P[q][v]), Pe[q][v]));
+            } else {
+                out.v[v] = __fadd_rn(P[q][v], Pe[q][v]);
+            }
         }
         if (j >= end) continue;
         if constexpr (EPI == 0) {
@@ -893,7 +964,21 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_
                                                 const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                                 float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
-    gather_tile<KB, V, EPI>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, z, ldz, y, ldy, n, pa);
+    gather_tile<KB, V, EPI, true>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, z, ldz, y, ldy, n, pa);
+}
+
+// The gather over point columns (gather_tile with EV = false)
+// (512-thread blocks of the product are capped to 3 resident CTAs' worth of
+// registers: the few spilled bytes cost less than the lost occupancy)
+template <int KB, int V, int EPI>
+__global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT == 512 && EPI == 0 ? 3 : 1) k_gather_pt(const uint32_t* __restrict__ colp,
+                                                                       const uint32_t* __restrict__ ent,
+                                                                       const uint32_t* __restrict__ titem_ptr,
+                                                                       const uint32_t* __restrict__ titem,
+                                                                       const float* z, int64_t ldz,
+                                                                       float* __restrict__ y, int64_t ldy, int64_t n,
+                                                                       PrArgs pa) {
+    gather_tile<KB, V, EPI, false>(blockIdx.x, colp, ent, titem_ptr, titem, nullptr, nullptr, z, ldz, y, ldy, n, pa);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the

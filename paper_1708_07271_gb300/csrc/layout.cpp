@@ -173,6 +173,57 @@ int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int i
     return BVG_OK;
 }
 
+// Point columns: per column j, the source rows k whose difference row holds
+// +1 (a residual id or a member of an interval) or -1 (a dropped id) at j,
+// rows in increasing order, as kTagPlus / kTagMinus words. Unlike the event
+// columns, an interval of length L costs L entries instead of two events,
+// but the gather then needs no running interval sum across columns (no scan,
+// no carry lists): y_j is the sum of column j's own entries. Tail items cut
+// each column's entries past the first kPointSlots into runs of at most
+// kTailItem.
+int build_point_cols(const uint32_t* rowp, const uint32_t* ent, int64_t n, PointCols& out) {
+    try {
+        out = PointCols{};
+        out.colp.assign(n + 1, 0);
+        std::vector<int64_t> cnt(n + 1, 0);
+        for (int64_t q = 0; q < (int64_t)rowp[n]; q++) {
+            const uint32_t w = ent[q], tag = w >> kIdBits, id = w & kIdMask;
+            if (tag == kTagPlus || tag == kTagMinus) {
+                cnt[id + 1]++;
+            } else {
+                const uint32_t len = ent[++q] & kIdMask;
+                for (uint32_t t = 0; t < len; t++) cnt[id + t + 1]++;
+            }
+        }
+        for (int64_t j = 0; j < n; j++) cnt[j + 1] += cnt[j];
+        if (cnt[n] >= ((int64_t)1 << 30)) return fail(BVG_ERR_UNSUPPORTED, "point columns: 2^30 entries or more");
+        for (int64_t j = 0; j <= n; j++) out.colp[j] = (uint32_t)cnt[j];
+        out.ent.assign((size_t)cnt[n], 0);
+        for (int64_t i = 0; i < n; i++)
+            for (uint32_t q = rowp[i]; q < rowp[i + 1]; q++) {
+                const uint32_t w = ent[q], tag = w >> kIdBits, id = w & kIdMask;
+                if (tag == kTagPlus || tag == kTagMinus) {
+                    out.ent[cnt[id]++] = pack(tag, (uint32_t)i);
+                } else {
+                    const uint32_t len = ent[++q] & kIdMask;
+                    for (uint32_t t = 0; t < len; t++) out.ent[cnt[id + t]++] = pack(kTagPlus, (uint32_t)i);
+                }
+            }
+        out.titem_ptr.assign(n + 1, 0);
+        for (int64_t j = 0; j < n; j++) {
+            out.titem_ptr[j] = (uint32_t)out.titem.size();
+            for (int64_t e = (int64_t)out.colp[j] + kPointSlots; e < (int64_t)out.colp[j + 1]; e += kTailItem) {
+                const int64_t c = std::min<int64_t>(kTailItem, (int64_t)out.colp[j + 1] - e);
+                out.titem.push_back((uint32_t)e | (uint32_t)(c - 1) << 30);
+            }
+        }
+        out.titem_ptr[n] = (uint32_t)out.titem.size();
+    } catch (const std::bad_alloc&) {
+        return fail(BVG_ERR_OOM, "point columns: host allocation failed");
+    }
+    return BVG_OK;
+}
+
 int get_layout(const bvg_host_graph* hg, const HostLayout** out) {
     std::lock_guard<std::mutex> lk(hg->layout_mu);
     if (!hg->layout) {
@@ -248,5 +299,32 @@ extern "C" int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_
     std::copy(P.irow.begin(), P.irow.end(), irow);
     std::copy(P.lrow.begin(), P.lrow.end(), lrow);
     std::copy(P.lint.begin(), P.lint.end(), lint);
+    return BVG_OK;
+}
+
+extern "C" int bvg_point_cols_size(const bvg_host_graph* g, int64_t* entries, int64_t* tail_items) {
+    if (!g || !entries || !tail_items) return fail(BVG_ERR_INVALID_ARG, "bvg_point_cols_size: NULL argument");
+    const HostLayout* L = nullptr;
+    int rc = get_layout(g, &L);
+    if (rc) return rc;
+    PointCols P;
+    if ((rc = build_point_cols(L->rowp.data(), L->ent.data(), g->n, P))) return rc;
+    *entries = (int64_t)P.ent.size();
+    *tail_items = (int64_t)P.titem.size();
+    return BVG_OK;
+}
+
+extern "C" int bvg_point_cols_fill(const bvg_host_graph* g, uint32_t* colp, uint32_t* ent, uint32_t* titem_ptr,
+                                   uint32_t* titem) {
+    if (!g || !colp || !ent || !titem_ptr || !titem) return fail(BVG_ERR_INVALID_ARG, "bvg_point_cols_fill: NULL argument");
+    const HostLayout* L = nullptr;
+    int rc = get_layout(g, &L);
+    if (rc) return rc;
+    PointCols P;
+    if ((rc = build_point_cols(L->rowp.data(), L->ent.data(), g->n, P))) return rc;
+    std::copy(P.colp.begin(), P.colp.end(), colp);
+    std::copy(P.ent.begin(), P.ent.end(), ent);
+    std::copy(P.titem_ptr.begin(), P.titem_ptr.end(), titem_ptr);
+    std::copy(P.titem.begin(), P.titem.end(), titem);
     return BVG_OK;
 }

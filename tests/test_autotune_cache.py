@@ -7,7 +7,8 @@ import pytest
 
 import paper_1708_07271_gb300 as bvg
 
-CFG = {"pull_tile": 256, "pull_prefix": 1, "prefix_min_len": 8, "gather_pdl": 0, "col_block": 16, "pull_item": 4}
+CFG = {"pull_tile": 256, "pull_prefix": 1, "prefix_min_len": 8, "gather_pdl": 0, "col_block": 16, "pull_item": 4,
+       "push_points": 1}
 
 
 def test_store_lookup_overwrite(tmp_path):
@@ -22,7 +23,7 @@ def test_store_lookup_overwrite(tmp_path):
     doc = json.loads(path.read_text())  # the file is plain JSON
     assert doc["version"] == 1 and [e["key"] for e in doc["entries"]] == ["dev/sm152/00ff/k1", "dev/sm152/00ff/k8"]
     assert doc["entries"][0]["push_us"] == 40.5 and doc["entries"][0]["pull_us"] == 100.25
-    new = dict(CFG, gather_pdl=1)
+    new = dict(CFG, gather_pdl=1, push_points=0)
     bvg.bvg_autotune_cache_store(path, "dev/sm152/00ff/k1", new)
     assert bvg.bvg_autotune_cache_lookup(path, "dev/sm152/00ff/k1") == new
     assert bvg.bvg_autotune_cache_lookup(path, "dev/sm152/00ff/k8") == other
@@ -45,8 +46,9 @@ def test_file_written_by_hand_is_read(tmp_path):
         {"key": "gpu/sm1/abc/k4", "pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1,
          "col_block": 4, "pull_item": 16, "push_us": 1e2, "pull_us": 2.5e2}]}, indent=2))
     got = bvg.bvg_autotune_cache_lookup(path, "gpu/sm1/abc/k4")
+    # a file without push_points (written before that setting existed) reads as -1, the default
     assert got == {"pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1, "col_block": 4,
-                   "pull_item": 16}
+                   "pull_item": 16, "push_points": -1}
 
 
 def test_bad_arguments(tmp_path):

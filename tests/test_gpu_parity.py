@@ -271,6 +271,22 @@ def test_full_size_products(web862k):
                 oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), "Ax 862k")
 
 
+def test_full_size_products_wide_block(web862k):
+    """n = 862,664 with k = 32 (the point-column gather): every entry of x A
+    and A x^T against the oracle."""
+    g, hg, dg, ref = web862k
+    x = synth.rhs(g.n, 32, synth.seed_for(2, 32))
+    x64 = x.astype(np.float64)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), "xA 862k k=32")
+    bvg.bvg_spmv_Ax(dg, xt, y)
+    check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), "Ax 862k k=32")
+
+
 def test_full_size_pagerank(web862k):
     g, hg, dg, ref = web862k
     p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
@@ -324,3 +340,61 @@ def test_launch_config_variants_same_results():
         bvg.bvg_set_config(dg, pull_tile=100)
     with pytest.raises(bvg.BvgError):
         bvg.bvg_set_config(dg, pull_item=5)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("points", [0, 1])
+def test_push_event_and_point_columns(name, points):
+    """The push gather over the event columns (intervals as start / end events
+    and a running sum) and over the point columns (every interval member its
+    own entry), forced for every column block width: both match the oracle,
+    and dyadic inputs match it bit for bit."""
+    g, hg, dg, ref = graph(name)
+    old = bvg.bvg_get_config(dg)
+    bvg.bvg_set_config(dg, push_points=points)
+    try:
+        for k in (1, 2, 8, 33):
+            x = synth.rhs(g.n, k, synth.seed_for(1, 400 + k))
+            x64 = x.astype(np.float64)
+            xt = torch.from_numpy(x).cuda()
+            y = torch.full_like(xt, float("nan"))
+            bvg.bvg_spmv_xA(dg, xt, y)
+            check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                        oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), f"xA points={points} {name} k={k}")
+        for k in (1, 4, 32):
+            x = synth.dyadic_rhs(g.n, k, synth.seed_for(1, 500 + k))
+            xt = torch.from_numpy(x).cuda()
+            y = torch.empty_like(xt)
+            bvg.bvg_spmv_xA(dg, xt, y)
+            np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_xA(g.row_ptr, g.col, x))
+    finally:
+        bvg.bvg_set_config(dg, **old)
+    info = bvg.bvg_dev_layout(dg)
+    if points:
+        assert info["point_entries"] == bvg.bvg_stats(hg)["nnz_diff"]
+
+
+@pytest.mark.parametrize("points", [0, 1])
+def test_pagerank_event_and_point_columns(points):
+    """PageRank (one vector and eight personalized ones) with the gather forced
+    onto either column layout: both converge to the oracle's vectors."""
+    g, hg, dg, ref = graph("social_20k")
+    old = bvg.bvg_get_config(dg)
+    bvg.bvg_set_config(dg, push_points=points)
+    try:
+        p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
+        assert rc == bvg.BVG_OK and res[0] < 1e-8, (rc, it, res)
+        pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000)
+        assert l1(p.cpu().numpy(), pstar) <= 1e-6
+        k = 8
+        P0 = np.zeros((g.n, k), np.float32)
+        P0[synth.nodes(k, g.n, 77), np.arange(k)] = 1.0
+        p, it, res, rc = bvg.bvg_pagerank(dg, p0=torch.from_numpy(P0).cuda(), tol=1e-8, max_iter=1000)
+        assert rc == bvg.BVG_OK and (res < 1e-8).all(), (rc, it, res)
+        want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, p0=P0.astype(np.float64), tol=1e-13,
+                                     max_iter=2000)
+        got = p.cpu().numpy()
+        for c in range(k):
+            assert l1(got[:, c], want[:, c]) <= 1e-6, c
+    finally:
+        bvg.bvg_set_config(dg, **old)

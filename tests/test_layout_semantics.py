@@ -14,8 +14,9 @@ TAG_SHIFT = 30
 MASK = (1 << 30) - 1
 
 
-def emulate_xA(L, x, tile):
-    n = L["n"]
+def chain_weights(L, x):
+    """z: x pushed down the reference chains (rows in reverse level order),
+    checked against the same weights read from the descendant masks."""
     meta = L["meta"].astype(np.int64)
     off = meta & 7
     depth = meta >> 3
@@ -31,6 +32,12 @@ def emulate_xA(L, x, tile):
         rows = np.nonzero((desc >> t) & 1)[0]
         zd[rows] += x[rows + t + 1]
     np.testing.assert_allclose(zd, z, rtol=1e-12)
+    return z
+
+
+def emulate_xA(L, x, tile):
+    n = L["n"]
+    z = chain_weights(L, x)
     tent = L["tent"].astype(np.int64)
     tag = tent >> TAG_SHIFT
     src = tent & MASK
@@ -185,3 +192,38 @@ def test_tail_items_cover_the_long_columns(name):
         np.testing.assert_array_equal(covered, np.arange(colp[j] + 3, colp[j + 1]))
     short = np.diff(colp) <= 3
     assert np.all(np.diff(tp)[short] == 0)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_point_columns_reproduce_products(name):
+    """The point columns: y_j = sum over column j's entries of +-z_k must give
+    x A; each column lists the nonzeros of column j of A' once, rows in
+    increasing order; the tail items cover each column past its first 4."""
+    g = GRAPHS[name]()
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    L = bvg.bvg_layout_view_get(hg)
+    P = bvg.bvg_point_cols(hg)
+    n = g.n
+    colp = P["colp"].astype(np.int64)
+    ent = P["ent"].astype(np.int64)
+    tag, src = ent >> TAG_SHIFT, ent & MASK
+    assert colp[0] == 0 and colp[-1] == len(ent) and np.all(np.diff(colp) >= 0)
+    assert np.all(tag < 2)
+    assert len(ent) == bvg.bvg_stats(hg)["nnz_diff"]  # dropped + added, interval members one by one
+    col = np.repeat(np.arange(n), np.diff(colp))
+    same = col[1:] == col[:-1]
+    assert np.all(src[1:][same] > src[:-1][same])  # rows increase within a column, no repeats
+    x = synth.rhs(n, 2, 5).astype(np.float64)
+    z = chain_weights(L, x)
+    y = np.zeros_like(z)
+    np.add.at(y, col, np.where(tag == 1, -1.0, 1.0)[:, None] * z[src])
+    np.testing.assert_allclose(y, oracle.csr_xA(g.row_ptr, g.col, x), rtol=1e-9, atol=1e-9)
+    tp = P["titem_ptr"].astype(np.int64)
+    items = P["titem"].astype(np.int64)
+    assert tp[0] == 0 and tp[-1] == len(items)
+    start, cnt = items & MASK, (items >> 30) + 1
+    assert np.all(cnt <= 4)
+    for j in np.nonzero(np.diff(colp) > 4)[0][:2000]:
+        covered = np.concatenate([np.arange(s, s + c) for s, c in zip(start[tp[j]:tp[j + 1]], cnt[tp[j]:tp[j + 1]])])
+        np.testing.assert_array_equal(covered, np.arange(colp[j] + 4, colp[j + 1]))
+    assert np.all(np.diff(tp)[np.diff(colp) <= 4] == 0)
