@@ -915,9 +915,16 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     }
     }  // EV
 
-    df Ssum[V], R[V], Dg[V];
+    // PageRank sums of this thread's CPT columns: a few terms, in FP32 (one
+    // rounding per term, relative to a partial sum of nonnegative terms), then
+    // compensated across the block
+    float Ssum[V], R[V], Dg[V];
+    float dl[V];  // the previous update's dangling mass, per right-hand side of this lane
 #pragma unroll
-    for (int v = 0; v < V; v++) Ssum[v] = R[v] = Dg[v] = df_zero();
+    for (int v = 0; v < V; v++) {
+        Ssum[v] = R[v] = Dg[v] = 0.f;
+        if constexpr (EPI == 1) dl[v] = (float)__ldcg(pa.sc_prev + 1 * KB + lane * V + v);
+    }
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
         const int64_t j = c0 + q;
@@ -943,17 +950,25 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             for (int v = 0; v < V; v++) {
                 const float p0j = pa.p0 ? p0v.v[v] : un;
                 const float gj = pa.dangling_uniform ? un : p0j;
-                const float dl = (float)pa.sc_prev[1 * KB + lane * V + v];
-                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl * gj);
+                const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl[v] * gj);
                 qn.v[v] = qj;
-                Ssum[v] = df_addf(Ssum[v], qj);
-                R[v] = df_addf(R[v], fabsf(__fsub_rn(qj, qp.v[v])));
-                if (io == 0.0f) Dg[v] = df_addf(Dg[v], qj);
+                Ssum[v] = __fadd_rn(Ssum[v], qj);
+                R[v] = __fadd_rn(R[v], fabsf(__fsub_rn(qj, qp.v[v])));
+                if (io == 0.0f) Dg[v] = __fadd_rn(Dg[v], qj);
             }
             stv<V>(pa.q_new + j * pa.ldq + lane * V, qn);
         }
     }
-    if constexpr (EPI == 1) pr_block_reduce<KB, V>(Ssum, R, Dg, pa, false);
+    if constexpr (EPI == 1) {
+        df Sd[V], Rd[V], Dd[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            Sd[v] = {Ssum[v], 0.f};
+            Rd[v] = {R[v], 0.f};
+            Dd[v] = {Dg[v], 0.f};
+        }
+        pr_block_reduce<KB, V>(Sd, Rd, Dd, pa, false);
+    }
 }
 
 template <int KB, int V, int EPI>
@@ -968,10 +983,12 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_
 }
 
 // The gather over point columns (gather_tile with EV = false)
-// (512-thread blocks of the product are capped to 3 resident CTAs' worth of
-// registers: the few spilled bytes cost less than the lost occupancy)
+// (registers capped for 3 resident 512-thread CTAs per SM for the product,
+// 2 for the PageRank update, and 4 for 256-thread CTAs: the few spilled bytes
+// cost less than the lost occupancy)
 template <int KB, int V, int EPI>
-__global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT == 512 && EPI == 0 ? 3 : 1) k_gather_pt(const uint32_t* __restrict__ colp,
+__global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT == 512 ? (EPI == 0 ? 3 : 2) : 4)
+    k_gather_pt(const uint32_t* __restrict__ colp,
                                                                        const uint32_t* __restrict__ ent,
                                                                        const uint32_t* __restrict__ titem_ptr,
                                                                        const uint32_t* __restrict__ titem,
