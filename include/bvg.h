@@ -188,7 +188,9 @@ int bvg_upload(const bvg_host_graph* g, void* stream, bvg_dev_graph** out);
 
 /* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j. The row sums
  * sum_j A'_ij x_j are formed per work item (bvg_pull_items_size), then each
- * row tile adds its rows' partials and resolves the chains in shared memory.
+ * row tile adds its rows' partials and resolves the chains in shared memory
+ * (a row with more than 32 items, a hub of a power-law graph, is summed by
+ * the whole tile's threads).
  * x, y: device n x k, leading dimension ld. Asynchronous. Errors:
  * INVALID_ARG, OOM (first call with a wider column block), CUDA. */
 int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
@@ -353,10 +355,11 @@ int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
  * candidate launch configuration (CUDA events on `stream`, median of 7 after
  * 2 warm-up calls, warm caches): first the push (x A) over the widest column
  * block (the largest power of two <= min(k, 32) and up to three halvings)
- * times gather overlap on/off times event or point columns, then the pull (A x^T) over entries per work
- * item {4, 8, 16} times rows per CTA of the row pass {256, 512} times the
- * length from which intervals stay unexpanded (32; also 16 and "never" when
- * the graph has intervals; rebuilding the items is part of the search).
+ * times gather overlap on/off times event or point columns, then the pull
+ * (A x^T) over entries per work item {4, 8, 16} times rows per CTA of the
+ * row pass {256, 512} times the length from which
+ * intervals stay unexpanded (32; also 16 and "never" when the graph has
+ * intervals; rebuilding the items is part of the search).
  * It applies the fastest choice to g (bvg_get_config shows it). With
  * cache_path != NULL it first looks the choice up in that JSON file under
  * the key "<device name>/sm<count>/<layout fingerprint>/k<k>" and, after a

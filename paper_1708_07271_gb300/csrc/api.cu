@@ -85,8 +85,13 @@ static int pick_v(int kb, int64_t ld, int64_t col, std::initializer_list<const v
 constexpr int kThreads = 256;
 
 // Rows per CTA: the halo of kHalo rows is recomputed by two CTAs, so tiles
-// stay large; shared memory grows with kb.
-static int pull_tile(int kb, const LaunchCfg& c) { return kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2); }
+// stay large; shared memory grows with kb, and the tile is halved until the
+// row sums (tile + kHalo rows x kb compensated values) fit in 200 KB.
+static int pull_tile(int kb, const LaunchCfg& c) {
+    int t = kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2);
+    while (t > 64 && (size_t)(t + kHalo) * kb * sizeof(df) > 200 * 1024) t /= 2;
+    return t;
+}
 // Columns per CTA of the gather kernel (k_gather's GatherShape).
 static int gather_tile(int kb, int v, const LaunchCfg&) {
     const int G = kb / v, NT = G >= 8 ? 512 : 256, NG = NT / G, CPT = std::max(2, 128 / NG);
@@ -616,7 +621,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
 
 extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     if (!g || !in) return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: NULL argument");
-    if (in->pull_tile < 64 || in->pull_tile > 2048 || (in->pull_tile & (in->pull_tile - 1)) ||
+    if (in->pull_tile < 64 || in->pull_tile > kPullMaxTile || (in->pull_tile & (in->pull_tile - 1)) ||
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
         in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)) ||
         (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16) || in->push_points < -1 ||

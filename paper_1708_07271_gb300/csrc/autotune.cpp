@@ -165,7 +165,8 @@ int write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
                       "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_points\": %d, "
                       "\"push_us\": %.3f, \"pull_us\": %.3f}",
                       first ? "" : ",", json_escape(kv.first).c_str(), c.pull_tile, c.pull_prefix, c.prefix_min_len,
-                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, kv.second.push_us, kv.second.pull_us);
+                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, kv.second.push_us,
+                      kv.second.pull_us);
         o << buf;
         first = false;
     }

@@ -232,20 +232,25 @@ __global__ void __launch_bounds__(256) k_pull_items(const uint32_t* __restrict__
     for (int v = 0; v < V; v++) part[k * KB + lane * V + v] = make_float2(acc[v].hi, acc[v].lo);
 }
 
+// Adds to acc the items' partial sums k0, k0 + step, ... < k1.
 template <int KB, int V>
-__device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k0, uint32_t k1, const float2* part,
-                                             const uint32_t* __restrict__ lrow, const uint32_t* __restrict__ lint,
-                                             const float* __restrict__ x, int64_t ldx, int lane,
-                                             const PrefixArgs& pf) {
-#pragma unroll
-    for (int v = 0; v < V; v++) acc[v] = df_zero();
-    for (uint32_t k = k0; k < k1; k++) {
+__device__ __forceinline__ void pull_row_entries(df (&acc)[V], uint32_t k0, uint32_t k1, uint32_t step,
+                                                 const float2* part, int lane) {
+    for (uint32_t k = k0; k < k1; k += step) {
 #pragma unroll
         for (int v = 0; v < V; v++) {
             const float2 p = __ldcg(part + (int64_t)k * KB + lane * V + v);
             acc[v] = df_add(acc[v], {p.x, p.y});
         }
     }
+}
+
+// Adds to acc the kept (long) intervals of row i: from the prefix of x, or
+// member by member.
+template <int KB, int V>
+__device__ __forceinline__ void pull_row_intervals(df (&acc)[V], int64_t i, const uint32_t* __restrict__ lrow,
+                                                   const uint32_t* __restrict__ lint, const float* __restrict__ x,
+                                                   int64_t ldx, int lane, const PrefixArgs& pf) {
     const uint32_t l0 = __ldg(lrow + i), l1 = __ldg(lrow + i + 1);
     for (uint32_t q = l0; q < l1; q++) {  // kept (long) intervals
         const uint32_t s0 = __ldg(lint + 2 * q), len = __ldg(lint + 2 * q + 1);
@@ -259,6 +264,18 @@ __device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k
             }
         }
     }
+}
+
+// Row sum of row i: its items' partial sums [k0, k1), then its kept intervals.
+template <int KB, int V>
+__device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k0, uint32_t k1, const float2* part,
+                                             const uint32_t* __restrict__ lrow, const uint32_t* __restrict__ lint,
+                                             const float* __restrict__ x, int64_t ldx, int lane,
+                                             const PrefixArgs& pf) {
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = df_zero();
+    pull_row_entries<KB, V>(acc, k0, k1, 1, part, lane);
+    pull_row_intervals<KB, V>(acc, i, lrow, lint, x, ldx, lane, pf);
 }
 
 // The reference chain of tile row r (indices into the tile's c): r, r's
@@ -275,6 +292,13 @@ __device__ __forceinline__ int pull_chain_of(const uint8_t* __restrict__ meta, i
     }
     return len;
 }
+
+// Rows of the row pass with more items than this are summed by the whole CTA
+// after the per-group loop, so a hub row (power-law out-degree) does not
+// leave one lane group walking it alone.
+constexpr uint32_t kPullLongItems = 32;
+// Largest row tile of the row pass (rows per CTA, plus the halo).
+constexpr int kPullMaxTile = 2048;
 
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ irow,
@@ -311,25 +335,79 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
         clen[j] = ro < cnt ? pull_chain_of(meta, lo, ro, idx[j]) : 0;
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the items' partial sums are ready
+    constexpr uint32_t kLong = kPullLongItems;
+    bool met_long = false;  // this thread's group left a long row for the whole CTA
 
+    auto row_range = [&](int r, uint32_t& k0, uint32_t& k1) {
+        k0 = __ldg(irow + lo + r);
+        k1 = __ldg(irow + lo + r + 1);
+    };
+    auto group_row = [&](int r, uint32_t k0, uint32_t k1) {
+        if (k1 - k0 > kLong) {
+            met_long = true;
+            return;
+        }
+        df acc[V];
+        pull_row_sum<KB, V>(acc, lo + r, k0, k1, part, lrow, lint, x, ldx, lane, pf);
+#pragma unroll
+        for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
+    };
 #pragma unroll
     for (int j = 0; j < PF; j++) {
         const int r = g + j * NG;
-        if (r < cnt) {
-            df acc[V];
-            pull_row_sum<KB, V>(acc, lo + r, kr[j][0], kr[j][1], part, lrow, lint, x, ldx, lane, pf);
-#pragma unroll
-            for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
-        }
+        if (r < cnt) group_row(r, kr[j][0], kr[j][1]);
     }
     for (int r = g + PF * NG; r < cnt; r += NG) {
-        df acc[V];
-        pull_row_sum<KB, V>(acc, lo + r, __ldg(irow + lo + r), __ldg(irow + lo + r + 1), part, lrow, lint, x, ldx,
-                            lane, pf);
-#pragma unroll
-        for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
+        uint32_t k0, k1;
+        row_range(r, k0, k1);
+        group_row(r, k0, k1);
     }
-    __syncthreads();
+    // the long rows (rare: hubs of a power-law graph), each by the whole CTA:
+    // every group sums a strided share, the groups of a warp combine by a
+    // fixed shuffle tree, then one thread per right-hand side adds the warps
+    // in order (deterministic)
+    if (__syncthreads_or(met_long)) {
+        constexpr int kMaskWords = (kPullMaxTile + kHalo + 31) / 32;
+        __shared__ uint32_t long_mask[kMaskWords];
+        const int mwords = (cnt + 31) / 32;
+        for (int t = threadIdx.x; t < mwords; t += blockDim.x) long_mask[t] = 0u;
+        __syncthreads();
+        for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+            uint32_t k0, k1;
+            row_range(r, k0, k1);
+            if (k1 - k0 > kLong) atomicOr(&long_mask[r >> 5], 1u << (r & 31));
+        }
+        __syncthreads();
+        constexpr int NWmax = 256 / 32;
+        __shared__ df long_part[NWmax][KB];
+        const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+        for (int wd = 0; wd < mwords; wd++) {
+            for (uint32_t bits = long_mask[wd]; bits; bits &= bits - 1) {
+                const int r = wd * 32 + __ffs(bits) - 1;
+                uint32_t k0, k1;
+                row_range(r, k0, k1);
+                df acc[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[v] = df_zero();
+                pull_row_entries<KB, V>(acc, k0 + (uint32_t)g, k1, (uint32_t)NG, part, lane);
+#pragma unroll
+                for (int v = 0; v < V; v++)
+                    for (int o = G; o < 32; o <<= 1) acc[v] = df_add(acc[v], df_shfl_xor(acc[v], o));
+                if (lane32 < G) {
+#pragma unroll
+                    for (int v = 0; v < V; v++) long_part[warp][lane32 * V + v] = acc[v];
+                }
+                __syncthreads();
+                if (threadIdx.x < KB) {
+                    df t[1] = {df_zero()};
+                    for (int w = 0; w < NW; w++) t[0] = df_add(t[0], long_part[w][threadIdx.x]);
+                    pull_row_intervals<KB, 1>(t, lo + r, lrow, lint, x, ldx, threadIdx.x, pf);
+                    c[(int64_t)r * KB + threadIdx.x] = t[0];
+                }
+                __syncthreads();
+            }
+        }
+    }
 
     auto emit = [&](int r, const int (&ix)[kMaxChain + 1], int len) {
         Vec<V> out;

@@ -177,7 +177,7 @@ def web_862k(seed: int | None = None) -> GraphSpec:
 def web_7m4(seed: int | None = None) -> GraphSpec:
     """n = 7.4 M, ~194 M edges (batched personalized PageRank)."""
     return GraphSpec(n=7_400_000, seed=seed_for(3) if seed is None else seed, p_copy=0.8, fidelity=0.985,
-                     extra_mean=0.35, fresh_mean=21.5, q_run=0.5, gap_mean=24.0)
+                     extra_mean=0.35, fresh_mean=23.0, q_run=0.5, gap_mean=24.0)
 
 
 def web_small(n: int, seed: int) -> GraphSpec:
@@ -196,14 +196,14 @@ def web_18m5(seed: int | None = None) -> GraphSpec:
 def web_22m7(seed: int | None = None) -> GraphSpec:
     """n = 22.7 M, ~640 M edges."""
     return GraphSpec(n=22_700_000, seed=seed_for(5) if seed is None else seed, p_copy=0.8, fidelity=0.985,
-                     extra_mean=0.4, fresh_mean=23.0, q_run=0.5, gap_mean=24.0)
+                     extra_mean=0.4, fresh_mean=24.5, q_run=0.5, gap_mean=24.0)
 
 
 def social_5m4(seed: int | None = None) -> GraphSpec:
     """n = 5.4 M, ~79 M edges: power-law out-degree (alpha 2.1), row copy
     probability 0.3, uniform random ids (weak locality)."""
     return GraphSpec(n=5_400_000, seed=seed_for(5, 1) if seed is None else seed, p_copy=0.3, fidelity=0.9,
-                     extra_mean=1.0, powerlaw=True, alpha=2.1, dmin=4, dmax=50_000, q_run=0.0,
+                     extra_mean=2.0, powerlaw=True, alpha=2.1, dmin=2, dmax=200_000, q_run=0.0,
                      gap_mean=24.0, random_ids=True)
 
 

@@ -46,7 +46,7 @@ def test_file_written_by_hand_is_read(tmp_path):
         {"key": "gpu/sm1/abc/k4", "pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1,
          "col_block": 4, "pull_item": 16, "push_us": 1e2, "pull_us": 2.5e2}]}, indent=2))
     got = bvg.bvg_autotune_cache_lookup(path, "gpu/sm1/abc/k4")
-    # a file without push_points (written before that setting existed) reads as -1, the default
+    # a file without push_points (written before that setting existed) reads it as -1, the default
     assert got == {"pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1, "col_block": 4,
                    "pull_item": 16, "push_points": -1}
 

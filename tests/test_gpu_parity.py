@@ -398,3 +398,45 @@ def test_pagerank_event_and_point_columns(points):
             assert l1(got[:, c], want[:, c]) <= 1e-6, c
     finally:
         bvg.bvg_set_config(dg, **old)
+
+
+def hub_graph():
+    """A web-like graph with hub rows: a few rows hold every other id (1,500
+    single entries, no runs: about a hundred work items or more), some of
+    them adjacent so that they reference one another and fall in the halo of
+    the next row tile."""
+    g = synth.copying_model(synth.GraphSpec(n=3000, seed=9, p_copy=0.7, fidelity=0.97, extra_mean=0.8,
+                                            fresh_mean=6.0, q_run=0.25, gap_mean=30.0))
+    even, odd = {0, 700, 2048, 2999}, {1, 63, 65, 1500, 2047}
+    rows = [np.arange(i % 2, g.n, 2, dtype=np.int32) if i in even | odd else g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
+            for i in range(g.n)]
+    rp = np.zeros(g.n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    return synth.Graph(g.n, rp, np.concatenate(rows).astype(np.int32))
+
+
+@pytest.mark.parametrize("tile,item", [(64, 4), (512, 8), (2048, 16)])
+def test_pull_hub_rows(tile, item):
+    """Rows with more than 32 work items are summed by the whole row tile:
+    results match the oracle for every column block, dyadic inputs bit for
+    bit, and repeated products are identical."""
+    g = hub_graph()
+    hg, dg, ref = encode(g)
+    bvg.bvg_set_config(dg, pull_tile=tile, pull_item=item)
+    for k in (1, 2, 8, 33):
+        x = synth.rhs(g.n, k, synth.seed_for(1, 800 + k))
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.full_like(xt, float("nan"))
+        bvg.bvg_spmv_Ax(dg, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                    oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), f"Ax hubs tile={tile} item={item} k={k}")
+        y2 = torch.empty_like(xt)
+        bvg.bvg_spmv_Ax(dg, xt, y2)
+        assert torch.equal(y, y2)
+    for k in (1, 32):
+        x = synth.dyadic_rhs(g.n, k, synth.seed_for(1, 900 + k))
+        xt = torch.from_numpy(x).cuda()
+        y = torch.empty_like(xt)
+        bvg.bvg_spmv_Ax(dg, xt, y)
+        np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_Ax(g.row_ptr, g.col, x))
