@@ -540,7 +540,9 @@ def run_bv(args):
         e2e_s.append(time.perf_counter() - t0)
     e2e_total = max_over_ranks(float(np.sum(e2e_s)))
     e2e = {"value": world * g.m * k * args.steps / e2e_total / 1e9, "unit": "Gedges/s",
-           "h2d_bytes_per_step": int(hx.numel() * 4), "d2h_bytes_per_step": int(hy.numel() * 4)}
+           "h2d_bytes_per_step": int(hx.numel() * 4), "d2h_bytes_per_step": int(hy.numel() * 4),
+           "path": "bvg_spmv_xA_host on page-locked buffers (copy to device scratch, product, copy back, "
+                   "synchronise), host wall clock per call"}
 
     # ---- PageRank to L1 < 1e-8, uniform start, single vector
     pr_runs = []

@@ -227,9 +227,10 @@ int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int
  * INVALID_ARG, UNSUPPORTED, CUDA. */
 int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
-/* Same as bvg_spmv_xA with x and y in HOST memory (pinned or pageable):
- * copies x to device scratch, runs the product, copies y back, and
- * synchronises `stream` before returning. ld == k. */
+/* Same as bvg_spmv_xA with x and y in HOST memory (page-locked, which copies
+ * fastest, or pageable), n x k, ld == k: copies x to device scratch, runs the
+ * product, copies y back, and synchronises `stream` before returning.
+ * Errors: INVALID_ARG (also when x and y alias), OOM, CUDA. */
 int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host, int32_t k, void* stream);
 
 /* PageRank by power iteration, Eq. (1): p_t = alpha p0 + (1 - alpha) p_{t-1} M,

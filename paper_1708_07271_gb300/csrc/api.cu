@@ -686,14 +686,9 @@ extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int
     return BVG_OK;
 }
 
-extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
-    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
-    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: NULL graph");
-    if (k < 1 || ld < k) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: need k >= 1 and ld >= k");
-    if (g->n == 0) return BVG_OK;
+// x A on vectors the device can address (checked by the callers).
+static int spmv_xA(bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
     int rc;
-    if ((rc = check_vec(g, x, "x")) || (rc = check_vec(g, y, "y"))) return rc;
-    if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: x and y must not alias");
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
@@ -708,6 +703,17 @@ extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, in
     return BVG_OK;
 }
 
+extern "C" int bvg_spmv_xA(const bvg_dev_graph* gc, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
+    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: NULL graph");
+    if (k < 1 || ld < k) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: need k >= 1 and ld >= k");
+    if (g->n == 0) return BVG_OK;
+    int rc;
+    if ((rc = check_vec(g, x, "x")) || (rc = check_vec(g, y, "y"))) return rc;
+    if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA: x and y must not alias");
+    return spmv_xA(g, x, y, k, ld, stream);
+}
+
 extern "C" int bvg_spmv_xA_host(const bvg_dev_graph* gc, const float* x_host, float* y_host, int32_t k,
                                 void* stream) {
     bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
@@ -715,6 +721,11 @@ extern "C" int bvg_spmv_xA_host(const bvg_dev_graph* gc, const float* x_host, fl
     if (k < 1) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_host: k < 1");
     if (g->n == 0) return BVG_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    if (x_host == y_host) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_host: x and y must not alias");
+    // staged through device scratch: one copy each way. (Reading and writing
+    // page-locked buffers in place through their device mapping instead was
+    // no faster: the chain and gather kernels then ran 2.3x slower on the
+    // CPU-GPU link than on HBM.)
     const int64_t need = g->n * (int64_t)k;
     if (g->s.stage_cap < need) {
         if (g->s.hx) cudaFree(g->s.hx);
@@ -728,7 +739,7 @@ extern "C" int bvg_spmv_xA_host(const bvg_dev_graph* gc, const float* x_host, fl
         g->s.stage_cap = need;
     }
     BVG_CUDA_TRY(cudaMemcpyAsync(g->s.hx, x_host, need * sizeof(float), cudaMemcpyHostToDevice, st));
-    int rc = bvg_spmv_xA(g, g->s.hx, g->s.hy, k, k, stream);
+    int rc = spmv_xA(g, g->s.hx, g->s.hy, k, k, stream);
     if (rc) return rc;
     BVG_CUDA_TRY(cudaMemcpyAsync(y_host, g->s.hy, need * sizeof(float), cudaMemcpyDeviceToHost, st));
     BVG_CUDA_TRY(cudaStreamSynchronize(st));

@@ -126,14 +126,23 @@ def test_csr_baseline_matches_oracle():
         np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64), rtol=1e-5)
 
 
-def test_host_buffer_product():
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("k", [1, 3, 32])
+def test_host_buffer_product(pinned, k):
+    """x A from host buffers, page-locked or pageable (both staged through
+    device scratch): the device product bit for bit."""
     g, hg, dg, ref = graph("ragged_1037")
-    x = synth.rhs(g.n, 3, 17)
-    y = np.zeros_like(x)
-    bvg.bvg_spmv_xA_host(dg, x, y)
+    x = synth.rhs(g.n, k, 17)
+    xt, yt = torch.from_numpy(x), torch.zeros(g.n, k)
+    if pinned:
+        xt, yt = xt.pin_memory(), yt.pin_memory()
+    bvg.bvg_spmv_xA_host(dg, xt, yt)
     x64 = x.astype(np.float64)
-    check_close(y, oracle.csr_xA(g.row_ptr, g.col, x64), oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True),
-                "host xA")
+    check_close(yt.numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), f"host xA pinned={pinned} k={k}")
+    yd = torch.empty(g.n, k, device="cuda")
+    bvg.bvg_spmv_xA(dg, xt.cuda(), yd)
+    assert torch.equal(yd.cpu(), yt)
 
 
 def test_empty_graph():
