@@ -12,8 +12,8 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
   pull         n (meta) + 4(n+1) (item offsets per row) + 4(items+1) (item starts)
                + 4*pull_entries (expanded entries) + 4(n+1) + 8*pull_intervals
                (kept intervals) + 4kn (x) + 4kn (y); the items' partial sums
-               (8 bytes per item and right-hand side, written then read back)
-               are scratch that stays in L2 and are not counted
+               (4 bytes per item and right-hand side, written then read back)
+               are scratch that stays in L2 at k = 1 and are not counted
   push_gather_pt  (point columns) 4(n+1) (column offsets) + 4*point_entries
                [+ 4(n+1) + 4*point_tail_items (tail items) when k <= 4, where one lane
                group owns a column and the tail items are shared out] + 4kn (z) + 4kn (y)

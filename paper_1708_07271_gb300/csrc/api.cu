@@ -179,7 +179,7 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
         }
         pf = PrefixArgs{lhi, llo, bhi, blo, Sh::PB, 0};
     }
-    float2* part = reinterpret_cast<float2*>(g->part);
+    float* part = g->part;
     if (g->nitems > 0) {
         constexpr int G = KB / V;
         const int64_t grid = (g->nitems + 256 / G - 1) / (256 / G);
@@ -205,7 +205,7 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = g->nitems > 0 ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_pull_rows<KB, V>, (const uint8_t*)g->meta, (const uint32_t*)g->irow, (const float2*)part,
+    cudaLaunchKernelEx(&cfg, k_pull_rows<KB, V>, (const uint8_t*)g->meta, (const uint32_t*)g->irow, (const float*)part,
                        (const uint32_t*)g->lrow, (const uint32_t*)g->lint, x, ldx, y, ldy, g->n, tile, pf);
 }
 
@@ -326,7 +326,7 @@ static int ensure_part(bvg_dev_graph* g, int kb) {
     if (g->part) cudaFree(g->part);
     g->part = nullptr;
     g->part_kcap = 0;
-    int rc = dev_alloc((void**)&g->part, (size_t)std::max<int64_t>(g->nitems, 1) * kb * 2 * sizeof(float), nullptr);
+    int rc = dev_alloc((void**)&g->part, (size_t)std::max<int64_t>(g->nitems, 1) * kb * sizeof(float), nullptr);
     if (rc) return rc;
     g->part_kcap = kb;
     return BVG_OK;

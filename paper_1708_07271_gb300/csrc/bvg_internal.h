@@ -183,7 +183,7 @@ struct bvg_dev_graph {
     uint32_t* lrow = nullptr;       // n + 1: kept intervals of row i are [lrow[i], lrow[i + 1])
     uint32_t* lint = nullptr;       // 2 per kept interval: start, length
     int64_t npent = 0, nitems = 0, nlint = 0;
-    float* part = nullptr;          // per item partial sums, compensated (hi, lo) x part_kcap
+    float* part = nullptr;          // per item partial sums (compensated, rounded once) x part_kcap
     int64_t part_kcap = 0;
     int pull_built_item = 0, pull_built_minlen = 0, pull_built_auto = -1;  // parameters the items were built with
     int64_t pull_bytes = 0;                          // device bytes of the item arrays

@@ -175,7 +175,9 @@ struct PrefixArgs {
 // items, not the rows, are the unit of parallel work):
 //   k_pull_items: one item per group of G = KB/V lanes, W straight-line
 //     predicated slots (the same instructions for every item), its
-//     compensated (hi, lo) partial sum written out;
+//     compensated partial sum rounded once to FP32 and written out (an error
+//     of at most u of the item's magnitudes; 4 bytes per item and right-hand
+//     side instead of 8);
 //   k_pull_rows: a CTA owns rows [a, a + tile); it sums the partials of its
 //     rows and of the kHalo rows before them (plus their kept intervals,
 //     from the prefix of x or member by member) into shared memory, then
@@ -204,7 +206,7 @@ template <int KB, int V, int W>
 __global__ void __launch_bounds__(256) k_pull_items(const uint32_t* __restrict__ pent,
                                                     const uint32_t* __restrict__ istart, int64_t nitems,
                                                     const float* __restrict__ x, int64_t ldx,
-                                                    float2* __restrict__ part) {
+                                                    float* __restrict__ part) {
     constexpr int G = KB / V;
     asm volatile("griddepcontrol.launch_dependents;");
     const int64_t k = (int64_t)blockIdx.x * (256 / G) + threadIdx.x / G;
@@ -228,20 +230,20 @@ __global__ void __launch_bounds__(256) k_pull_items(const uint32_t* __restrict__
     for (int t = 0; t < W; t++)
 #pragma unroll
         for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], (w[t] >> 31) ? -xv[t].v[v] : xv[t].v[v]);
+    Vec<V> pv;
 #pragma unroll
-    for (int v = 0; v < V; v++) part[k * KB + lane * V + v] = make_float2(acc[v].hi, acc[v].lo);
+    for (int v = 0; v < V; v++) pv.v[v] = df_val(acc[v]);  // rounded once
+    stv<V>(part + k * KB + lane * V, pv);
 }
 
 // Adds to acc the items' partial sums k0, k0 + step, ... < k1.
 template <int KB, int V>
 __device__ __forceinline__ void pull_row_entries(df (&acc)[V], uint32_t k0, uint32_t k1, uint32_t step,
-                                                 const float2* part, int lane) {
+                                                 const float* part, int lane) {
     for (uint32_t k = k0; k < k1; k += step) {
+        const Vec<V> p = ldv_cg<V>(part + (int64_t)k * KB + lane * V);
 #pragma unroll
-        for (int v = 0; v < V; v++) {
-            const float2 p = __ldcg(part + (int64_t)k * KB + lane * V + v);
-            acc[v] = df_add(acc[v], {p.x, p.y});
-        }
+        for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], p.v[v]);
     }
 }
 
@@ -268,7 +270,7 @@ __device__ __forceinline__ void pull_row_intervals(df (&acc)[V], int64_t i, cons
 
 // Row sum of row i: its items' partial sums [k0, k1), then its kept intervals.
 template <int KB, int V>
-__device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k0, uint32_t k1, const float2* part,
+__device__ __forceinline__ void pull_row_sum(df (&acc)[V], int64_t i, uint32_t k0, uint32_t k1, const float* part,
                                              const uint32_t* __restrict__ lrow, const uint32_t* __restrict__ lint,
                                              const float* __restrict__ x, int64_t ldx, int lane,
                                              const PrefixArgs& pf) {
@@ -302,7 +304,7 @@ constexpr int kPullMaxTile = 2048;
 
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ meta, const uint32_t* __restrict__ irow,
-                                                   const float2* part, const uint32_t* __restrict__ lrow,
+                                                   const float* part, const uint32_t* __restrict__ lrow,
                                                    const uint32_t* __restrict__ lint, const float* __restrict__ x,
                                                    int64_t ldx, float* __restrict__ y, int64_t ldy, int64_t n,
                                                    int tile, PrefixArgs pf) {
