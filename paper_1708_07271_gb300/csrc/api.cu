@@ -266,7 +266,9 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
 template <int KB, int V>
 static void launch_pr_init(const bvg_dev_graph* g, const float* p_init, int64_t ldi, const PrArgs& pa,
                            cudaStream_t st) {
-    const int tile = gather_tile(KB, V, g->cfg);
+    // wide column blocks: 8 gather tiles per CTA (a CTA of one 128-column
+    // tile spends more on its share of the reduction than on its columns)
+    const int tile = gather_tile(KB, V, g->cfg) * (KB >= 8 ? 8 : 1);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pr_init", st);
     k_pr_init<KB, V><<<(unsigned)grid, kThreads, 0, st>>>(p_init, ldi, g->n, tile, pa);

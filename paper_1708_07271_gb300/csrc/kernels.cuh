@@ -589,7 +589,10 @@ __device__ __forceinline__ double pr_warp_sum(const double* __restrict__ base, i
     return t;
 }
 
-template <int KB, int V>
+// F32WARP: the threads' values are plain FP32 partials (lo = 0) and the
+// warp's shuffle tree adds them in FP32 (a few roundings relative to the
+// warp's sum of nonnegative terms); the warps are then combined compensated.
+template <int KB, int V, bool F32WARP = false>
 __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArgs& pa, bool init) {
     constexpr int G = KB / V;
     __shared__ df sh_part[32][3][KB];
@@ -598,9 +601,15 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
 #pragma unroll
     for (int v = 0; v < V; v++) {
         for (int o = 16; o >= G; o >>= 1) {
-            S[v] = df_add(S[v], df_shfl_xor(S[v], o));
-            R[v] = df_add(R[v], df_shfl_xor(R[v], o));
-            Dg[v] = df_add(Dg[v], df_shfl_xor(Dg[v], o));
+            if constexpr (F32WARP) {
+                S[v].hi = __fadd_rn(S[v].hi, __shfl_xor_sync(0xffffffffu, S[v].hi, o));
+                R[v].hi = __fadd_rn(R[v].hi, __shfl_xor_sync(0xffffffffu, R[v].hi, o));
+                Dg[v].hi = __fadd_rn(Dg[v].hi, __shfl_xor_sync(0xffffffffu, Dg[v].hi, o));
+            } else {
+                S[v] = df_add(S[v], df_shfl_xor(S[v], o));
+                R[v] = df_add(R[v], df_shfl_xor(R[v], o));
+                Dg[v] = df_add(Dg[v], df_shfl_xor(Dg[v], o));
+            }
         }
     }
     if (lane32 < G) {
@@ -718,6 +727,28 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     for (int q = 0; q < CPT; q++)
 #pragma unroll
         for (int t = 0; t < S; t++) w[q][t] = cp[q] + t < cp[q + 1] ? __ldg(tent + cp[q] + t) : 0u;
+    // PageRank epilogue inputs: the previous iterate was written by the
+    // previous update, which completed before this update's chain kernel
+    // started, and the teleport vectors and 1/outdeg never change; so they
+    // are fetched before the wait too (into registers for one right-hand
+    // side, into L2 otherwise, where registers are scarce)
+    constexpr bool kPfRegs = EPI == 1 && KB == 1;
+    float io_pf[CPT], qp_pf[CPT], p0_pf[CPT];
+    if constexpr (EPI == 1) {
+#pragma unroll
+        for (int q = 0; q < CPT; q++) {
+            const int64_t j = c0 + q;
+            if (j >= end) continue;
+            if constexpr (kPfRegs) {
+                io_pf[q] = __ldg(pa.inv_outdeg + j);
+                qp_pf[q] = __ldg(pa.q_prev + j * pa.ldq);
+                p0_pf[q] = pa.p0 ? __ldg(pa.p0 + j * pa.ldp0) : 0.f;
+            } else {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pa.q_prev + j * pa.ldq + lane * V));
+                if (pa.p0) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa.p0 + j * pa.ldp0 + lane * V));
+            }
+        }
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");  // z (and the PageRank state) are ready
     if constexpr (EPI == 1) {
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
@@ -995,9 +1026,9 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     }
     }  // EV
 
-    // PageRank sums of this thread's CPT columns: a few terms, in FP32 (one
-    // rounding per term, relative to a partial sum of nonnegative terms), then
-    // compensated across the block
+    // PageRank sums of this thread's CPT columns and then of its warp: plain
+    // FP32 adds (a few roundings, relative to partial sums of nonnegative
+    // terms), then compensated across the warps of the block
     float Ssum[V], R[V], Dg[V];
     float dl[V];  // the previous update's dangling mass, per right-hand side of this lane
 #pragma unroll
@@ -1022,10 +1053,18 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         if constexpr (EPI == 0) {
             stv<V>(y + j * ldy + lane * V, out);
         } else {
-            const float io = __ldg(pa.inv_outdeg + j);
             const float un = 1.0f / (float)n;
-            Vec<V> qp = ldv<V>(pa.q_prev + j * pa.ldq + lane * V), qn, p0v;
-            if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0 + lane * V);
+            float io;
+            Vec<V> qp, qn, p0v;
+            if constexpr (kPfRegs) {
+                io = io_pf[q];
+                qp.v[0] = qp_pf[q];
+                p0v.v[0] = p0_pf[q];
+            } else {
+                io = __ldg(pa.inv_outdeg + j);
+                qp = ldv<V>(pa.q_prev + j * pa.ldq + lane * V);
+                if (pa.p0) p0v = ldv<V>(pa.p0 + j * pa.ldp0 + lane * V);
+            }
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float p0j = pa.p0 ? p0v.v[v] : un;
@@ -1047,7 +1086,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             Rd[v] = {R[v], 0.f};
             Dd[v] = {Dg[v], 0.f};
         }
-        pr_block_reduce<KB, V>(Sd, Rd, Dd, pa, false);
+        pr_block_reduce<KB, V, true>(Sd, Rd, Dd, pa, false);
     }
 }
 
