@@ -142,18 +142,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel: str, source_digest: str):
+def profile_traffic(kernel: str, source_digest: str, k: int = 1):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (line 'traffic_bytes_per_launch: <B> source: <digest>')."""
+    the current kernel source, for this kernel family and k (line
+    'traffic_bytes_per_launch: <B> source: <digest> kernel: <family> k: <k>')."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
+    pat = re.compile(r"\s*traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source:\s*([0-9a-f]+)"
+                     r"\s+kernel:\s*(\S+)\s+k:\s*(\d+)")
     for fn in sorted(os.listdir(d)):
-        if not fn.startswith(kernel) or not fn.endswith((".md", ".txt")):
+        if not fn.endswith((".md", ".txt")):
             continue
         for line in open(os.path.join(d, fn)):
-            m = re.match(r"\s*traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source:\s*([0-9a-f]+)", line)
-            if m and m.group(2) == source_digest:
+            m = pat.match(line)
+            if m and m.group(2) == source_digest and m.group(3) == kernel and int(m.group(4)) == k:
                 return float(m.group(1))
     return None
 
@@ -326,7 +329,8 @@ def krhs_leg(args, bvg, synth, torch, flush, timed, dg, g, k=32):
             b = bytemodel.KERNELS[name](L, k)
             sec = ms / cnt * 1e-3
             kernels[name] = {"avg_us": sec * 1e6, "algorithmic_bytes": b, "achieved_gbs": b / sec / 1e9,
-                             "frac": b / sec / 1e9 / peak}
+                             "frac": b / sec / 1e9 / peak,
+                             "traffic": None if args.config3 else profile_traffic(name, kernel_source_digest(), k)}
     seeds = synth.nodes(k, g.n, synth.seed_for(3, 2))
     p0 = torch.zeros((g.n, k), dtype=torch.float32, device="cuda")
     p0[torch.from_numpy(seeds.astype(np.int64)).cuda(), torch.arange(k, device="cuda")] = 1.0
@@ -507,7 +511,7 @@ def run_bv(args):
     dom_bytes = bytemodel.KERNELS[dom_name](L, k)
     dom_avg_s = dom_ms / dom_launches * 1e-3
     achieved = dom_bytes / dom_avg_s / 1e9
-    traffic = profile_traffic(dom_name, kernel_source_digest())
+    traffic = profile_traffic(dom_name, kernel_source_digest(), k)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom_name, "algorithmic_bytes": dom_bytes,
                 "avg_launch_us": dom_avg_s * 1e6, "peak_kind": f"{peak_kind} HBM copy",
