@@ -237,7 +237,7 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
         TraceScope ts(g, "push_gather_pt", st);
         launch_pdl(g->cfg.gather_pdl, k_gather_pt<KB, V, 0>, grid, GatherShape<KB, V>::NT, st,
                    (const uint32_t*)g->pcolp, (const uint32_t*)g->pcent, (const uint32_t*)g->ptitem_ptr,
-                   (const uint32_t*)g->ptitem, z, ldz, y, ldy, g->n, pa);
+                   (const uint32_t*)g->ptitem, (const uint8_t*)g->plong, z, ldz, y, ldy, g->n, pa);
         return;
     }
     TraceScope ts(g, "push_gather", st);
@@ -254,7 +254,8 @@ static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz
         TraceScope ts(g, "pr_gather_pt", st);
         launch_pdl(g->cfg.gather_pdl, k_gather_pt<KB, V, 1>, grid, GatherShape<KB, V>::NT, st,
                    (const uint32_t*)g->pcolp, (const uint32_t*)g->pcent, (const uint32_t*)g->ptitem_ptr,
-                   (const uint32_t*)g->ptitem, z, ldz, (float*)nullptr, (int64_t)0, g->n, pa);
+                   (const uint32_t*)g->ptitem, (const uint8_t*)g->plong, z, ldz, (float*)nullptr, (int64_t)0, g->n,
+                   pa);
         return;
     }
     TraceScope ts(g, "pr_gather", st);
@@ -386,7 +387,8 @@ int ensure_points(bvg_dev_graph* g, void* stream) {
     if (rc) return rc;
     int64_t bytes = 0;
     if ((rc = upload_vec(&g->pcolp, P.colp, st, &bytes)) || (rc = upload_vec(&g->pcent, P.ent, st, &bytes)) ||
-        (rc = upload_vec(&g->ptitem_ptr, P.titem_ptr, st, &bytes)) || (rc = upload_vec(&g->ptitem, P.titem, st, &bytes)))
+        (rc = upload_vec(&g->ptitem_ptr, P.titem_ptr, st, &bytes)) || (rc = upload_vec(&g->ptitem, P.titem, st, &bytes)) ||
+        (rc = upload_vec(&g->plong, P.long_chunk, st, &bytes)))
         return rc;
     BVG_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
     g->npcent = (int64_t)P.ent.size();
@@ -541,7 +543,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)

@@ -36,6 +36,7 @@ struct BatchEntry {
     int64_t chain_tile0;   // first chain tile of this graph in the grid
     int64_t gather_tile0;  // first gather tile of this graph in the grid
     int points;            // 1: the gather reads point columns (no carry lists)
+    const uint8_t* long_chunk;  // point columns: 128-column chunks holding a long column
 };
 
 // Largest i with tab[i].tile0 <= blk (graphs with no rows are not in the table).
@@ -66,11 +67,11 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const B
     PrArgs pa{};
     const int64_t blk = (int64_t)blockIdx.x - e.gather_tile0;
     if (e.points)
-        gather_tile<KB, V, 0, false>(blk, e.colp, e.tent, e.titem_ptr, e.titem, nullptr, nullptr, e.z, KB, e.y + c0, ld,
-                                     e.n, pa);
+        gather_tile<KB, V, 0, false>(blk, e.colp, e.tent, e.titem_ptr, e.titem, nullptr, nullptr, e.long_chunk, e.z, KB,
+                                     e.y + c0, ld, e.n, pa);
     else
-        gather_tile<KB, V, 0, true>(blk, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr, e.carry, e.z, KB, e.y + c0,
-                                    ld, e.n, pa);
+        gather_tile<KB, V, 0, true>(blk, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr, e.carry, nullptr, e.z, KB,
+                                    e.y + c0, ld, e.n, pa);
 }
 
 }  // namespace bvg
@@ -318,6 +319,7 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
             e.tent = e.points ? g->pcent : g->tent;
             e.titem_ptr = e.points ? g->ptitem_ptr : g->titem_ptr;
             e.titem = e.points ? g->ptitem : g->titem;
+            e.long_chunk = e.points ? g->plong : nullptr;
             e.carry_ptr = g->carry_ptr;
             e.carry = g->carry;
             e.x = xs[b->slot[i]];

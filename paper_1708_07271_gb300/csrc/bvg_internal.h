@@ -43,6 +43,8 @@ constexpr int kGatherSlots = 3;
 constexpr int kTailItem = 4;
 // Point columns (see build_point_cols): straight-line slots per column.
 constexpr int kPointSlots = 4;
+// Point columns with more tail entries than this are summed by a whole CTA.
+constexpr uint32_t kLongColumn = 256;
 inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
 
 void set_error(const char* fmt, ...);
@@ -68,6 +70,7 @@ int build_pull_items(const uint32_t* rowp, const uint32_t* ent, int64_t n, int i
 // Point columns built from row-major difference rows (see build_point_cols).
 struct PointCols {
     std::vector<uint32_t> colp, ent, titem_ptr, titem;
+    std::vector<uint8_t> long_chunk;  // per kCarryTile columns: 1 if one has more than kPointSlots + kLongColumn entries
 };
 int build_point_cols(const uint32_t* rowp, const uint32_t* ent, int64_t n, PointCols& out);
 
@@ -194,6 +197,7 @@ struct bvg_dev_graph {
     uint32_t* pcent = nullptr;      // kTagPlus / kTagMinus | source row
     uint32_t* ptitem_ptr = nullptr; // n + 1
     uint32_t* ptitem = nullptr;     // start in pcent | (count - 1) << 30
+    uint8_t* plong = nullptr;       // per kCarryTile columns: holds a column longer than kPointSlots + kLongColumn
     int64_t npcent = 0, nptitem = 0, pcol_bytes = 0;
     int pcol_state = 0;             // 0 not built, 1 built, -1 too many entries (the event columns serve)
     std::vector<uint32_t> host_rowp, host_ent;       // the difference rows, to rebuild the items

@@ -682,6 +682,32 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
     }
 }
 
+// The FP32 sum sr of one run of point entries [e0, min(e0 + kTailItem, e1))
+// (signs applied by an exact FMA with +-1).
+template <int V>
+__device__ __forceinline__ void point_run(float (&sr)[V], uint32_t e0, uint32_t e1, const uint32_t* __restrict__ ent,
+                                          const float* z, int64_t ldz, int lane) {
+    const uint32_t cnt = e1 - e0;
+    uint32_t we[kTailItem];
+#pragma unroll
+    for (int t = 0; t < kTailItem; t++) we[t] = (uint32_t)t < cnt ? __ldg(ent + e0 + t) : 0u;
+    Vec<V> zc[kTailItem];
+#pragma unroll
+    for (int t = 0; t < kTailItem; t++) {
+#pragma unroll
+        for (int v = 0; v < V; v++) zc[t].v[v] = 0.f;
+        if ((uint32_t)t < cnt) zc[t] = ldv_ca<V>(z + (int64_t)id_of(we[t]) * ldz + lane * V);
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) sr[v] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kTailItem; t++) {
+        const float sg = (we[t] >> kIdBits) & 1 ? -1.f : 1.f;  // sg * z is exact
+#pragma unroll
+        for (int v = 0; v < V; v++) sr[v] = __fmaf_rn(sg, zc[t].v[v], sr[v]);
+    }
+}
+
 // One tile of the gather (columns [blk * T, blk * T + T)); shared by the
 // one-graph and the multi-graph kernels.
 template <int KB, int V, int EPI, bool EV>
@@ -690,7 +716,8 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                                             const uint32_t* __restrict__ titem_ptr,
                                             const uint32_t* __restrict__ titem,
                                             const uint32_t* __restrict__ carry_ptr,
-                                            const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
+                                            const uint32_t* __restrict__ carry,
+                                            const uint8_t* __restrict__ long_chunk, const float* z, int64_t ldz,
                                             float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32;
@@ -714,6 +741,16 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         ip[q] = __ldg(titem_ptr + (c0 + q < end ? c0 + q : end));
     }
     const uint32_t it0 = __ldg(titem_ptr + a), it1 = __ldg(titem_ptr + end);  // the tile's tail items
+    // point columns, lane groups of several lanes: a column with more than
+    // kLongColumn tail entries (a hub of a graph with power-law in-degree) is
+    // summed by the whole CTA; the layout flags the 128-column chunks that
+    // hold one, so other tiles pay nothing for it
+    bool tile_long = false;
+    if constexpr (!EV && G > 1) {
+#pragma unroll
+        for (int c = 0; c < T / kCarryTile; c++)
+            if (a + (int64_t)c * kCarryTile < n) tile_long |= __ldg(long_chunk + a / kCarryTile + c) != 0;
+    }
     uint32_t cr0 = 0, cr1 = 0, csrc = 0;
     if constexpr (EV) {
         const int64_t ct = a / kCarryTile;
@@ -840,33 +877,82 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
         // of its magnitudes however long it is
 #pragma unroll
         for (int q = 0; q < CPT; q++) {
+            if (cp[q + 1] > cp[q] + S + kLongColumn) continue;  // left for the whole CTA below
             for (uint32_t e0 = cp[q] + S; e0 < cp[q + 1]; e0 += kTailItem) {
-                const uint32_t cnt = cp[q + 1] - e0;
-                uint32_t we[kTailItem];
-#pragma unroll
-                for (int t = 0; t < kTailItem; t++) we[t] = (uint32_t)t < cnt ? __ldg(tent + e0 + t) : 0u;
-                Vec<V> zc[kTailItem];
-#pragma unroll
-                for (int t = 0; t < kTailItem; t++) {
-#pragma unroll
-                    for (int v = 0; v < V; v++) zc[t].v[v] = 0.f;
-                    if ((uint32_t)t < cnt) zc[t] = ldv_ca<V>(z + (int64_t)id_of(we[t]) * ldz + lane * V);
-                }
                 float sr[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) sr[v] = 0.f;
-#pragma unroll
-                for (int t = 0; t < kTailItem; t++) {
-                    const float sg = (we[t] >> kIdBits) & 1 ? -1.f : 1.f;  // sg * z is exact
-#pragma unroll
-                    for (int v = 0; v < V; v++) sr[v] = __fmaf_rn(sg, zc[t].v[v], sr[v]);
-                }
+                point_run<V>(sr, e0, cp[q + 1], tent, z, ldz, lane);
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     float s_, e_;
                     two_sum(P[q][v], sr[v], s_, e_);
                     P[q][v] = s_;
                     Pe[q][v] = __fadd_rn(Pe[q][v], e_);
+                }
+            }
+        }
+        // long columns, each by the whole CTA: every group sums a strided
+        // share of the entries, the groups of a warp combine by a fixed
+        // shuffle tree and one thread per right-hand side adds the warps in
+        // order (deterministic); the owning group adds the result to its column
+        if (tile_long) {  // the same in every thread of the CTA
+            constexpr int NWl = NT / 32;
+            __shared__ uint32_t long_mask[(T + 31) / 32];
+            __shared__ df long_part[NWl][KB];
+            __shared__ df long_res[KB];
+            for (int t = threadIdx.x; t < (T + 31) / 32; t += NT) long_mask[t] = 0u;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < CPT; q++)
+                if (lane == 0 && cp[q + 1] > cp[q] + S + kLongColumn) {
+                    const int cc = g * CPT + q;
+                    atomicOr(&long_mask[cc >> 5], 1u << (cc & 31));
+                }
+            __syncthreads();
+            for (int wd = 0; wd < (T + 31) / 32; wd++) {
+                for (uint32_t bits = long_mask[wd]; bits; bits &= bits - 1) {
+                    const int cc = wd * 32 + __ffs(bits) - 1;
+                    const uint32_t eb = __ldg(colp + a + cc) + S, ee = __ldg(colp + a + cc + 1);
+                    df acc[V];
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[v] = df_zero();
+                    // one entry per group and step (few registers: this path
+                    // must not raise the register need of the common one)
+                    for (uint32_t e = eb + (uint32_t)g; e < ee; e += (uint32_t)(NT / G)) {
+                        const uint32_t we = __ldg(tent + e);
+                        const Vec<V> zv = ldv_ca<V>(z + (int64_t)id_of(we) * ldz + lane * V);
+                        const float sg = (we >> kIdBits) & 1 ? -1.f : 1.f;
+#pragma unroll
+                        for (int v = 0; v < V; v++) acc[v] = df_addf(acc[v], sg * zv.v[v]);
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; v++)
+                        for (int o = G; o < 32; o <<= 1) acc[v] = df_add(acc[v], df_shfl_xor(acc[v], o));
+                    if (lane32 < G) {
+#pragma unroll
+                        for (int v = 0; v < V; v++) long_part[warp][lane32 * V + v] = acc[v];
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < KB) {
+                        df t = df_zero();
+                        for (int w = 0; w < NWl; w++) t = df_add(t, long_part[w][threadIdx.x]);
+                        long_res[threadIdx.x] = t;
+                    }
+                    __syncthreads();
+                    // every thread, predicated (a runtime column index here
+                    // would move P and Pe to local memory): two_sum of P with
+                    // 0 leaves P and Pe unchanged
+#pragma unroll
+                    for (int q = 0; q < CPT; q++) {
+                        const bool mine = g * CPT + q == cc;
+#pragma unroll
+                        for (int v = 0; v < V; v++) {
+                            const df r = long_res[lane * V + v];
+                            float s_, e_;
+                            two_sum(P[q][v], mine ? r.hi : 0.f, s_, e_);
+                            P[q][v] = s_;
+                            Pe[q][v] = __fadd_rn(Pe[q][v], mine ? __fadd_rn(e_, r.lo) : e_);
+                        }
+                    }
                 }
             }
         }
@@ -1098,7 +1184,8 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_
                                                 const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                                 float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
-    gather_tile<KB, V, EPI, true>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, z, ldz, y, ldy, n, pa);
+    gather_tile<KB, V, EPI, true>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, nullptr, z, ldz, y, ldy,
+                                  n, pa);
 }
 
 // The gather over point columns (gather_tile with EV = false)
@@ -1111,10 +1198,12 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT
                                                                        const uint32_t* __restrict__ ent,
                                                                        const uint32_t* __restrict__ titem_ptr,
                                                                        const uint32_t* __restrict__ titem,
+                                                                       const uint8_t* __restrict__ long_chunk,
                                                                        const float* z, int64_t ldz,
                                                                        float* __restrict__ y, int64_t ldy, int64_t n,
                                                                        PrArgs pa) {
-    gather_tile<KB, V, EPI, false>(blockIdx.x, colp, ent, titem_ptr, titem, nullptr, nullptr, z, ldz, y, ldy, n, pa);
+    gather_tile<KB, V, EPI, false>(blockIdx.x, colp, ent, titem_ptr, titem, nullptr, nullptr, long_chunk, z, ldz, y,
+                                   ldy, n, pa);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the

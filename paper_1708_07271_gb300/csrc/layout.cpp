@@ -218,6 +218,9 @@ int build_point_cols(const uint32_t* rowp, const uint32_t* ent, int64_t n, Point
             }
         }
         out.titem_ptr[n] = (uint32_t)out.titem.size();
+        out.long_chunk.assign((size_t)((n + kCarryTile - 1) / kCarryTile), 0);
+        for (int64_t j = 0; j < n; j++)
+            if ((int64_t)out.colp[j + 1] - out.colp[j] > (int64_t)kPointSlots + kLongColumn) out.long_chunk[j / kCarryTile] = 1;
     } catch (const std::bad_alloc&) {
         return fail(BVG_ERR_OOM, "point columns: host allocation failed");
     }

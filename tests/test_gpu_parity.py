@@ -449,3 +449,62 @@ def test_pull_hub_rows(tile, item):
         y = torch.empty_like(xt)
         bvg.bvg_spmv_Ax(dg, xt, y)
         np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_Ax(g.row_ptr, g.col, x))
+
+
+def hub_column_graph():
+    """A web-like graph with two hub columns: every row links to node 5 with
+    probability 1/2 and to node 2500 with probability 3/10, independently, so
+    the reference copies cannot absorb them: columns 5 and 2500 of A' hold
+    about 1,300 and 1,000 entries."""
+    g = synth.copying_model(synth.GraphSpec(n=3000, seed=11, p_copy=0.7, fidelity=0.97, extra_mean=0.8,
+                                            fresh_mean=6.0, q_run=0.25, gap_mean=30.0))
+    u = synth.uniform(2 * g.n, synth.seed_for(1, 77)).reshape(2, g.n)
+    rows = []
+    for i in range(g.n):
+        r = set(g.col[g.row_ptr[i]:g.row_ptr[i + 1]].tolist())
+        if u[0, i] < 0.5:
+            r.add(5)
+        if u[1, i] < 0.3:
+            r.add(2500)
+        rows.append(np.array(sorted(r), np.int32))
+    rp = np.zeros(g.n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    return synth.Graph(g.n, rp, np.concatenate(rows))
+
+
+@pytest.mark.parametrize("points", [-1, 1])
+def test_push_hub_columns(points):
+    """Columns with more than 256 tail entries are summed by the whole CTA
+    (wide column blocks over point columns): x A matches the oracle for every
+    column block, dyadic inputs bit for bit, repeated products are identical,
+    and 8 personalized PageRank vectors converge to the oracle's."""
+    g = hub_column_graph()
+    hg, dg, ref = encode(g)
+    cnt = np.diff(bvg.bvg_point_cols(hg)["colp"].astype(np.int64))
+    assert cnt[5] > 4 + 256 and cnt[2500] > 4 + 256
+    bvg.bvg_set_config(dg, push_points=points)
+    for k in (1, 2, 8, 16, 32, 33):
+        x = synth.rhs(g.n, k, synth.seed_for(1, 1000 + k))
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.full_like(xt, float("nan"))
+        bvg.bvg_spmv_xA(dg, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                    oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), f"xA hub columns points={points} k={k}")
+        y2 = torch.empty_like(xt)
+        bvg.bvg_spmv_xA(dg, xt, y2)
+        assert torch.equal(y, y2)
+    for k in (8, 32):
+        x = synth.dyadic_rhs(g.n, k, synth.seed_for(1, 1100 + k))
+        xt = torch.from_numpy(x).cuda()
+        y = torch.empty_like(xt)
+        bvg.bvg_spmv_xA(dg, xt, y)
+        np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), oracle.csr_xA(g.row_ptr, g.col, x))
+    k = 8
+    P0 = np.zeros((g.n, k), np.float32)
+    P0[synth.nodes(k, g.n, 78), np.arange(k)] = 1.0
+    p, it, res, rc = bvg.bvg_pagerank(dg, p0=torch.from_numpy(P0).cuda(), tol=1e-8, max_iter=1000)
+    assert rc == bvg.BVG_OK and (res < 1e-8).all(), (rc, it, res)
+    want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, p0=P0.astype(np.float64), tol=1e-13, max_iter=2000)
+    for c in range(k):
+        assert l1(p.cpu().numpy()[:, c], want[:, c]) <= 1e-6, c
