@@ -1101,13 +1101,19 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
 #pragma unroll
         for (int v = 0; v < V; v++) run[v] = df_add_rn(wpre_s[warp][lane * V + v], excl[v]);
     } else {
+        // the earlier warps' totals by a fixed shuffle tree: group gi of this
+        // warp holds warp gi's total (when gi < warp), three levels add the
+        // eight groups, and group 0's sum is taken by every group
+        static_assert(NW == 8 && 32 / G >= NW, "eight warps, at least eight lane groups per warp");
+        const int gi = lane32 / G;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            df r = run_s[lane * V + v];
+            df t = gi < warp ? wtot_s[gi][lane * V + v] : df_zero();
 #pragma unroll
-            for (int w2 = 0; w2 < NW; w2++)
-                if (w2 < warp) r = df_add_rn(r, wtot_s[w2][lane * V + v]);
-            run[v] = df_add_rn(r, excl[v]);
+            for (int o = G; o < NW * G; o <<= 1) t = df_add_rn(t, df_shfl_xor(t, o));
+            t.hi = __shfl_sync(0xffffffffu, t.hi, lane);
+            t.lo = __shfl_sync(0xffffffffu, t.lo, lane);
+            run[v] = df_add_rn(df_add_rn(run_s[lane * V + v], t), excl[v]);
         }
     }
     }  // EV
