@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--config5", action="store_true",
                     help="run the BV-vs-CSR crossover on the social graph n = 5.4 M and the web graph n = 22.7 M "
                          "(k = 8)")
+    ap.add_argument("--config4", action="store_true",
+                    help="train the warm-start network on 200 generated graphs (n log-uniform in [1e5, 1e6]) and "
+                         "evaluate it on the web-like graph n = 18.5 M")
     return ap.parse_args()
 
 
@@ -344,12 +347,25 @@ def krhs_leg(args, bvg, synth, torch, flush, timed, dg, g, k=32):
         runs.append((time.perf_counter() - t0, it, float(np.max(res)), rc))
     runs.sort()
     s_, it, res, rc = runs[len(runs) // 2]
+    # the same personalized solves one vector at a time (the first two seeds)
+    singles = []
+    for c in range(2):
+        p1 = p0[:, c:c + 1].contiguous()
+        o1 = torch.empty_like(p1)
+        bvg.bvg_pagerank(dg, p0=p1, tol=1e-8, max_iter=1000, out=o1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it1, _, _ = bvg.bvg_pagerank(dg, p0=p1, tol=1e-8, max_iter=1000, out=o1)
+        singles.append((time.perf_counter() - t0, it1))
+    per_vector = float(np.mean([t for t, _ in singles]))
     gd = lambda ms: g.m * k * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
     return {"k": k, "graph": workload_name(g), "xA_gedges_s": gd(push), "xA_ms_per_step": float(np.mean(push)),
             "Ax_gedges_s": gd(pull), "Ax_ms_per_step": float(np.mean(pull)),
             "push_roofline": {"peak_gbs": peak, "peak_kind": f"{peak_kind} HBM copy", "kernels": kernels},
             "ppr": {"vectors": k, "seconds": s_, "iterations": it, "max_l1_resid": res, "status": rc,
-                    "teleport": "one-hot seed nodes"}}
+                    "teleport": "one-hot seed nodes", "one_vector_seconds": per_vector,
+                    "one_vector_iterations": [i for _, i in singles],
+                    "speedup_vs_one_at_a_time": k * per_vector / s_}}
 
 
 def batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard):
@@ -388,12 +404,16 @@ def batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard):
             "launches_per_step": 2, "split": f"graphs split over {world} rank(s), longest first"}
 
 
-def warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it):
+def warmstart_leg(args, bvg, synth, torch, dg, g, pr_s, pr_it):
     """The learned warm start on the bench graph: the network is trained on
     PageRank vectors that bvg_pagerank computes on eight generated graphs
     (n log-uniform in [1e5, 3e5]), then PageRank on the bench graph starts
-    from its prediction. Time includes the features and the prediction."""
-    sizes = synth.multi_graph_sizes(count=8, lo=1e5, hi=3e5, seed=synth.seed_for(4, 7))
+    from its prediction. Time includes the features and the prediction.
+    With --config4: 200 training graphs, n log-uniform in [1e5, 1e6], and the
+    evaluation on the web-like graph n = 18.5 M (its uniform-start solve
+    timed here too)."""
+    count, hi = (200, 1e6) if args.config4 else (8, 3e5)
+    sizes = synth.multi_graph_sizes(count=count, lo=1e5, hi=hi, seed=synth.seed_for(4, 7))
     train, pstars = [], []
     for i, n in enumerate(sizes):
         gt = synth.copying_model(synth.web_small(int(n), synth.seed_for(4, 100 + i)))
@@ -406,6 +426,20 @@ def warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it):
     t0 = time.perf_counter()
     loss = bvg.bvg_warmstart_train(net, train, pstars, epochs=10, lr=3e-3, batch=16384)
     train_s = time.perf_counter() - t0
+    del train
+    if args.config4:
+        g = synth.copying_model(synth.web_18m5())
+        dg = bvg.bvg_upload(bvg.bvg_encode(g.row_ptr, g.col))
+        pu = torch.empty(g.n, device="cuda")
+        bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000, out=pu)
+        uruns = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, uit, _, _ = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000, out=pu)
+            uruns.append((time.perf_counter() - t0, uit))
+        uruns.sort()
+        pr_s, pr_it = uruns[1]
     p = torch.empty(g.n, device="cuda")
     p_init = torch.empty(g.n, device="cuda")
     bvg.bvg_warmstart_predict(net, dg, out=p_init)
@@ -419,8 +453,8 @@ def warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it):
         runs.append((time.perf_counter() - t0, it, float(res[0]), rc))
     runs.sort()
     s, it, res, rc = runs[len(runs) // 2]
-    return {"seconds": s, "iterations": it, "l1_resid": res, "status": rc, "uniform_seconds": pr_s,
-            "uniform_iterations": pr_it, "train_seconds": train_s, "train_loss": loss,
+    return {"graph": workload_name(g), "seconds": s, "iterations": it, "l1_resid": res, "status": rc,
+            "uniform_seconds": pr_s, "uniform_iterations": pr_it, "train_seconds": train_s, "train_loss": loss,
             "train_graphs": len(sizes), "train_nodes": int(sum(int(v) for v in sizes))}
 
 
@@ -563,7 +597,7 @@ def run_bv(args):
     variants = None if args.no_variants else variants_leg(args, bvg, synth, torch, timed, dg, g, cg)
     krhs = None if args.no_krhs else krhs_leg(args, bvg, synth, torch, flush, timed, dg, g)
     batch = None if args.no_batch else batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard)
-    warm = None if args.no_warmstart else warmstart_leg(bvg, synth, torch, dg, g, pr_s, pr_it)
+    warm = None if args.no_warmstart else warmstart_leg(args, bvg, synth, torch, dg, g, pr_s, pr_it)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -190,7 +190,7 @@ def web_small(n: int, seed: int) -> GraphSpec:
 def web_18m5(seed: int | None = None) -> GraphSpec:
     """n = 18.5 M, ~298 M edges (warm-start evaluation)."""
     return GraphSpec(n=18_500_000, seed=seed_for(4) if seed is None else seed, p_copy=0.8, fidelity=0.985,
-                     extra_mean=0.3, fresh_mean=12.5, q_run=0.5, gap_mean=24.0)
+                     extra_mean=0.3, fresh_mean=10.1, q_run=0.5, gap_mean=24.0)
 
 
 def web_22m7(seed: int | None = None) -> GraphSpec:
