@@ -181,9 +181,13 @@ int bvg_point_cols_fill(const bvg_host_graph* g, uint32_t* colp, uint32_t* ent, 
 /* Builds the device layout of `g` (row-major difference rows for A x^T, the
  * same entries grouped by column for x A, per-row reference offsets and
  * chain depths, 1/outdeg) and copies it to the current device on `stream`.
- * Also allocates the scratch the products use, so no later product call
- * allocates. The host graph may be freed after this returns. *out is owned
- * by the caller (bvg_free_dev). Errors: INVALID_ARG, OOM, CUDA. */
+ * Also allocates the scratch of one-column products. The first product with
+ * a wider column block grows that scratch, and the first x A with a column
+ * block of 4 or more (under the default launch configuration) builds the
+ * point columns (bvg_point_cols_size) and synchronises its stream; a caller
+ * that must not allocate later makes one such call first, or uses
+ * bvg_spmv_xA_noalloc. The host graph may be freed after this returns. *out
+ * is owned by the caller (bvg_free_dev). Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_upload(const bvg_host_graph* g, void* stream, bvg_dev_graph** out);
 
 /* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j. The row sums
