@@ -105,6 +105,8 @@ def library_path() -> str:
 def load(build_if_needed: bool = True):
     """Loads libbvg.so (building it first if asked and out of date)."""
     global _lib
+    if _lib is not None:  # every call goes through here: no lock once loaded
+        return _lib
     with _lock:
         if _lib is not None:
             return _lib
