@@ -1050,7 +1050,9 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
                     }
                 }
             }
-            __syncthreads();
+            // the next round overwrites the item sums; after the last round
+            // nothing does (the same condition in every thread)
+            if (r0 + NGR < it1) __syncthreads();
         }
     }
     // exclusive prefix of the group totals across the block (event columns only)
