@@ -227,3 +227,43 @@ def test_point_columns_reproduce_products(name):
         covered = np.concatenate([np.arange(s, s + c) for s, c in zip(start[tp[j]:tp[j + 1]], cnt[tp[j]:tp[j + 1]])])
         np.testing.assert_array_equal(covered, np.arange(colp[j] + 4, colp[j + 1]))
     assert np.all(np.diff(tp)[np.diff(colp) <= 4] == 0)
+
+
+def _csr(rows, n):
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.asarray(r, np.int32) for r in rows]) if rp[-1] else np.zeros(0, np.int32)
+    return rp, col
+
+
+@pytest.mark.parametrize("case", ["no_edges", "one_row", "identical_rows", "full_interval"])
+def test_point_columns_edge_cases(case):
+    """Point columns of degenerate graphs: no edges, a single row, rows that
+    are all copies of their reference (A' nearly empty), and a row that is one
+    interval over every id (every member listed once)."""
+    n = {"no_edges": 40, "one_row": 1, "identical_rows": 300, "full_interval": 200}[case]
+    if case == "no_edges":
+        rows = [[] for _ in range(n)]
+    elif case == "one_row":
+        rows = [[0]]
+    elif case == "identical_rows":
+        rows = [[3, 17, 18, 19, 20, 21, 250] for _ in range(n)]
+    else:
+        rows = [list(range(n)) if i == 5 else [i] for i in range(n)]
+    rp, col = _csr(rows, n)
+    hg = bvg.bvg_encode(rp, col)
+    P = bvg.bvg_point_cols(hg)
+    L = bvg.bvg_layout_view_get(hg)
+    colp = P["colp"].astype(np.int64)
+    assert len(colp) == n + 1 and colp[0] == 0 and colp[-1] == len(P["ent"])
+    assert len(P["ent"]) == bvg.bvg_stats(hg)["nnz_diff"]
+    x = synth.rhs(n, 3, 9).astype(np.float64)
+    z = chain_weights(L, x)
+    ent = P["ent"].astype(np.int64)
+    y = np.zeros_like(z)
+    np.add.at(y, np.repeat(np.arange(n), np.diff(colp)), np.where(ent >> TAG_SHIFT == 1, -1.0, 1.0)[:, None]
+              * z[ent & MASK])
+    np.testing.assert_allclose(y, oracle.csr_xA(rp, col, x), rtol=1e-12, atol=1e-12)
+    if case == "identical_rows":  # only the rows without a reference carry entries, all 7 of theirs
+        ref, _ = bvg.bvg_get_refs(hg)
+        assert len(P["ent"]) == 7 * int(np.sum(ref < 0))
