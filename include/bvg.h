@@ -52,7 +52,7 @@ typedef enum {
     BVG_ERR_NUMERIC = -6,       /* NaN/Inf met (e.g. in a PageRank iterate) */
     BVG_ERR_TIMEOUT = -7,       /* a bounded device wait ran out */
     BVG_ERR_CORRUPT = -8,       /* bitstream fails to decode */
-    BVG_ERR_UNSUPPORTED = -9    /* size or option outside what this build handles */
+    BVG_ERR_UNSUPPORTED = -9    /* size or option outside what the library supports */
 } bvg_status;
 
 typedef struct bvg_host_graph bvg_host_graph; /* host encoding: refs, difference rows, bitstream */
