@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--config5", action="store_true",
                     help="run the BV-vs-CSR crossover on the social graph n = 5.4 M and the web graph n = 22.7 M "
                          "(k = 8)")
+    ap.add_argument("--window-sweep", action="store_true",
+                    help="encode the bench graph with window W in {1, 3, 5, 7} and chain bound R in {1, 2, 3}: "
+                         "compression and both products' speed")
     ap.add_argument("--config4", action="store_true",
                     help="train the warm-start network on 200 generated graphs (n log-uniform in [1e5, 1e6]) and "
                          "evaluate it on the web-like graph n = 18.5 M")
@@ -299,6 +302,32 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
     if args.config5:
         out["social_5m4"] = crossover(synth.social_5m4(), 1)
         out["web_22m7_k8"] = crossover(synth.web_22m7(), 8)
+    return out
+
+
+def window_sweep_leg(args, bvg, torch, timed, g):
+    """The reference window W (Sec. 4) and the chain bound R against
+    compression and speed: the bench graph encoded with W in {1, 3, 5, 7}
+    (the device layout stores r_i as a 3-bit offset, so W <= 7) and R in
+    {1, 2, 3}; x A and A x^T at k = 1, L2 flushed before each product."""
+    import synth
+    x = torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
+    y = torch.empty_like(x)
+    out = []
+    for w in (1, 3, 5, 7):
+        for r in (1, 2, 3):
+            hs = bvg.bvg_encode(g.row_ptr, g.col, window=w, max_chain=r)
+            st = bvg.bvg_stats(hs)
+            ds = bvg.bvg_upload(hs)
+            res = {"window": w, "max_chain": r, "m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
+                   "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"]}
+            for name, fn in (("xA", lambda: bvg.bvg_spmv_xA(ds, x, y)), ("Ax", lambda: bvg.bvg_spmv_Ax(ds, x, y))):
+                for _ in range(args.warmup):
+                    fn()
+                ms = timed(fn, args.steps)
+                res[name + "_gedges_s"] = g.m * len(ms) / (np.sum(ms) * 1e-3) / 1e9
+            out.append(res)
+            del ds
     return out
 
 
@@ -598,6 +627,7 @@ def run_bv(args):
     krhs = None if args.no_krhs else krhs_leg(args, bvg, synth, torch, flush, timed, dg, g)
     batch = None if args.no_batch else batch_leg(args, bvg, synth, torch, flush, timed, world, rank, shard)
     warm = None if args.no_warmstart else warmstart_leg(args, bvg, synth, torch, dg, g, pr_s, pr_it)
+    wsweep = window_sweep_leg(args, bvg, torch, timed, g) if args.window_sweep else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -619,7 +649,7 @@ def run_bv(args):
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
-            "k_rhs": krhs, "batch": batch, "warm_start": warm, "variants": variants,
+            "k_rhs": krhs, "batch": batch, "warm_start": warm, "variants": variants, "window_sweep": wsweep,
             "compression": {"m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
                             "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"],
                             "structure_MB": L["structure_bytes"] / 1e6},

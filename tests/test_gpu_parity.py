@@ -508,3 +508,31 @@ def test_push_hub_columns(points):
     want, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, p0=P0.astype(np.float64), tol=1e-13, max_iter=2000)
     for c in range(k):
         assert l1(p.cpu().numpy()[:, c], want[:, c]) <= 1e-6, c
+
+
+@pytest.mark.parametrize("window,max_chain", [(1, 1), (3, 2), (5, 3), (7, 1)])
+def test_other_windows_and_chain_bounds(window, max_chain):
+    """Encodings with a shorter reference window W (Sec. 4) or chain bound R:
+    both products and PageRank match the oracle (the oracle decodes its own
+    references from the same encoding)."""
+    g = synth.copying_model(synth.tiny_web())
+    hg = bvg.bvg_encode(g.row_ptr, g.col, window=window, max_chain=max_chain)
+    ref, depth = bvg.bvg_get_refs(hg)
+    assert depth.max() <= max_chain and np.all((ref < 0) | (np.arange(g.n) - ref <= window))
+    dg = bvg.bvg_upload(hg)
+    for k in (1, 8, 33):
+        x = synth.rhs(g.n, k, synth.seed_for(1, 1200 + k))
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.full_like(xt, float("nan"))
+        bvg.bvg_spmv_xA(dg, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                    oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), f"xA W={window} R={max_chain} k={k}")
+        y.fill_(float("nan"))
+        bvg.bvg_spmv_Ax(dg, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                    oracle.bv_Ax(g.row_ptr, g.col, ref, x64, absval=True), f"Ax W={window} R={max_chain} k={k}")
+    p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
+    assert rc == bvg.BVG_OK and res[0] < 1e-8
+    pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000)
+    assert l1(p.cpu().numpy(), pstar) <= 1e-6
