@@ -86,10 +86,10 @@ constexpr int kThreads = 256;
 
 // Rows per CTA: the halo of kHalo rows is recomputed by two CTAs, so tiles
 // stay large; shared memory grows with kb, and the tile is halved until the
-// row sums (tile + kHalo rows x kb compensated values) fit in 200 KB.
+// row sums (tile + kHalo rows x kb floats) fit in 200 KB.
 static int pull_tile(int kb, const LaunchCfg& c) {
     int t = kb <= 4 ? c.pull_tile : std::max(128, c.pull_tile / 2);
-    while (t > 64 && (size_t)(t + kHalo) * kb * sizeof(df) > 200 * 1024) t /= 2;
+    while (t > 64 && (size_t)(t + kHalo) * kb * sizeof(float) > 200 * 1024) t /= 2;
     return t;
 }
 // Columns per CTA of the gather kernel (k_gather's GatherShape).
@@ -191,7 +191,7 @@ static void launch_pull(const bvg_dev_graph* g, const float* x, int64_t ldx, flo
         }
     }
     const int tile = pull_tile(KB, g->cfg);
-    const size_t smem = (size_t)(tile + kHalo) * KB * sizeof(df);
+    const size_t smem = (size_t)(tile + kHalo) * KB * sizeof(float);
     set_smem(k_pull_rows<KB, V>, smem);
     const int64_t grid = (g->n + tile - 1) / tile;
     TraceScope ts(g, "pull_rows", st);

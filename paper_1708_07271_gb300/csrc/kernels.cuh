@@ -314,7 +314,11 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
     constexpr int PF = G == 1 ? 2 : 0;
     constexpr int PFA = PF > 0 ? PF : 1;
     extern __shared__ float4 smem_pull[];
-    df* c = reinterpret_cast<df*>(smem_pull);  // [(tile + kHalo) * KB]
+    // [(tile + kHalo) * KB] row sums, each compensated and then rounded once
+    // to FP32 (half the shared memory of keeping them compensated, so twice
+    // the resident CTAs for wide column blocks); the chains add them
+    // compensated
+    float* c = reinterpret_cast<float*>(smem_pull);
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
     const int64_t a = (int64_t)blockIdx.x * tile;
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
         df acc[V];
         pull_row_sum<KB, V>(acc, lo + r, k0, k1, part, lrow, lint, x, ldx, lane, pf);
 #pragma unroll
-        for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = acc[v];
+        for (int v = 0; v < V; v++) c[(int64_t)r * KB + lane * V + v] = df_val(acc[v]);
     };
 #pragma unroll
     for (int j = 0; j < PF; j++) {
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
                     df t[1] = {df_zero()};
                     for (int w = 0; w < NW; w++) t[0] = df_add(t[0], long_part[w][threadIdx.x]);
                     pull_row_intervals<KB, 1>(t, lo + r, lrow, lint, x, ldx, threadIdx.x, pf);
-                    c[(int64_t)r * KB + threadIdx.x] = t[0];
+                    c[(int64_t)r * KB + threadIdx.x] = df_val(t[0]);
                 }
                 __syncthreads();
             }
@@ -415,8 +419,8 @@ __global__ void __launch_bounds__(256) k_pull_rows(const uint8_t* __restrict__ m
         Vec<V> out;
 #pragma unroll
         for (int v = 0; v < V; v++) {
-            df sacc = c[(int64_t)ix[len - 1] * KB + lane * V + v];
-            for (int t = len - 2; t >= 0; t--) sacc = df_add(c[(int64_t)ix[t] * KB + lane * V + v], sacc);
+            df sacc = {c[(int64_t)ix[len - 1] * KB + lane * V + v], 0.f};
+            for (int t = len - 2; t >= 0; t--) sacc = df_addf(sacc, c[(int64_t)ix[t] * KB + lane * V + v]);
             out.v[v] = df_val(sacc);
         }
         stv<V>(y + (lo + r) * ldy + lane * V, out);
