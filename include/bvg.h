@@ -406,6 +406,51 @@ typedef struct {
 } bvg_layout_info;
 int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 
+/* ------------------------------------------ biclique representation */
+
+/* The second compressed format of the paper's final remarks (Sec. 7): the
+ * edges are split into bicliques (S_r, C_r), every node of S_r pointing to
+ * every node of C_r, stored as the two lists (|S_r| + |C_r| words for
+ * |S_r| * |C_r| edges), plus residual edges. A x^T is then c_r = sum over C_r
+ * of x, added to y_i for every i in S_r, plus the residual edges. The paper
+ * cites an extraction method without describing it; bvg_biclique_encode uses
+ * its own deterministic greedy miner (rows keyed by a min-hash of their
+ * remaining successors, per pass; within a run of equal keys a biclique grows
+ * row by row while |S| * |C| - (|S| + |C|) does not shrink, and is kept when
+ * that saving is positive; bicliques with equal column sets are then merged).
+ * Host only. */
+typedef struct bvg_biclique bvg_biclique;  /* host decomposition */
+typedef struct {
+    int32_t passes;    /* min-hash passes; 0 = 4 */
+    int32_t min_rows;  /* rows of a biclique at least; 0 = 2 */
+    int32_t min_cols;  /* columns of a biclique at least; 0 = 2 */
+    int32_t pad;
+    uint64_t seed;     /* hash seed */
+} bvg_biclique_params;
+typedef struct {
+    int64_t n, m;
+    int64_t bicliques;       /* number of bicliques */
+    int64_t s_total, c_total; /* sum |S_r|, sum |C_r| */
+    int64_t residual;        /* residual edges */
+    int64_t words;           /* s_total + c_total + residual */
+    int64_t biclique_edges;  /* sum |S_r| * |C_r| (= m - residual) */
+} bvg_biclique_info;
+/* Decomposes the CSR of A (rows sorted, no repeats, ids in [0, n), n < 2^31;
+ * copied). params may be NULL (defaults). *out is owned by the caller
+ * (bvg_free_biclique). Synchronous. Errors: INVALID_ARG, OOM. */
+int bvg_biclique_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                        const bvg_biclique_params* params, bvg_biclique** out);
+int bvg_biclique_stats(const bvg_biclique* b, bvg_biclique_info* out);
+/* The decomposition into caller buffers sized from bvg_biclique_stats:
+ * s_ptr[bicliques + 1], s_idx[s_total] (the rows of biclique r are
+ * s_idx[s_ptr[r], s_ptr[r + 1]), increasing), c_ptr[bicliques + 1],
+ * c_idx[c_total] (its columns, increasing), r_ptr[n + 1], r_col[residual]
+ * (the residual edges of row i, increasing). The bicliques and the residual
+ * edges are disjoint and together are exactly the edges of A. */
+int bvg_biclique_get(const bvg_biclique* b, int64_t* s_ptr, int32_t* s_idx, int64_t* c_ptr, int32_t* c_idx,
+                     int64_t* r_ptr, int32_t* r_col);
+void bvg_free_biclique(bvg_biclique* b);
+
 /* --------------------------------------------------- plain CSR baseline */
 
 /* Device CSR of A and of A^T built from a host CSR (same input rules as

@@ -40,7 +40,7 @@ EXPORTED = [
     "bvg_warmstart_predict", "bvg_free_mlp", "bvg_batch_create", "bvg_batch_size", "bvg_batch_spmv_xA",
     "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
     "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
-    "bvg_point_cols_fill",
+    "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
 ]
 
 
@@ -82,6 +82,15 @@ class LayoutView(ctypes.Structure):
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
                 ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32)]
+
+
+class BicliqueParams(ctypes.Structure):
+    _fields_ = [("passes", _I32), ("min_rows", _I32), ("min_cols", _I32), ("pad", _I32), ("seed", ctypes.c_uint64)]
+
+
+class BicliqueInfo(ctypes.Structure):
+    _fields_ = [(f, _I64) for f in ("n", "m", "bicliques", "s_total", "c_total", "residual", "words",
+                                      "biclique_edges")]
 
 
 class AutotuneInfo(ctypes.Structure):
@@ -171,6 +180,11 @@ def load(build_if_needed: bool = True):
             "bvg_pull_items_fill": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
             "bvg_point_cols_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
             "bvg_point_cols_fill": ([_P, _P, _P, _P, _P], ctypes.c_int),
+            "bvg_biclique_encode": ([_I64, _P, _P, ctypes.POINTER(BicliqueParams), ctypes.POINTER(_P)],
+                                    ctypes.c_int),
+            "bvg_biclique_stats": ([_P, ctypes.POINTER(BicliqueInfo)], ctypes.c_int),
+            "bvg_biclique_get": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+            "bvg_free_biclique": ([_P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -687,4 +701,31 @@ def bvg_point_cols(hg: HostGraph) -> dict:
            "bvg_point_cols_fill")
     out["ent"] = out["ent"][:e.value]
     out["titem"] = out["titem"][:t.value]
+    return out
+
+
+def bvg_biclique_encode(row_ptr, col, passes: int = 4, min_rows: int = 2, min_cols: int = 2,
+                        seed: int = 0) -> dict:
+    """The biclique decomposition of a CSR graph (Sec. 7; host only): the
+    arrays s_ptr, s_idx, c_ptr, c_idx, r_ptr, r_col and the sizes."""
+    lib = load()
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    prm = BicliqueParams(passes, min_rows, min_cols, 0, seed)
+    h = _P()
+    _check(lib.bvg_biclique_encode(n, rp.ctypes.data, ci.ctypes.data, ctypes.byref(prm), ctypes.byref(h)),
+           "bvg_biclique_encode")
+    try:
+        info = BicliqueInfo()
+        _check(lib.bvg_biclique_stats(h, ctypes.byref(info)), "bvg_biclique_stats")
+        out = {"s_ptr": np.zeros(info.bicliques + 1, np.int64), "s_idx": np.zeros(max(info.s_total, 1), np.int32),
+               "c_ptr": np.zeros(info.bicliques + 1, np.int64), "c_idx": np.zeros(max(info.c_total, 1), np.int32),
+               "r_ptr": np.zeros(n + 1, np.int64), "r_col": np.zeros(max(info.residual, 1), np.int32)}
+        _check(lib.bvg_biclique_get(h, *[out[f].ctypes.data for f in ("s_ptr", "s_idx", "c_ptr", "c_idx", "r_ptr",
+                                                                      "r_col")]), "bvg_biclique_get")
+    finally:
+        lib.bvg_free_biclique(h)
+    out["s_idx"] = out["s_idx"][:info.s_total]
+    out["c_idx"] = out["c_idx"][:info.c_total]
+    out["r_col"] = out["r_col"][:info.residual]
+    out.update({f: getattr(info, f) for f, _ in BicliqueInfo._fields_})
     return out
