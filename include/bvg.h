@@ -408,7 +408,7 @@ int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 
 /* ------------------------------------------ biclique representation */
 
-/* The second compressed format of the paper's final remarks (Sec. 7): the
+/* The second compressed format of the paper's final remarks (Sec. 6): the
  * edges are split into bicliques (S_r, C_r), every node of S_r pointing to
  * every node of C_r, stored as the two lists (|S_r| + |C_r| words for
  * |S_r| * |C_r| edges), plus residual edges. A x^T is then c_r = sum over C_r

@@ -1,7 +1,7 @@
 """ORACLE -- test infrastructure only (see the package docstring).
 
 The biclique representation of a binary adjacency matrix, as the paper's
-final remarks (Sec. 7) describe it: the edges are split into bicliques
+final remarks (Sec. 6) describe it: the edges are split into bicliques
 (S_r, C_r), every node of S_r pointing to every node of C_r, plus a set of
 residual edges. A biclique's |S_r| * |C_r| edges are stored as the two lists,
 |S_r| + |C_r| words.
@@ -32,7 +32,7 @@ def _spans(ptr, idx, r):
 
 
 def biclique_Ax(dec: dict, x: np.ndarray) -> np.ndarray:
-    """y = A x^T on the biclique representation (Sec. 7); x is n or n x k."""
+    """y = A x^T on the biclique representation (Sec. 6); x is n or n x k."""
     x = np.asarray(x, np.float64)
     xs = x.reshape(x.shape[0], -1)
     y = np.zeros_like(xs)
@@ -83,5 +83,5 @@ def edges_of(dec: dict, n: int) -> np.ndarray:
 
 def words(dec: dict) -> int:
     """Words of the representation: |S_r| + |C_r| per biclique plus one per
-    residual edge (Sec. 7)."""
+    residual edge (Sec. 6)."""
     return int(len(dec["s_idx"]) + len(dec["c_idx"]) + len(dec["r_col"]))

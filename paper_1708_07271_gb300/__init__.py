@@ -706,7 +706,7 @@ def bvg_point_cols(hg: HostGraph) -> dict:
 
 def bvg_biclique_encode(row_ptr, col, passes: int = 4, min_rows: int = 2, min_cols: int = 2,
                         seed: int = 0) -> dict:
-    """The biclique decomposition of a CSR graph (Sec. 7; host only): the
+    """The biclique decomposition of a CSR graph (Sec. 6; host only): the
     arrays s_ptr, s_idx, c_ptr, c_idx, r_ptr, r_col and the sizes."""
     lib = load()
     rp, ci, n = _csr_arrays(row_ptr, col)

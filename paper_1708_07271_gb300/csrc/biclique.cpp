@@ -1,5 +1,5 @@
 // Biclique representation of a binary adjacency matrix (the second
-// compressed format of the paper's final remarks, Sec. 7): the edges are
+// compressed format of the paper's final remarks, Sec. 6): the edges are
 // split into bicliques (S_r, C_r), every node of S_r pointing to every node of
 // C_r, stored as the two lists (|S_r| + |C_r| words for |S_r| * |C_r| edges),
 // plus residual edges.

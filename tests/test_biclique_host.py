@@ -1,4 +1,4 @@
-"""The host biclique extractor (Sec. 7's second compressed format): the
+"""The host biclique extractor (Sec. 6's second compressed format): the
 decomposition stores exactly the graph's edges (bicliques and residual
 edges disjoint), the oracle's biclique products on it equal the plain CSR
 products, it is deterministic, and it finds planted bicliques. No GPU."""

@@ -1,4 +1,4 @@
-"""The biclique oracle (Sec. 7) against what fixes it independently: a
+"""The biclique oracle (Sec. 6) against what fixes it independently: a
 hand-worked example (tests/golden/biclique_example_n6.txt) and dense
 brute force on random decompositions. No GPU needed."""
 import os
