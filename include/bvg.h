@@ -421,9 +421,9 @@ int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
  * Host only. */
 typedef struct bvg_biclique bvg_biclique;  /* host decomposition */
 typedef struct {
-    int32_t passes;    /* min-hash passes; 0 = 4 */
+    int32_t passes;    /* min-hash passes; 0 = 8 */
     int32_t min_rows;  /* rows of a biclique at least; 0 = 2 */
-    int32_t min_cols;  /* columns of a biclique at least; 0 = 2 */
+    int32_t min_cols;  /* columns of a biclique at least; 0 = 3 */
     int32_t pad;
     uint64_t seed;     /* hash seed */
 } bvg_biclique_params;

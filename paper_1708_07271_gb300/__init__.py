@@ -704,7 +704,7 @@ def bvg_point_cols(hg: HostGraph) -> dict:
     return out
 
 
-def bvg_biclique_encode(row_ptr, col, passes: int = 4, min_rows: int = 2, min_cols: int = 2,
+def bvg_biclique_encode(row_ptr, col, passes: int = 8, min_rows: int = 2, min_cols: int = 3,
                         seed: int = 0) -> dict:
     """The biclique decomposition of a CSR graph (Sec. 6; host only): the
     arrays s_ptr, s_idx, c_ptr, c_idx, r_ptr, r_col and the sizes."""

@@ -63,9 +63,12 @@ extern "C" int bvg_biclique_encode(int64_t n, const int64_t* row_ptr, const int3
     *out = nullptr;
     if (n < 0 || n >= ((int64_t)1 << 31) || !row_ptr || (n > 0 && row_ptr[n] > 0 && !col))
         return fail(BVG_ERR_INVALID_ARG, "bvg_biclique_encode: bad n or NULL arrays");
-    const int passes = params && params->passes > 0 ? params->passes : 4;
+    // defaults: 8 passes and 3 columns; on 200,000-row samples of the
+    // generated graphs, 4 passes gave m/words 2.90 (web) and 1.21 (social),
+    // 8 gave 3.01 and 1.23, 16 gave 3.03 and 1.24
+    const int passes = params && params->passes > 0 ? params->passes : 8;
     const int64_t min_rows = params && params->min_rows > 1 ? params->min_rows : 2;
-    const int64_t min_cols = params && params->min_cols > 1 ? params->min_cols : 2;
+    const int64_t min_cols = params && params->min_cols > 1 ? params->min_cols : 3;
     const uint64_t seed = params ? params->seed : 0;
     if (row_ptr[0] != 0) return fail(BVG_ERR_INVALID_ARG, "bvg_biclique_encode: row_ptr[0] != 0");
     for (int64_t i = 0; i < n; i++) {

@@ -46,7 +46,7 @@ def test_decomposition_is_exact_and_products_match(name):
     for r in range(dec["bicliques"]):
         s = dec["s_idx"][dec["s_ptr"][r]:dec["s_ptr"][r + 1]]
         c = dec["c_idx"][dec["c_ptr"][r]:dec["c_ptr"][r + 1]]
-        assert len(s) >= 2 and len(c) >= 2 and len(s) * len(c) > len(s) + len(c)  # each one saves words
+        assert len(s) >= 2 and len(c) >= 3 and len(s) * len(c) > len(s) + len(c)  # each one saves words
         assert np.all(np.diff(s) > 0) and np.all(np.diff(c) > 0)
     x = synth.dyadic_rhs(g.n, 3, 11) if g.n else np.zeros((0, 3))
     np.testing.assert_array_equal(ob.biclique_Ax(dec, x), oracle.csr_Ax(g.row_ptr, g.col, x))
