@@ -449,6 +449,14 @@ int bvg_biclique_stats(const bvg_biclique* b, bvg_biclique_info* out);
  * edges are disjoint and together are exactly the edges of A. */
 int bvg_biclique_get(const bvg_biclique* b, int64_t* s_ptr, int32_t* s_idx, int64_t* c_ptr, int32_t* c_idx,
                      int64_t* r_ptr, int32_t* r_col);
+/* The lists a device product gathers from, into caller buffers: row_ptr2
+ * [n + 1] and row_bic[s_total] (the bicliques whose S holds row i: for A x^T,
+ * y_i adds their c_r), col_ptr2[n + 1] and col_bic[c_total] (the bicliques
+ * whose C holds column j: for x A, y_j adds their sum over S), rt_ptr[n + 1]
+ * and rt_row[residual] (the residual edges into column j, by source row).
+ * Every list is increasing. Host only. Errors: INVALID_ARG. */
+int bvg_biclique_gather_lists(const bvg_biclique* b, int64_t* row_ptr2, int32_t* row_bic, int64_t* col_ptr2,
+                              int32_t* col_bic, int64_t* rt_ptr, int32_t* rt_row);
 void bvg_free_biclique(bvg_biclique* b);
 
 /* --------------------------------------------------- plain CSR baseline */

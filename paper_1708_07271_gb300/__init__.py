@@ -41,6 +41,7 @@ EXPORTED = [
     "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
     "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
     "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
+    "bvg_biclique_gather_lists",
 ]
 
 
@@ -185,6 +186,7 @@ def load(build_if_needed: bool = True):
             "bvg_biclique_stats": ([_P, ctypes.POINTER(BicliqueInfo)], ctypes.c_int),
             "bvg_biclique_get": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
             "bvg_free_biclique": ([_P], None),
+            "bvg_biclique_gather_lists": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -722,10 +724,19 @@ def bvg_biclique_encode(row_ptr, col, passes: int = 8, min_rows: int = 2, min_co
                "r_ptr": np.zeros(n + 1, np.int64), "r_col": np.zeros(max(info.residual, 1), np.int32)}
         _check(lib.bvg_biclique_get(h, *[out[f].ctypes.data for f in ("s_ptr", "s_idx", "c_ptr", "c_idx", "r_ptr",
                                                                       "r_col")]), "bvg_biclique_get")
+        out.update({"row_ptr2": np.zeros(n + 1, np.int64), "row_bic": np.zeros(max(info.s_total, 1), np.int32),
+                    "col_ptr2": np.zeros(n + 1, np.int64), "col_bic": np.zeros(max(info.c_total, 1), np.int32),
+                    "rt_ptr": np.zeros(n + 1, np.int64), "rt_row": np.zeros(max(info.residual, 1), np.int32)})
+        _check(lib.bvg_biclique_gather_lists(h, *[out[f].ctypes.data for f in ("row_ptr2", "row_bic", "col_ptr2",
+                                                                               "col_bic", "rt_ptr", "rt_row")]),
+               "bvg_biclique_gather_lists")
     finally:
         lib.bvg_free_biclique(h)
     out["s_idx"] = out["s_idx"][:info.s_total]
     out["c_idx"] = out["c_idx"][:info.c_total]
     out["r_col"] = out["r_col"][:info.residual]
+    out["row_bic"] = out["row_bic"][:info.s_total]
+    out["col_bic"] = out["col_bic"][:info.c_total]
+    out["rt_row"] = out["rt_row"][:info.residual]
     out.update({f: getattr(info, f) for f, _ in BicliqueInfo._fields_})
     return out

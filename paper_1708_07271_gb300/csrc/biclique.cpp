@@ -217,4 +217,38 @@ extern "C" int bvg_biclique_get(const bvg_biclique* b, int64_t* s_ptr, int32_t* 
     return BVG_OK;
 }
 
+// Inverse memberships and the residual edges by column: the arrays a device
+// product gathers from. row_bic[row_ptr2[i], row_ptr2[i + 1]) are the
+// bicliques whose S holds row i (A x^T: y_i adds their c_r);
+// col_bic[col_ptr2[j], col_ptr2[j + 1]) those whose C holds column j (x A: y_j
+// adds their d_r); rt_row[rt_ptr[j], rt_ptr[j + 1]) the residual edges into
+// column j, by source row. Every list is increasing.
+extern "C" int bvg_biclique_gather_lists(const bvg_biclique* b, int64_t* row_ptr2, int32_t* row_bic, int64_t* col_ptr2,
+                                         int32_t* col_bic, int64_t* rt_ptr, int32_t* rt_row) {
+    if (!b || !row_ptr2 || !col_ptr2 || !rt_ptr || (!row_bic && !b->s_idx.empty()) ||
+        (!col_bic && !b->c_idx.empty()) || (!rt_row && !b->r_col.empty()))
+        return fail(BVG_ERR_INVALID_ARG, "bvg_biclique_gather_lists: NULL array");
+    const int64_t n = b->n, nb = (int64_t)b->s_ptr.size() - 1;
+    // counting sorts; bicliques and source rows are visited in increasing order
+    std::fill(row_ptr2, row_ptr2 + n + 1, 0);
+    std::fill(col_ptr2, col_ptr2 + n + 1, 0);
+    std::fill(rt_ptr, rt_ptr + n + 1, 0);
+    for (int32_t i : b->s_idx) row_ptr2[i + 1]++;
+    for (int32_t j : b->c_idx) col_ptr2[j + 1]++;
+    for (int32_t j : b->r_col) rt_ptr[j + 1]++;
+    for (int64_t t = 0; t < n; t++) {
+        row_ptr2[t + 1] += row_ptr2[t];
+        col_ptr2[t + 1] += col_ptr2[t];
+        rt_ptr[t + 1] += rt_ptr[t];
+    }
+    std::vector<int64_t> fr(row_ptr2, row_ptr2 + n), fc(col_ptr2, col_ptr2 + n), ft(rt_ptr, rt_ptr + n);
+    for (int64_t r = 0; r < nb; r++) {
+        for (int64_t e = b->s_ptr[r]; e < b->s_ptr[r + 1]; e++) row_bic[fr[b->s_idx[e]]++] = (int32_t)r;
+        for (int64_t e = b->c_ptr[r]; e < b->c_ptr[r + 1]; e++) col_bic[fc[b->c_idx[e]]++] = (int32_t)r;
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t e = b->r_ptr[i]; e < b->r_ptr[i + 1]; e++) rt_row[ft[b->r_col[e]]++] = (int32_t)i;
+    return BVG_OK;
+}
+
 extern "C" void bvg_free_biclique(bvg_biclique* b) { delete b; }
