@@ -108,6 +108,31 @@ int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
  * Errors: INVALID_ARG, CORRUPT. */
 int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx);
 
+/* The encoding's bitstream (Sec. 4 representation written with the codes of
+ * R4: gamma-coded reference offsets, copy blocks, interval and residual
+ * counts, delta-coded gaps), most significant bit first in 64-bit words.
+ * *nbits gets its length; if words != NULL the first ceil(nbits / 64) words
+ * are copied there (cap_words at least that, else INVALID_ARG). Host only. */
+int bvg_bitstream_get(const bvg_host_graph* g, uint64_t* words, int64_t cap_words, int64_t* nbits);
+
+/* Decodes a caller-provided bitstream of n rows and m edges, written with
+ * the window and minimum interval length of `params` (NULL = defaults), into
+ * caller arrays row_ptr[n + 1] and col_idx[m]. Every count, offset and id is
+ * checked against n, m, the window and the rows decoded so far before use:
+ * a damaged or truncated stream returns BVG_ERR_CORRUPT and never reads or
+ * writes outside the given buffers. Host only. Errors: INVALID_ARG,
+ * UNSUPPORTED, CORRUPT, OOM. */
+int bvg_decode_bits(int64_t n, int64_t m, const bvg_encode_params* params, const uint64_t* words, int64_t nbits,
+                    int64_t* row_ptr, int32_t* col_idx);
+
+/* Testing hook (the paper has no counterpart): after `after` further
+ * allocation checkpoints, the next one fails once, as if the host or device
+ * allocator had run out, and the call that reached it returns BVG_ERR_OOM
+ * after releasing what it had allocated. Checkpoints: the start of
+ * bvg_encode's allocations and every device allocation of bvg_upload and
+ * the products. after < 0 disables the hook (the default). Always BVG_OK. */
+int bvg_debug_fail_alloc(int64_t after);
+
 /* Fills *out with the sizes of the encoding. */
 int bvg_stats(const bvg_host_graph* g, bvg_graph_stats* out);
 
@@ -231,6 +256,13 @@ int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int
  * INVALID_ARG, UNSUPPORTED, CUDA. */
 int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
+/* Reports a bounded device wait that ran out in an earlier launch on this
+ * graph (the fused x A kernel waits for its TMA copies at most about 2 s and
+ * then marks the graph and writes NaN outputs rather than hang): synchronises
+ * `stream`, returns BVG_ERR_TIMEOUT (and clears the mark) if one did, else
+ * BVG_OK. The paper has no counterpart. */
+int bvg_device_check(const bvg_dev_graph* g, void* stream);
+
 /* Same as bvg_spmv_xA with x and y in HOST memory (page-locked, which copies
  * fastest, or pageable), n x k, ld == k: copies x to device scratch, runs the
  * product, copies y back, and synchronises `stream` before returning.
@@ -305,9 +337,9 @@ int bvg_mlp_set_params(bvg_mlp* net, const float* host, int64_t count);
 /* Copies the FP32 parameters to host memory. Synchronises the device. */
 int bvg_mlp_get_params(const bvg_mlp* net, float* host, int64_t count);
 /* Node features of g into feat (device, n x 8 floats, 16-byte aligned):
- * log1p(in-degree), log1p(out-degree), reference-chain depth (Sec. 3.1),
+ * log1p(in-degree), log1p(out-degree), reference-chain depth (Sec. 4),
  * fraction of the out-neighbours stored in intervals of the difference row
- * (Sec. 3.2), log1p(mean out-degree of the out-neighbours), log1p(weighted
+ * (Sec. 4), log1p(mean out-degree of the out-neighbours), log1p(weighted
  * in-degree sum_{j -> i} 1/outdeg(j)), 0, 0. The degrees come from two
  * compressed products: (1, 1/outdeg) A with k = 2, and A outdeg^T.
  * May grow the graph's scratch. Asynchronous on `stream`. */
@@ -350,8 +382,13 @@ typedef struct {
     int32_t gather_pdl;     /* 1: the push gather overlaps the chain kernel's tail (programmatic launch) */
     int32_t col_block;      /* widest column block of a product: power of two in [1, 32] (default 32) */
     int32_t pull_item;      /* pull: entries per work item, 4, 8 or 16 (default 8) */
-    int32_t push_points;    /* push gather over the point columns: -1 for column blocks of 4 or more right-hand
-                               sides (default), 0 never (event columns), 1 always */
+    int32_t push_points;    /* push gather over the point columns: -1 for every column block (default), 0 never
+                               (the event columns: intervals as start / end events and a running FP32 sum across
+                               the tile, whose error is bounded relative to that running sum, not to the column's
+                               own terms), 1 always */
+    int32_t push_fused;     /* x A for one right-hand side in one kernel (exact fixed-point sums, TMA-staged
+                               structure): -1 when at most 5% of its column tiles read rows outside their window
+                               (default), 0 never, 1 always */
 } bvg_launch_config;
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
@@ -422,8 +459,8 @@ int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 typedef struct bvg_biclique bvg_biclique;  /* host decomposition */
 typedef struct {
     int32_t passes;    /* min-hash passes; 0 = 8 */
-    int32_t min_rows;  /* rows of a biclique at least; 0 = 2 */
-    int32_t min_cols;  /* columns of a biclique at least; 0 = 3 */
+    int32_t min_rows;  /* rows of a biclique at least; any value below 2 selects the default 2 */
+    int32_t min_cols;  /* columns of a biclique at least; any value below 2 selects the default 3 */
     int32_t pad;
     uint64_t seed;     /* hash seed */
 } bvg_biclique_params;

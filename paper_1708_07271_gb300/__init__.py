@@ -41,7 +41,8 @@ EXPORTED = [
     "bvg_free_batch", "bvg_autotune", "bvg_autotune_info_get", "bvg_autotune_key", "bvg_autotune_cache_lookup",
     "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
     "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
-    "bvg_biclique_gather_lists",
+    "bvg_biclique_gather_lists", "bvg_bitstream_get", "bvg_decode_bits", "bvg_debug_fail_alloc",
+    "bvg_device_check",
 ]
 
 
@@ -82,7 +83,7 @@ class LayoutView(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
-                ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32)]
+                ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32), ("push_fused", _I32)]
 
 
 class BicliqueParams(ctypes.Structure):
@@ -187,6 +188,10 @@ def load(build_if_needed: bool = True):
             "bvg_biclique_get": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
             "bvg_free_biclique": ([_P], None),
             "bvg_biclique_gather_lists": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+            "bvg_bitstream_get": ([_P, _P, _I64, ctypes.POINTER(_I64)], ctypes.c_int),
+            "bvg_decode_bits": ([_I64, _I64, ctypes.POINTER(EncodeParams), _P, _I64, _P, _P], ctypes.c_int),
+            "bvg_debug_fail_alloc": ([_I64], ctypes.c_int),
+            "bvg_device_check": ([_P, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -299,6 +304,39 @@ def bvg_decode(hg: HostGraph):
     ci = np.empty(max(m, 1), np.int32)
     _check(load().bvg_decode(hg.ptr, rp.ctypes.data, ci.ctypes.data), "bvg_decode")
     return rp, ci[:m]
+
+
+def bvg_bitstream_get(hg: HostGraph):
+    """The encoding's bitstream: (uint64 words, number of bits)."""
+    nb = _I64()
+    lib = load()
+    _check(lib.bvg_bitstream_get(hg.ptr, None, 0, ctypes.byref(nb)), "bvg_bitstream_get")
+    words = np.zeros(max(1, (nb.value + 63) // 64), np.uint64)
+    _check(lib.bvg_bitstream_get(hg.ptr, words.ctypes.data, len(words), ctypes.byref(nb)), "bvg_bitstream_get")
+    return words[:(nb.value + 63) // 64], nb.value
+
+
+def bvg_decode_bits(n: int, m: int, words, nbits: int, window=7, min_interval=4):
+    """Decodes a bitstream (uint64 words, MSB first) of n rows and m edges into
+    CSR (row_ptr, col)."""
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(max(m, 1), np.int32)
+    prm = EncodeParams(window, 0, min_interval, 0)
+    _check(load().bvg_decode_bits(n, m, ctypes.byref(prm), w.ctypes.data if len(w) else None, nbits,
+                                  rp.ctypes.data, ci.ctypes.data), "bvg_decode_bits")
+    return rp, ci[:m]
+
+
+def bvg_device_check(dg, stream=None) -> None:
+    """Raises BvgError(BVG_ERR_TIMEOUT) if a bounded device wait ran out in an
+    earlier launch on this graph (synchronises the stream)."""
+    _check(load().bvg_device_check(dg.ptr, _stream(stream)), "bvg_device_check")
+
+
+def bvg_debug_fail_alloc(after: int) -> None:
+    """Testing hook: the allocation checkpoint reached after `after` more fails once (-1 disables)."""
+    _check(load().bvg_debug_fail_alloc(after), "bvg_debug_fail_alloc")
 
 
 def bvg_stats(hg: HostGraph) -> dict:
@@ -667,7 +705,7 @@ def bvg_autotune_cache_lookup(path, key: str):
 
 
 def bvg_autotune_cache_store(path, key: str, config: dict, push_us: float = 0.0, pull_us: float = 0.0):
-    c = LaunchConfig(**{f: int(config.get(f, -1) if f == "push_points" else config[f])
+    c = LaunchConfig(**{f: int(config.get(f, -1) if f in ("push_points", "push_fused") else config[f])
                         for f, _ in LaunchConfig._fields_})
     _check(load().bvg_autotune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c), push_us, pull_us),
            "bvg_autotune_cache_store")

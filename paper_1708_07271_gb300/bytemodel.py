@@ -18,6 +18,14 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
                [+ 4(n+1) + 4*point_tail_items (tail items) when k <= 4, where one lane
                group owns a column and the tail items are shared out] + 4kn (z) + 4kn (y)
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
+  push_fused   (one right-hand side, one kernel) n (meta) + 4(n+1) (column offsets)
+               + 4*col_entries + 4*(carry_tiles+1) + 4*carry_entries + ceil(n/1024)
+               (per-tile flags) + 4n (x) + 4n (y); the chain weights never leave
+               shared memory, and the window rows read by two neighbouring tiles
+               come from L2 the second time
+  pr_fused     push_fused + 4n (1/outdeg) [+ 4n (p0) when a teleport vector is
+               given]: x is the previous iterate (read once), the new iterate is
+               written in place of y
   pr_chain     push_chain + 4n (1/outdeg)
   pr_gather    push_gather - 4kn (y not stored) + 4n (1/outdeg) + 4kn (q_prev)
                + 4kn (q_new) [+ 4kn (p0) when teleport vectors are given]; pr_gather_pt
@@ -67,8 +75,20 @@ def pr_gather_pt(L: dict, k: int, with_p0: bool) -> int:
     return push_gather_pt(L, k) - 4 * k * n + 4 * n + 8 * k * n + (4 * k * n if with_p0 else 0)
 
 
+def push_fused(L: dict, k: int) -> int:
+    n = L["n"]
+    return (n + 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
+            + (n + 1023) // 1024 + 8 * k * n)
+
+
+def pr_fused(L: dict, k: int, with_p0: bool = False) -> int:
+    n = L["n"]
+    return push_fused(L, k) + 4 * n + (4 * k * n if with_p0 else 0)
+
+
 def xA_total(L: dict, k: int) -> int:
     return push_chain(L, k) + push_gather(L, k)
 
 
-KERNELS = {"push_gather": push_gather, "push_gather_pt": push_gather_pt, "push_chain": push_chain, "pull": pull}
+KERNELS = {"push_gather": push_gather, "push_gather_pt": push_gather_pt, "push_chain": push_chain, "pull": pull,
+           "push_fused": push_fused}

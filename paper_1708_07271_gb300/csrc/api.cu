@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "kernels.cuh"
+#include "fused.cuh"
 
 using namespace bvg;
 
@@ -17,6 +17,7 @@ namespace bvg {
 static int dev_alloc(void** p, size_t bytes, int64_t* total) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (inject_alloc_failure()) return fail(BVG_ERR_OOM, "cudaMalloc(%zu): injected failure", bytes);
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -220,12 +221,54 @@ static void launch_chain(const bvg_dev_graph* g, const float* x, int64_t ldx, co
 // Whether the gather of a kb-wide column block reads the point columns
 // (which ensure_points has built when this is true).
 bool use_points(const bvg_dev_graph* g, int kb) {
+    (void)kb;
     if (g->pcol_state != 1) return false;
-    return g->cfg.push_points == 1 || (g->cfg.push_points < 0 && kb >= 4);
+    return g->cfg.push_points != 0;
 }
 bool want_points(const bvg_dev_graph* g, int kb) {
+    (void)kb;
     if (g->pcol_state < 0) return false;
-    return g->cfg.push_points == 1 || (g->cfg.push_points < 0 && kb >= 4);
+    return g->cfg.push_points != 0;
+}
+
+// Whether a one-vector column block runs as the fused kernel (fused.cuh): by
+// default when at most 1 in 20 column tiles reads rows outside its window
+// (graphs with locality); it needs the point columns for its compensated
+// path.
+bool use_fused(const bvg_dev_graph* g, int kb) {
+    if (kb != 1 || g->pcol_state != 1 || !g->tile_far) return false;
+    if (g->cfg.push_fused == 0) return false;
+    return g->cfg.push_fused == 1 || g->fx_far_tiles * 20 <= g->fx_tiles;
+}
+
+FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* y,
+                   int64_t ldy) {
+    FxArgs fa{};
+    fa.meta = g->meta;
+    fa.desc = g->desc;
+    fa.colp = g->colp;
+    fa.tent = g->tent;
+    fa.carry_ptr = g->carry_ptr;
+    fa.carry = g->carry;
+    fa.pcolp = g->pcolp;
+    fa.pcent = g->pcent;
+    fa.tile_far = g->tile_far;
+    fa.x = x;
+    fa.ldx = ldx;
+    fa.rowscale = rowscale;
+    fa.y = y;
+    fa.ldy = ldy;
+    fa.n = g->n;
+    fa.err = g->err;
+    return fa;
+}
+
+static void launch_fused(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy,
+                         cudaStream_t st) {
+    const int64_t grid = (g->n + kFxT - 1) / kFxT;
+    PrArgs pa{};
+    TraceScope ts(g, "push_fused", st);
+    k_push_fx<0><<<(unsigned)grid, kFxNT, 0, st>>>(fused_args(g, x, ldx, nullptr, y, ldy), pa);
 }
 
 template <int KB, int V>
@@ -449,7 +492,7 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
     return BVG_OK;
 }
 
-static int check_vec(const bvg_dev_graph* g, const void* p, const char* what) {
+int check_vec(const bvg_dev_graph* g, const void* p, const char* what) {
     if (!p) return fail(BVG_ERR_INVALID_ARG, "%s is NULL", what);
     if ((uintptr_t)p % 4) return fail(BVG_ERR_INVALID_ARG, "%s is not 4-byte aligned", what);
     int d = device_of(p);
@@ -500,7 +543,11 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->ntitem = (int64_t)L->titem.size();
         g->ncarry = (int64_t)L->carry.size();
         g->fingerprint = layout_fingerprint(*L, n, hg->m);
-        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
+        // meta padded by 32 bytes: the fused kernel copies 16-byte aligned
+        // supersets of its row window
+        std::vector<uint8_t> meta_pad(L->meta);
+        meta_pad.resize((size_t)n + 32, 0);
+        if ((rc = upload_vec(&g->meta, meta_pad, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
             (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
             (rc = upload_vec(&g->titem_ptr, L->titem_ptr, st, &g->bytes)) ||
@@ -514,6 +561,41 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->host_rowp = L->rowp;
         g->host_ent = L->ent;
         if ((rc = build_pull_items(g, g->cfg.pull_item, g->cfg.prefix_min_len, g->cfg.pull_prefix, st))) {
+            bvg_free_dev(g);
+            return rc;
+        }
+        // the fused one-vector push: tiles of kFxT columns that read a row
+        // outside their window (an entry or an open interval's source row)
+        {
+            const int64_t tiles = (n + kFxT - 1) / kFxT;
+            std::vector<uint8_t> far((size_t)tiles, 0);
+            int64_t nfar = 0;
+            for (int64_t t = 0; t < tiles; t++) {
+                const int64_t a = t * kFxT, e = std::min<int64_t>(n, a + kFxT);
+                const int64_t w0 = std::max<int64_t>(0, a - kFxB), w1 = std::min<int64_t>(n, a + kFxT + kFxB);
+                bool f = false;
+                for (uint32_t q = L->colp[a]; q < L->colp[e] && !f; q++) {
+                    const int64_t k = L->tent[q] & kIdMask;
+                    f = k < w0 || k >= w1;
+                }
+                for (int64_t ct = a / kCarryTile; ct < (e + kCarryTile - 1) / kCarryTile && !f; ct++)
+                    for (uint32_t q = L->carry_ptr[ct]; q < L->carry_ptr[ct + 1] && !f; q++)
+                        f = (int64_t)L->carry[q] < w0 || (int64_t)L->carry[q] >= w1;
+                far[(size_t)t] = f ? 1 : 0;
+                nfar += f ? 1 : 0;
+            }
+            g->fx_tiles = tiles;
+            g->fx_far_tiles = nfar;
+            if ((rc = upload_vec(&g->tile_far, far, st, &g->bytes)) ||
+                (rc = dev_alloc((void**)&g->err, sizeof(unsigned int), nullptr))) {
+                bvg_free_dev(g);
+                return rc;
+            }
+            BVG_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(unsigned int), st));
+        }
+        // the point columns (the gather of every column block, and the fused
+        // kernel's compensated path)
+        if ((rc = ensure_points(g, st))) {
             bvg_free_dev(g);
             return rc;
         }
@@ -543,7 +625,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_far, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -620,6 +702,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
     out->col_block = g->cfg.col_block;
     out->pull_item = g->cfg.pull_item;
     out->push_points = g->cfg.push_points;
+    out->push_fused = g->cfg.push_fused;
     return BVG_OK;
 }
 
@@ -629,16 +712,18 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
         in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)) ||
         (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16) || in->push_points < -1 ||
-        in->push_points > 1)
+        in->push_points > 1 || in->push_fused < -1 || in->push_fused > 1)
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
                                          "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
-                                         "of two in [1, 32], pull_item in {4, 8, 16}, push_points in {-1,0,1}");
+                                         "of two in [1, 32], pull_item in {4, 8, 16}, push_points and push_fused "
+                                         "in {-1,0,1}");
     if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen ||
         (in->pull_prefix < 0 ? 1 : 0) != g->pull_built_auto) {
         int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, in->pull_prefix, nullptr);
         if (rc) return rc;
     }
-    if (in->gather_pdl != g->cfg.gather_pdl || in->push_points != g->cfg.push_points)
+    if (in->gather_pdl != g->cfg.gather_pdl || in->push_points != g->cfg.push_points ||
+        in->push_fused != g->cfg.push_fused)
         drop_pr_graph(g);  // the PageRank graph was captured with the old launch
     g->cfg.pull_tile = in->pull_tile;
     g->cfg.pull_prefix = in->pull_prefix;
@@ -647,6 +732,7 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     g->cfg.col_block = in->col_block;
     g->cfg.pull_item = in->pull_item;
     g->cfg.push_points = in->push_points;
+    g->cfg.push_fused = in->push_fused;
     return BVG_OK;
 }
 
@@ -696,6 +782,11 @@ static int spmv_xA(bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));
+        if (use_fused(g, kb)) {
+            launch_fused(g, x + c0, ld, y + c0, ld, st);
+            c0 += kb;
+            continue;
+        }
         if ((rc = ensure_z(g, kb))) return rc;
         if (want_points(g, kb) && (rc = ensure_points(g, st))) return rc;
         const int v = pick_v(kb, ld, c0, {x, y});
@@ -747,6 +838,22 @@ extern "C" int bvg_spmv_xA_host(const bvg_dev_graph* gc, const float* x_host, fl
     if (rc) return rc;
     BVG_CUDA_TRY(cudaMemcpyAsync(y_host, g->s.hy, need * sizeof(float), cudaMemcpyDeviceToHost, st));
     BVG_CUDA_TRY(cudaStreamSynchronize(st));
+    return BVG_OK;
+}
+
+extern "C" int bvg_device_check(const bvg_dev_graph* gc, void* stream) {
+    bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
+    if (!g) return fail(BVG_ERR_INVALID_ARG, "bvg_device_check: NULL graph");
+    if (!g->err) return BVG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int h = 0;
+    BVG_CUDA_TRY(cudaMemcpyAsync(&h, g->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    BVG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h) {
+        BVG_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(unsigned int), st));
+        BVG_CUDA_TRY(cudaStreamSynchronize(st));
+        return fail(BVG_ERR_TIMEOUT, "bvg_device_check: a bounded device wait ran out in an earlier launch");
+    }
     return BVG_OK;
 }
 
@@ -812,7 +919,8 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     // is captured once per configuration and replayed; the device state makes
     // updates past convergence or max_iter return at once.
     constexpr int kChunk = 8;
-    const int key[5] = {kb, v, dangling, p0 != nullptr, use_points(g, kb) ? 1 : 0};
+    const bool fused = use_fused(g, kb);
+    const int key[6] = {kb, v, dangling, p0 != nullptr, use_points(g, kb) ? 1 : 0, fused ? 1 : 0};
     if (g->s.pr_exec && (memcmp(key, g->s.pr_key, sizeof(key)) || g->s.pr_key_alpha != base.alpha ||
                          g->s.pr_key_ptr != g->s.q[0] || g->s.pr_key_z != g->s.z))
         drop_pr_graph(g);
@@ -823,6 +931,13 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
         pa.q_new = g->s.q[1 - par];
         pa.sc_prev = g->s.sc[par];
         pa.sc_new = g->s.sc[1 - par];
+        if (fused) {  // one kernel per update, a programmatic dependent of the previous one
+            const int64_t grid = (g->n + kFxT - 1) / kFxT;
+            TraceScope ts(g, "pr_fused", st);
+            launch_pdl(1, k_push_fx<1>, grid, kFxNT, st, fused_args(g, g->s.q[par], kb, g->inv_outdeg, nullptr, 0),
+                       pa);
+            return;
+        }
         BVG_KV_CASES(launch_chain, g, g->s.q[par], kb, g->inv_outdeg, g->s.z, kb, pst, st);
         BVG_KV_CASES(launch_gather_pr, g, g->s.z, kb, pa, st);
     };

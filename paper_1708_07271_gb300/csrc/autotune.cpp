@@ -95,7 +95,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                     if (!sc.eat('{')) return false;
                     std::string key;
                     CacheEntry e{};
-                    e.cfg = {512, -1, 32, 1, 32, 8, -1};
+                    e.cfg = {512, -1, 32, 1, 32, 8, -1, -1};
                     int fields = 0;
                     do {
                         std::string f;
@@ -113,6 +113,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                         else if (f == "col_block") e.cfg.col_block = (int32_t)v, fields++;
                         else if (f == "pull_item") e.cfg.pull_item = (int32_t)v, fields++;
                         else if (f == "push_points") e.cfg.push_points = (int32_t)v;  // absent in older files: -1
+                        else if (f == "push_fused") e.cfg.push_fused = (int32_t)v;    // absent in older files: -1
                         else if (f == "push_us") e.push_us = v;
                         else if (f == "pull_us") e.pull_us = v;
                     } while (sc.eat(','));
@@ -163,9 +164,9 @@ int write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
         std::snprintf(buf, sizeof buf,
                       "%s\n  {\"key\": \"%s\", \"pull_tile\": %d, \"pull_prefix\": %d, \"prefix_min_len\": %d, "
                       "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_points\": %d, "
-                      "\"push_us\": %.3f, \"pull_us\": %.3f}",
+                      "\"push_fused\": %d, \"push_us\": %.3f, \"pull_us\": %.3f}",
                       first ? "" : ",", json_escape(kv.first).c_str(), c.pull_tile, c.pull_prefix, c.prefix_min_len,
-                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, kv.second.push_us,
+                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, c.push_fused, kv.second.push_us,
                       kv.second.pull_us);
         o << buf;
         first = false;
@@ -326,13 +327,18 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
         release();
         return rc;
     }
+    // one right-hand side: the fused kernel too (which has no overlap or column layout to choose)
+    const int fz_lo = kpow == 1 ? 0 : -1, fz_hi = kpow == 1 ? 1 : -1;
+    for (int fz = fz_lo; fz <= fz_hi; fz++)
     for (int cb = kpow; cb >= std::max(1, kpow / 8); cb >>= 1) {
         for (int pdl = 0; pdl <= 1; pdl++)
             for (int pts = 0; pts <= 1; pts++) {
+                if (fz == 1 && (pdl == 0 || pts == 0)) continue;
                 bvg_launch_config c = base;
                 c.col_block = cb;
                 c.gather_pdl = pdl;
                 c.push_points = pts;
+                c.push_fused = fz;
                 double us = 0;
                 if ((rc = bvg_set_config(g, &c)) || (rc = time_op(push, st, t, &us))) {
                     bvg_set_config(g, &base);

@@ -15,7 +15,7 @@
 #include <new>
 #include <vector>
 
-#include "kernels.cuh"
+#include "fused.cuh"
 
 using namespace bvg;
 
@@ -37,33 +37,53 @@ struct BatchEntry {
     int64_t gather_tile0;  // first gather tile of this graph in the grid
     int points;            // 1: the gather reads point columns (no carry lists)
     const uint8_t* long_chunk;  // point columns: 128-column chunks holding a long column
+    int64_t fx_tile0;      // one-vector blocks of a graph on the fused kernel: its first tile there
+    FxArgs fx;             // that graph's fused-kernel arguments (x, y set per column block)
 };
 
-// Largest i with tab[i].tile0 <= blk (graphs with no rows are not in the table).
-template <bool CHAIN>
+// Largest i with tab[i].tile0 <= blk (graphs with no rows are not in the
+// table; a graph with no tiles in this grid shares its tile0 with the next
+// graph, which the search then picks). WHICH: 0 chain, 1 gather, 2 fused.
+template <int WHICH>
 __device__ __forceinline__ int find_graph(const BatchEntry* __restrict__ tab, int count, int64_t blk) {
     int lo = 0, hi = count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int64_t t0 = CHAIN ? tab[mid].chain_tile0 : tab[mid].gather_tile0;
+        const int64_t t0 = WHICH == 0 ? tab[mid].chain_tile0 : (WHICH == 1 ? tab[mid].gather_tile0 : tab[mid].fx_tile0);
         if (t0 <= blk) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
+// One-vector column block of the graphs that use the fused kernel: every
+// such graph's tiles in one grid, each CTA the same tile code as the
+// one-graph product (bit-identical results).
+__global__ void __launch_bounds__(kFxNT) k_fx_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
+                                                  int64_t c0) {
+    __shared__ __align__(16) FxSmem S;
+    const BatchEntry& e = tab[find_graph<2>(tab, count, blockIdx.x)];
+    FxArgs fa = e.fx;
+    fa.x = e.x + c0;
+    fa.ldx = ld;
+    fa.y = e.y + c0;
+    fa.ldy = ld;
+    PrArgs pa{};
+    fx_tile<0>((int64_t)blockIdx.x - e.fx_tile0, fa, pa, S);
+}
+
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_chain_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
                                                      int64_t c0) {
     asm volatile("griddepcontrol.launch_dependents;");
-    const BatchEntry e = tab[find_graph<true>(tab, count, blockIdx.x)];
+    const BatchEntry e = tab[find_graph<0>(tab, count, blockIdx.x)];
     chain_tile<KB, V>((int64_t)blockIdx.x - e.chain_tile0, e.desc, e.x + c0, ld, nullptr, e.z, KB, e.n);
 }
 
 template <int KB, int V>
 __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
                                                       int64_t c0) {
-    const BatchEntry e = tab[find_graph<false>(tab, count, blockIdx.x)];
+    const BatchEntry e = tab[find_graph<1>(tab, count, blockIdx.x)];
     PrArgs pa{};
     const int64_t blk = (int64_t)blockIdx.x - e.gather_tile0;
     if (e.points)
@@ -121,6 +141,7 @@ static void gather_grid_tiles(int64_t n, int64_t& t) { t = (n + GatherShape<KB, 
 template <int KB, int V>
 static void launch_batch_pair(const BatchEntry* tab, int count, int64_t chain_tiles, int64_t gather_tiles,
                               int64_t ld, int64_t c0, cudaStream_t st) {
+    if (chain_tiles == 0) return;  // every graph of this block runs on the fused kernel
     k_chain_batch<KB, V><<<(unsigned)chain_tiles, ChainShape<KB, V>::NT, 0, st>>>(tab, count, ld, c0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)gather_tiles);
@@ -306,13 +327,25 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
     b->ring_next = (r + 1) % bvg_batch::kRing;
     BVG_BATCH_TRY(cudaEventSynchronize(b->ring_ev[r]), "bvg_batch_spmv_xA");
     BatchEntry* h = b->host_ring + (size_t)r * cnt * b->table_blocks;
-    std::vector<int64_t> chain_tiles(nb), gather_tiles(nb);
+    std::vector<int64_t> chain_tiles(nb), gather_tiles(nb), fx_tiles(nb);
     for (int bi = 0; bi < nb; bi++) {
         const int kb = blocks[bi], v = vs[bi];
-        int64_t ct = 0, gt = 0, zoff = 0;
+        int64_t ct = 0, gt = 0, ft = 0, zoff = 0;
         for (int i = 0; i < cnt; i++) {
             const bvg_dev_graph* g = b->graphs[i];
             BatchEntry& e = h[(size_t)bi * cnt + i];
+            e.fx_tile0 = ft;
+            e.chain_tile0 = ct;
+            e.gather_tile0 = gt;
+            if (use_fused(g, kb)) {  // the same choice as the one-graph product
+                e.fx = fused_args(g, nullptr, 1, nullptr, nullptr, 1);
+                e.x = xs[b->slot[i]];
+                e.y = ys[b->slot[i]];
+                e.n = g->n;
+                ft += (g->n + kFxT - 1) / kFxT;
+                continue;
+            }
+            e.fx = FxArgs{};
             e.desc = g->desc;
             e.points = use_points(g, kb) ? 1 : 0;
             e.colp = e.points ? g->pcolp : g->colp;
@@ -337,6 +370,7 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
         }
         chain_tiles[bi] = ct;
         gather_tiles[bi] = gt;
+        fx_tiles[bi] = ft;
     }
     cudaStream_t st = (cudaStream_t)stream;
     // a call on another stream than the last one waits for it (the table is shared)
@@ -355,6 +389,9 @@ extern "C" int bvg_batch_spmv_xA(bvg_batch* b, const float* const* xs, float* co
         int64_t c0 = 0;
         for (int bi = 0; bi < nb; bi++) {
             const int kb = blocks[bi], v = vs[bi];
+            if (fx_tiles[bi] > 0)
+                k_fx_batch<<<(unsigned)fx_tiles[bi], kFxNT, 0, b->cap_stream>>>(b->table + (size_t)bi * cnt, cnt,
+                                                                               (int64_t)k, c0);
             BVG_BATCH_KV(launch_batch_pair, b->table + (size_t)bi * cnt, cnt, chain_tiles[bi], gather_tiles[bi],
                          (int64_t)k, c0, b->cap_stream);
             c0 += kb;

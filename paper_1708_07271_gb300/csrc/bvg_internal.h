@@ -49,6 +49,9 @@ inline uint32_t pack(uint32_t tag, uint32_t v) { return (tag << kIdBits) | v; }
 
 void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);
+// True when the allocation-failure hook (bvg_debug_fail_alloc) says that this
+// allocation checkpoint fails; the caller then reports BVG_ERR_OOM.
+bool inject_alloc_failure();
 
 // Host copy of the device layout (built once per host graph, see layout.cpp).
 struct HostLayout {
@@ -109,7 +112,10 @@ struct LaunchCfg {
     int pull_item = 8;          // pull: entries per work item (4, 8 or 16)
     int gather_pdl = 1;         // launch the gather so it overlaps the chain kernel's tail
     int col_block = 32;         // widest column block of a product (power of two <= 32)
-    int push_points = -1;       // x A gather over point columns: -1 for column blocks of at least 4, 0 never, 1 always
+    int push_points = -1;       // x A gather over point columns: -1 every column block (default), 0 never (event
+                                // columns), 1 always
+    int push_fused = -1;        // x A for one right-hand side in one fused kernel (fused.cuh): -1 when the graph
+                                // has locality (few tiles read rows outside their window), 0 never, 1 always
 };
 
 struct TuneInfo {
@@ -139,7 +145,7 @@ struct DevScratch {
     // CUDA graph of a chunk of PageRank updates, and what it was built for
     void* pr_exec = nullptr;            // cudaGraphExec_t
     void* cap_stream = nullptr;         // private stream the update graph is captured on
-    int pr_key[5] = {0, 0, 0, 0, 0};    // kb, v, dangling, has p0, point columns
+    int pr_key[6] = {0, 0, 0, 0, 0, 0}; // kb, v, dangling, has p0, point columns, fused update
     float pr_key_alpha = 0.f;
     const void* pr_key_ptr = nullptr;   // q[0] when captured
     const void* pr_key_z = nullptr;     // z when captured
@@ -199,6 +205,11 @@ struct bvg_dev_graph {
     uint32_t* ptitem = nullptr;     // start in pcent | (count - 1) << 30
     uint8_t* plong = nullptr;       // per kCarryTile columns: holds a column longer than kPointSlots + kLongColumn
     int64_t npcent = 0, nptitem = 0, pcol_bytes = 0;
+    // fused one-vector push (fused.cuh): per tile of its columns, 1 if an
+    // entry or a carry source lies outside the tile's row window
+    uint8_t* tile_far = nullptr;
+    int64_t fx_tiles = 0, fx_far_tiles = 0;
+    unsigned int* err = nullptr;    // device word: a bounded wait ran out (read and cleared by bvg_device_check)
     int pcol_state = 0;             // 0 not built, 1 built, -1 too many entries (the event columns serve)
     std::vector<uint32_t> host_rowp, host_ent;       // the difference rows, to rebuild the items
     int64_t bytes = 0;
@@ -216,6 +227,9 @@ namespace bvg {
 int ensure_points(bvg_dev_graph* g, void* stream);
 bool want_points(const bvg_dev_graph* g, int kb);
 bool use_points(const bvg_dev_graph* g, int kb);
+// A vector argument of a device product: not NULL, 4-byte aligned, and device
+// (or managed) memory of the graph's device; otherwise INVALID_ARG (api.cu).
+int check_vec(const bvg_dev_graph* g, const void* p, const char* what);
 }  // namespace bvg
 
 struct bvg_csr_graph {

@@ -25,6 +25,16 @@ void set_error(const char* fmt, ...) {
     g_last_error = buf;
 }
 
+// Allocation-failure injection for tests: the checkpoint reached when the
+// counter is 0 fails once (the counter then stays at -1, disabled).
+static std::atomic<int64_t> g_fail_alloc_after{-1};
+bool inject_alloc_failure() {
+    int64_t v = g_fail_alloc_after.load();
+    while (v >= 0)
+        if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
 int fail(int status, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -203,6 +213,11 @@ using namespace bvg;
 
 extern "C" const char* bvg_last_error(void) { return bvg::last_error(); }
 
+extern "C" int bvg_debug_fail_alloc(int64_t after) {
+    bvg::g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return BVG_OK;
+}
+
 extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                           const bvg_encode_params* params, bvg_host_graph** out) {
     if (!out) return fail(BVG_ERR_INVALID_ARG, "bvg_encode: out is NULL");
@@ -246,6 +261,7 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
     bvg_host_graph* g = new (std::nothrow) bvg_host_graph();
     if (!g) return fail(BVG_ERR_OOM, "bvg_encode: host allocation failed");
     try {
+        if (inject_alloc_failure()) throw std::bad_alloc();
         g->n = n;
         g->m = m;
         g->window = W;
@@ -429,11 +445,14 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
     return BVG_OK;
 }
 
-extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx) {
-    if (!g || !row_ptr || (g->m > 0 && !col_idx)) return fail(BVG_ERR_INVALID_ARG, "bvg_decode: NULL argument");
-    const int64_t n = g->n, m = g->m;
-    const int L = g->min_interval;
-    BitReader br(g->bits.data(), g->nbits);
+// Decodes a bitstream of n rows and m edges written with window W and minimum
+// interval length L into caller buffers row_ptr[n + 1], col_idx[m]. Every
+// count, offset and id read from the stream is checked against n, m, W and
+// the rows already decoded before it is used, so a damaged or truncated
+// stream gives BVG_ERR_CORRUPT and never an access outside the buffers.
+static int decode_stream(int64_t n, int64_t m, int W, int L, const uint64_t* bits, int64_t nbits,
+                         int64_t* row_ptr, int32_t* col_idx) {
+    BitReader br(bits, nbits);
     row_ptr[0] = 0;
     int64_t pos = 0;
     std::vector<int32_t> kept, ivs, res;
@@ -442,7 +461,7 @@ extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* co
         ivs.clear();
         res.clear();
         uint64_t off = br.gamma() - 1;
-        if (br.bad || (int64_t)off > i || off > (uint64_t)g->window)
+        if (br.bad || (int64_t)off > i || off > (uint64_t)W)
             return fail(BVG_ERR_CORRUPT, "bvg_decode: bad reference at row %lld", (long long)i);
         if (off > 0) {
             int64_t rr = i - (int64_t)off;
@@ -462,6 +481,8 @@ extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* co
                 }
                 if (br.bad || len < 0 || e + len > lr || (b > 0 && len < 1))
                     return fail(BVG_ERR_CORRUPT, "bvg_decode: bad copy block at row %lld", (long long)i);
+                if (keep && pos + (int64_t)kept.size() + len > m)
+                    return fail(BVG_ERR_CORRUPT, "bvg_decode: more edges than m at row %lld", (long long)i);
                 if (keep)
                     for (int64_t t = 0; t < len; t++) kept.push_back(col_idx[row_ptr[rr] + e + t]);
                 e += len;
@@ -476,6 +497,8 @@ extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* co
             int64_t len = (int64_t)br.gamma() + L - 1;
             if (br.bad || s0 < 0 || len < L || s0 + len > n)
                 return fail(BVG_ERR_CORRUPT, "bvg_decode: bad interval at row %lld", (long long)i);
+            if (pos + (int64_t)(kept.size() + ivs.size()) + len > m)
+                return fail(BVG_ERR_CORRUPT, "bvg_decode: more edges than m at row %lld", (long long)i);
             for (int64_t q = 0; q < len; q++) ivs.push_back((int32_t)(s0 + q));
             prev_end = s0 + len;
         }
@@ -485,6 +508,8 @@ extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* co
         for (uint64_t t = 0; t < nres; t++) {
             int64_t j = t == 0 ? i + unfold(br.delta() - 1) : prev + (int64_t)br.delta();
             if (br.bad || j < 0 || j >= n) return fail(BVG_ERR_CORRUPT, "bvg_decode: bad residual at row %lld", (long long)i);
+            if (pos + (int64_t)(kept.size() + ivs.size() + res.size()) + 1 > m)
+                return fail(BVG_ERR_CORRUPT, "bvg_decode: more edges than m at row %lld", (long long)i);
             res.push_back((int32_t)j);
             prev = j;
         }
@@ -500,8 +525,37 @@ extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* co
         pos += (int64_t)total;
         row_ptr[i + 1] = pos;
     }
-    if (pos != m || br.pos != g->nbits) return fail(BVG_ERR_CORRUPT, "bvg_decode: stream length mismatch");
+    if (pos != m || br.pos != nbits) return fail(BVG_ERR_CORRUPT, "bvg_decode: stream length mismatch");
     return BVG_OK;
+}
+
+extern "C" int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx) {
+    if (!g || !row_ptr || (g->m > 0 && !col_idx)) return fail(BVG_ERR_INVALID_ARG, "bvg_decode: NULL argument");
+    return decode_stream(g->n, g->m, g->window, g->min_interval, g->bits.data(), g->nbits, row_ptr, col_idx);
+}
+
+extern "C" int bvg_bitstream_get(const bvg_host_graph* g, uint64_t* words, int64_t cap_words, int64_t* nbits) {
+    if (!g || !nbits) return fail(BVG_ERR_INVALID_ARG, "bvg_bitstream_get: NULL argument");
+    *nbits = g->nbits;
+    if (!words) return BVG_OK;
+    const int64_t need = (g->nbits + 63) / 64;
+    if (cap_words < need) return fail(BVG_ERR_INVALID_ARG, "bvg_bitstream_get: %lld words needed", (long long)need);
+    for (int64_t t = 0; t < need; t++) words[t] = g->bits[t];
+    return BVG_OK;
+}
+
+extern "C" int bvg_decode_bits(int64_t n, int64_t m, const bvg_encode_params* params, const uint64_t* words,
+                               int64_t nbits, int64_t* row_ptr, int32_t* col_idx) {
+    if (n < 0 || m < 0 || nbits < 0 || !row_ptr || (m > 0 && !col_idx) || (nbits > 0 && !words))
+        return fail(BVG_ERR_INVALID_ARG, "bvg_decode_bits: bad sizes or NULL arrays");
+    const int W = params && params->window ? params->window : 7;
+    const int L = params && params->min_interval ? params->min_interval : 4;
+    if (W < 1 || W > kMaxWindow || L < 2) return fail(BVG_ERR_UNSUPPORTED, "bvg_decode_bits: window / min_interval");
+    try {
+        return decode_stream(n, m, W, L, words, nbits, row_ptr, col_idx);
+    } catch (const std::bad_alloc&) {
+        return fail(BVG_ERR_OOM, "bvg_decode_bits: host allocation failed");
+    }
 }
 
 extern "C" int bvg_stats(const bvg_host_graph* g, bvg_graph_stats* out) {

@@ -78,9 +78,19 @@ extern "C" int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float
                                    void* stream) {
     if (!g || !x || !y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_noalloc: NULL argument");
     if (k < 1 || ld < k) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_noalloc: need k >= 1 and ld >= k");
-    if ((uintptr_t)x % 4 || (uintptr_t)y % 4) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_noalloc: misaligned");
     if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_noalloc: x and y must not alias");
     if (g->n == 0) return BVG_OK;
+    // the kernels below run on the current device against the graph's
+    // structure arrays and the current device's scratch: both must be the
+    // graph's device, and x, y its memory (a host or foreign pointer is
+    // refused here rather than faulting in a kernel)
+    int cur = -1;
+    BVG_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != g->device)
+        return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_xA_noalloc: current device %d is not the graph's device %d", cur,
+                    g->device);
+    int rc0;
+    if ((rc0 = check_vec(g, x, "x")) || (rc0 = check_vec(g, y, "y"))) return rc0;
     if (g->n > kNoAllocScratchFloats)
         return fail(BVG_ERR_UNSUPPORTED,
                     "bvg_spmv_xA_noalloc: n = %lld exceeds the fixed scratch of %lld floats (n * column block "

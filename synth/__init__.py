@@ -153,6 +153,36 @@ def dyadic_rhs(n: int, k: int, seed: int, bits: int = 10) -> np.ndarray:
     return (np.floor(u * 16.0) / float(1 << bits)).astype(np.float32)
 
 
+def signed_rhs(n: int, k: int, seed: int) -> np.ndarray:
+    """x ~ U(-1, 1), row-major n x k, drawn in FP64 and rounded to FP32: signed
+    inputs, where sums along reference chains and across columns cancel."""
+    return (2.0 * uniform(n * k, seed) - 1.0).reshape(n, k).astype(np.float32)
+
+
+def wide_rhs(n: int, k: int, seed: int, span: int = 20) -> np.ndarray:
+    """Signed x whose magnitudes spread over 2^-span .. 2^span: x = s * m * 2^e
+    with s = +-1, m ~ U[1, 2) and e a uniform integer in [-span, span], each
+    from its own counter-based draw; rounded to FP32."""
+    u = uniform(3 * n * k, seed).reshape(3, n * k)
+    s = np.where(u[0] < 0.5, -1.0, 1.0)
+    m = 1.0 + u[1]
+    e = np.floor(u[2] * (2 * span + 1)).astype(np.int64) - span
+    return (s * np.ldexp(m, e)).reshape(n, k).astype(np.float32)
+
+
+def signed_dyadic_rhs(n: int, k: int, seed: int, bits: int = 10) -> np.ndarray:
+    """x = integer / 2^bits with integers in [-16, 15]: signed, and every partial
+    sum of such values is exact in FP32 and FP64."""
+    u = uniform(n * k, seed).reshape(n, k)
+    return ((np.floor(u * 32.0) - 16.0) / float(1 << bits)).astype(np.float32)
+
+
+def input_kind(kind: str, n: int, k: int, seed: int) -> np.ndarray:
+    """Right-hand sides by name: 'uniform' (U(0,1)), 'signed' (U(-1,1)),
+    'wide' (signed, magnitudes 2^-20 .. 2^20)."""
+    return {"uniform": rhs, "signed": signed_rhs, "wide": wide_rhs}[kind](n, k, seed)
+
+
 def seed_for(workload: int, graph: int = 0) -> int:
     return BASE_SEED + 1000 * workload + graph
 
@@ -217,6 +247,7 @@ def spec_dict(spec: GraphSpec) -> dict:
     return asdict(spec)
 
 
-__all__ = ["GraphSpec", "Graph", "copying_model", "uniform", "rhs", "nodes", "dyadic_rhs", "seed_for",
+__all__ = ["GraphSpec", "Graph", "copying_model", "uniform", "rhs", "nodes", "dyadic_rhs", "signed_rhs", "wide_rhs",
+           "signed_dyadic_rhs", "input_kind", "seed_for",
            "tiny_web", "web_862k", "web_7m4", "web_small", "web_18m5", "web_22m7", "social_5m4",
            "multi_graph_sizes", "build", "replace"]

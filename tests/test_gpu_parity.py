@@ -360,7 +360,7 @@ def test_push_event_and_point_columns(name, points):
     and dyadic inputs match it bit for bit."""
     g, hg, dg, ref = graph(name)
     old = bvg.bvg_get_config(dg)
-    bvg.bvg_set_config(dg, push_points=points)
+    bvg.bvg_set_config(dg, push_points=points, push_fused=0)
     try:
         for k in (1, 2, 8, 33):
             x = synth.rhs(g.n, k, synth.seed_for(1, 400 + k))
@@ -389,7 +389,7 @@ def test_pagerank_event_and_point_columns(points):
     onto either column layout: both converge to the oracle's vectors."""
     g, hg, dg, ref = graph("social_20k")
     old = bvg.bvg_get_config(dg)
-    bvg.bvg_set_config(dg, push_points=points)
+    bvg.bvg_set_config(dg, push_points=points, push_fused=0)
     try:
         p, it, res, rc = bvg.bvg_pagerank(dg, tol=1e-8, max_iter=1000)
         assert rc == bvg.BVG_OK and res[0] < 1e-8, (rc, it, res)
@@ -536,3 +536,31 @@ def test_other_windows_and_chain_bounds(window, max_chain):
     assert rc == bvg.BVG_OK and res[0] < 1e-8
     pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=2000)
     assert l1(p.cpu().numpy(), pstar) <= 1e-6
+
+
+@pytest.mark.parametrize("after", [0, 3, 9])
+def test_upload_allocation_failure(after):
+    """A device allocation of bvg_upload that fails (the allocation-failure
+    hook makes the given checkpoint fail) returns BVG_ERR_OOM and releases
+    what was allocated; the next upload of the same graph works and gives the
+    oracle's product."""
+    g, hg, _, ref = graph("tiny_web")
+    free0, _ = torch.cuda.mem_get_info()
+    bvg.bvg_debug_fail_alloc(after)
+    try:
+        with pytest.raises(bvg.BvgError) as e:
+            bvg.bvg_upload(hg)
+        assert e.value.status == bvg.BVG_ERR_OOM
+    finally:
+        bvg.bvg_debug_fail_alloc(-1)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 < 8 << 20  # nothing of the failed upload is kept (allocator granularity aside)
+    dg = bvg.bvg_upload(hg)
+    x = synth.rhs(g.n, 1, 5)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    bvg.bvg_spmv_xA(dg, xt, y)
+    x64 = x.astype(np.float64)
+    check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                oracle.bv_xA(g.row_ptr, g.col, ref, x64, absval=True), "xA after a failed upload")

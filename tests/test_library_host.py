@@ -126,3 +126,95 @@ def test_bits_per_edge_reported():
     assert 0 < st["bits_per_edge"] < 32
     assert st["bitstream_bits"] == pytest.approx(st["bits_per_edge"] * st["m"])
     assert st["device_bytes"] > 0
+
+
+# ---------------------------------------------------------------- damaged streams, allocation failure
+def _stream(name="tiny_web"):
+    g = dict(graphs())[name]
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    words, nbits = bvg.bvg_bitstream_get(hg)
+    return g, hg, words, nbits
+
+
+def test_decode_bits_round_trip():
+    """The exported bitstream decodes (through the caller-stream decoder) to
+    the encoded graph bit for bit."""
+    for name in ("tiny_web", "social", "empty"):
+        g, hg, words, nbits = _stream(name)
+        assert nbits == bvg.bvg_stats(hg)["bitstream_bits"]
+        rp, ci = bvg.bvg_decode_bits(g.n, g.m, words, nbits)
+        np.testing.assert_array_equal(rp, g.row_ptr)
+        np.testing.assert_array_equal(ci, g.col)
+
+
+def test_truncated_streams_are_corrupt():
+    """A stream cut short anywhere (or with extra bits) fails with
+    BVG_ERR_CORRUPT."""
+    g, hg, words, nbits = _stream()
+    rng = np.random.default_rng(1)
+    for cut in [nbits - 1, nbits - 7, nbits // 2, 64, 1, 0] + list(rng.integers(1, nbits, 20)):
+        # the decoder reads no bit past the stated length
+        with pytest.raises(bvg.BvgError) as e:
+            bvg.bvg_decode_bits(g.n, g.m, words, int(cut))
+        assert e.value.status == bvg.BVG_ERR_CORRUPT, cut
+    with pytest.raises(bvg.BvgError) as e:  # the stream followed by one spare bit
+        bvg.bvg_decode_bits(g.n, g.m, np.append(words, np.uint64(0)), nbits + 1)
+    assert e.value.status == bvg.BVG_ERR_CORRUPT
+
+
+def test_flipped_bits_are_caught_or_change_the_graph():
+    """Single flipped bits: the decoder returns BVG_ERR_CORRUPT or a CSR that
+    differs from the original; it never returns the original graph from a
+    damaged stream, and never reads or writes outside its buffers. Most flips
+    are caught outright."""
+    g, hg, words, nbits = _stream()
+    rng = np.random.default_rng(2)
+    caught = 0
+    positions = rng.choice(nbits, 300, replace=False)
+    for pos in positions:
+        w = words.copy()
+        w[pos // 64] ^= np.uint64(1 << (63 - int(pos) % 64))
+        try:
+            rp, ci = bvg.bvg_decode_bits(g.n, g.m, w, nbits)
+        except bvg.BvgError as e:
+            assert e.status == bvg.BVG_ERR_CORRUPT, pos
+            caught += 1
+            continue
+        assert not (np.array_equal(rp, g.row_ptr) and np.array_equal(ci, g.col)), pos
+    assert caught >= len(positions) // 2, caught
+
+
+def test_corrupt_stream_edge_cases():
+    """Hand-made streams: all zero bits (an endless unary prefix), a reference
+    offset past the window, a wrong edge count, a wrong row count."""
+    g, hg, words, nbits = _stream()
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_decode_bits(g.n, g.m, np.zeros_like(words), nbits)
+    assert e.value.status == bvg.BVG_ERR_CORRUPT
+    # row 0 written with reference offset 1 (gamma(2) = 010): no earlier row
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_decode_bits(2, 0, np.array([np.uint64(0b010 << 61)]), 3)
+    assert e.value.status == bvg.BVG_ERR_CORRUPT
+    for m in (g.m - 1, g.m + 1):
+        with pytest.raises(bvg.BvgError) as e:
+            bvg.bvg_decode_bits(g.n, m, words, nbits)
+        assert e.value.status == bvg.BVG_ERR_CORRUPT
+    with pytest.raises(bvg.BvgError) as e:
+        bvg.bvg_decode_bits(g.n - 1, g.m, words, nbits)
+    assert e.value.status == bvg.BVG_ERR_CORRUPT
+
+
+def test_allocation_failure_hook_gives_oom():
+    """The allocation-failure hook makes bvg_encode fail with BVG_ERR_OOM
+    once; the next call succeeds and encodes the same graph."""
+    g = dict(graphs())["tiny_web"]
+    bvg.bvg_debug_fail_alloc(0)
+    try:
+        with pytest.raises(bvg.BvgError) as e:
+            bvg.bvg_encode(g.row_ptr, g.col)
+        assert e.value.status == bvg.BVG_ERR_OOM
+    finally:
+        bvg.bvg_debug_fail_alloc(-1)
+    hg = bvg.bvg_encode(g.row_ptr, g.col)
+    rp, ci = bvg.bvg_decode(hg)
+    np.testing.assert_array_equal(ci, g.col)

@@ -60,3 +60,64 @@ def test_features_on_worked_example():
     wdeg = [8 / 15, 3 / 2, 9 / 20, 59 / 60, 59 / 60, 59 / 60, 5 / 6, 11 / 15]
     assert abs(sum(wdeg) - 7) < 1e-12
     np.testing.assert_allclose(f[:, 5], np.log1p(wdeg))
+
+
+def _golden_theta(g):
+    """The parameter vector of the hand-worked example (zeros elsewhere)."""
+    p = {name: np.zeros(shape) for name, shape in mlp.SIZES}
+    for u in range(3):
+        p["W1"][u] = [float(v) for v in g[f"W1_{u}"]]
+    p["b1"][:3] = [float(v) for v in g["b1_012"]]
+    for u in range(2):
+        p["W2"][u, :3] = [float(v) for v in g[f"W2_{u}_012"]]
+    p["b2"][:2] = [float(v) for v in g["b2_01"]]
+    p["w3"][:2] = [float(v) for v in g["w3_01"]]
+    p["b3"][0] = float(g["b3"][0])
+    return mlp.pack(p)
+
+
+def test_forward_on_hand_worked_example():
+    """The forward map against values worked out by hand: the bias of every
+    layer, ReLU before the bfloat16 rounding of the first hidden layer (a tie
+    rounded to even), the rounding of a weight (a tie), and the output bias
+    added after the output product; and the same network without rounding."""
+    g = load_golden("mlp_forward_n2.txt")
+    theta = _golden_theta(g)
+    f = np.array([[float(v) for v in g["f_A"]] + [0, 0], [float(v) for v in g["f_B"]] + [0, 0]])
+    yq, _ = mlp.forward(theta, f, quantize=True)
+    np.testing.assert_array_equal(yq, [float(v) for v in g["yhat_bf16"]])
+    y64, _ = mlp.forward(theta, f, quantize=False)
+    np.testing.assert_array_equal(y64, [float(v) for v in g["yhat_fp64"]])
+
+
+def test_forward_matches_torch_layers():
+    """The forward map against a network assembled from torch.nn layers in
+    FP64 (nn.Linear, nn.ReLU) from the same parameter layout, with torch's own
+    bfloat16 conversion for the rounding steps: random weights and inputs."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    theta = mlp.init(11).astype(np.float64)
+    theta += rng.normal(0, 0.05, theta.shape)  # nonzero biases too
+    f = rng.normal(0, 1.5, (300, 8))
+    p = mlp.unpack(theta)
+
+    def rnd(a):
+        return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
+
+    for quantize in (True, False):
+        q = rnd if quantize else (lambda a: torch.as_tensor(a, dtype=torch.float64))
+        l1 = torch.nn.Linear(mlp.NF, mlp.H).double()
+        l2 = torch.nn.Linear(mlp.H, mlp.H).double()
+        l3 = torch.nn.Linear(mlp.H, 1).double()
+        with torch.no_grad():
+            l1.weight.copy_(q(p["W1"]))
+            l1.bias.copy_(torch.as_tensor(p["b1"]))
+            l2.weight.copy_(q(p["W2"]))
+            l2.bias.copy_(torch.as_tensor(p["b2"]))
+            l3.weight.copy_(q(p["w3"]).reshape(1, -1))
+            l3.bias.copy_(torch.as_tensor(p["b3"]))
+            h1 = torch.nn.ReLU()(l1(torch.as_tensor(f[:, :mlp.NF])))
+            h1 = rnd(h1.numpy().astype(np.float32)) if quantize else h1
+            want = l3(torch.nn.ReLU()(l2(h1))).reshape(-1).numpy()
+        got, _ = mlp.forward(theta, f, quantize=quantize)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
