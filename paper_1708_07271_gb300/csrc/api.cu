@@ -236,7 +236,7 @@ bool want_points(const bvg_dev_graph* g, int kb) {
 // (graphs with locality); it needs the point columns for its compensated
 // path.
 bool use_fused(const bvg_dev_graph* g, int kb) {
-    if (kb != 1 || g->pcol_state != 1 || !g->tile_far) return false;
+    if (kb != 1 || g->pcol_state != 1 || !g->tile_win) return false;
     if (g->cfg.push_fused == 0) return false;
     return g->cfg.push_fused == 1 || g->fx_far_tiles * 20 <= g->fx_tiles;
 }
@@ -244,7 +244,6 @@ bool use_fused(const bvg_dev_graph* g, int kb) {
 FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* y,
                    int64_t ldy) {
     FxArgs fa{};
-    fa.meta = g->meta;
     fa.desc = g->desc;
     fa.colp = g->colp;
     fa.tent = g->tent;
@@ -252,7 +251,7 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     fa.carry = g->carry;
     fa.pcolp = g->pcolp;
     fa.pcent = g->pcent;
-    fa.tile_far = g->tile_far;
+    fa.tile_win = (const uint4*)g->tile_win;
     fa.x = x;
     fa.ldx = ldx;
     fa.rowscale = rowscale;
@@ -543,13 +542,14 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         g->ntitem = (int64_t)L->titem.size();
         g->ncarry = (int64_t)L->carry.size();
         g->fingerprint = layout_fingerprint(*L, n, hg->m);
-        // meta padded by 32 bytes: the fused kernel copies 16-byte aligned
-        // supersets of its row window
-        std::vector<uint8_t> meta_pad(L->meta);
-        meta_pad.resize((size_t)n + 32, 0);
-        if ((rc = upload_vec(&g->meta, meta_pad, st, &g->bytes)) || (rc = upload_vec(&g->desc, L->desc, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
+        // descendant masks and column entries padded (8 and 4 words): the
+        // fused kernel copies 16-byte aligned supersets of its ranges
+        std::vector<uint32_t> desc_pad(L->desc), tent_pad(L->tent);
+        desc_pad.resize(((size_t)n + 3) / 4 * 4 + 8, 0u);
+        tent_pad.resize((L->tent.size() + 3) / 4 * 4 + 4, 0u);
+        if ((rc = upload_vec(&g->meta, L->meta, st, &g->bytes)) || (rc = upload_vec(&g->desc, desc_pad, st, &g->bytes)) || (rc = upload_vec(&g->rowp, L->rowp, st, &g->bytes)) ||
             (rc = upload_vec(&g->ent, L->ent, st, &g->bytes)) || (rc = upload_vec(&g->colp, L->colp, st, &g->bytes)) ||
-            (rc = upload_vec(&g->tent, L->tent, st, &g->bytes)) ||
+            (rc = upload_vec(&g->tent, tent_pad, st, &g->bytes)) ||
             (rc = upload_vec(&g->titem_ptr, L->titem_ptr, st, &g->bytes)) ||
             (rc = upload_vec(&g->titem, L->titem, st, &g->bytes)) ||
             (rc = upload_vec(&g->carry_ptr, L->carry_ptr, st, &g->bytes)) ||
@@ -564,33 +564,51 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
-        // the fused one-vector push: tiles of kFxT columns that read a row
-        // outside their window (an entry or an open interval's source row)
+        // the fused one-vector push: each tile's row window, the span of the
+        // rows its entries and its open intervals come from (kFxW at most:
+        // a tile reading a wider span is flagged and keeps a window around
+        // its own columns)
         {
             const int64_t tiles = (n + kFxT - 1) / kFxT;
-            std::vector<uint8_t> far((size_t)tiles, 0);
+            std::vector<uint32_t> win((size_t)tiles * 4, 0u);
             int64_t nfar = 0;
             for (int64_t t = 0; t < tiles; t++) {
                 const int64_t a = t * kFxT, e = std::min<int64_t>(n, a + kFxT);
-                const int64_t w0 = std::max<int64_t>(0, a - kFxB), w1 = std::min<int64_t>(n, a + kFxT + kFxB);
-                bool f = false;
-                for (uint32_t q = L->colp[a]; q < L->colp[e] && !f; q++) {
+                int64_t lo = INT64_MAX, hi = -1;
+                for (uint32_t q = L->colp[a]; q < L->colp[e]; q++) {
                     const int64_t k = L->tent[q] & kIdMask;
-                    f = k < w0 || k >= w1;
+                    lo = std::min(lo, k);
+                    hi = std::max(hi, k);
                 }
-                for (int64_t ct = a / kCarryTile; ct < (e + kCarryTile - 1) / kCarryTile && !f; ct++)
-                    for (uint32_t q = L->carry_ptr[ct]; q < L->carry_ptr[ct + 1] && !f; q++)
-                        f = (int64_t)L->carry[q] < w0 || (int64_t)L->carry[q] >= w1;
-                far[(size_t)t] = f ? 1 : 0;
-                nfar += f ? 1 : 0;
+                for (int64_t ct = a / kCarryTile; ct < (e + kCarryTile - 1) / kCarryTile; ct++)
+                    for (uint32_t q = L->carry_ptr[ct]; q < L->carry_ptr[ct + 1]; q++) {
+                        lo = std::min<int64_t>(lo, L->carry[q]);
+                        hi = std::max<int64_t>(hi, L->carry[q]);
+                    }
+                uint32_t far = 0;
+                if (hi < 0) {  // nothing to read
+                    lo = a;
+                    hi = a;
+                } else if (hi + 1 - lo > kFxW) {
+                    far = 1;
+                    lo = std::max<int64_t>(0, std::min<int64_t>(a - (kFxW - kFxT) / 2, n - kFxW));
+                    hi = std::min<int64_t>(n, lo + kFxW) - 1;
+                }
+                win[(size_t)t * 4] = (uint32_t)lo;
+                win[(size_t)t * 4 + 1] = (uint32_t)(hi + 1);
+                win[(size_t)t * 4 + 2] = far;
+                nfar += far;
             }
             g->fx_tiles = tiles;
             g->fx_far_tiles = nfar;
-            if ((rc = upload_vec(&g->tile_far, far, st, &g->bytes)) ||
+            uint32_t* dwin = nullptr;
+            if ((rc = upload_vec(&dwin, win, st, &g->bytes)) ||
                 (rc = dev_alloc((void**)&g->err, sizeof(unsigned int), nullptr))) {
+                if (dwin) cudaFree(dwin);
                 bvg_free_dev(g);
                 return rc;
             }
+            g->tile_win = dwin;
             BVG_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(unsigned int), st));
         }
         // the point columns (the gather of every column block, and the fused
@@ -625,7 +643,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_far, g->err};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)

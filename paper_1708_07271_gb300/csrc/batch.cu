@@ -59,7 +59,7 @@ __device__ __forceinline__ int find_graph(const BatchEntry* __restrict__ tab, in
 // One-vector column block of the graphs that use the fused kernel: every
 // such graph's tiles in one grid, each CTA the same tile code as the
 // one-graph product (bit-identical results).
-__global__ void __launch_bounds__(kFxNT) k_fx_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
+__global__ void __launch_bounds__(kFxNT, 6) k_fx_batch(const BatchEntry* __restrict__ tab, int count, int64_t ld,
                                                   int64_t c0) {
     __shared__ __align__(16) FxSmem S;
     const BatchEntry& e = tab[find_graph<2>(tab, count, blockIdx.x)];

@@ -207,7 +207,7 @@ struct bvg_dev_graph {
     int64_t npcent = 0, nptitem = 0, pcol_bytes = 0;
     // fused one-vector push (fused.cuh): per tile of its columns, 1 if an
     // entry or a carry source lies outside the tile's row window
-    uint8_t* tile_far = nullptr;
+    void* tile_win = nullptr;       // uint4 per tile: first and end row of its window, 1 if it reads a row outside
     int64_t fx_tiles = 0, fx_far_tiles = 0;
     unsigned int* err = nullptr;    // device word: a bounded wait ran out (read and cleared by bvg_device_check)
     int pcol_state = 0;             // 0 not built, 1 built, -1 too many entries (the event columns serve)

@@ -4,29 +4,30 @@
 //
 // A CTA owns kFxT consecutive columns [a, a + kFxT) and computes, in shared
 // memory, everything its columns need:
-//   1. the reference offsets (meta) of a window of rows around the tile, one
-//      TMA bulk copy (cp.async.bulk, mbarrier completion), and x of those rows
-//      (plain coalesced loads);
+//   1. the descendant masks of a window of rows around the tile and the
+//      tile's column-major entries, by two TMA bulk copies (cp.async.bulk,
+//      mbarrier completion), and x of the window rows (coalesced loads);
 //   2. the chain weights z of the window rows;
-//   3. the entries of its columns, +-z_k into each column's sums;
+//   3. each thread's 4 columns: +-z_k of their entries into the column's
+//      point sum or event sum;
 //   4. the running interval sum and y_j, rounded once.
-// No global scratch, no second launch, no grid-wide synchronisation. Two
-// arithmetic paths, chosen per tile (the same choice in every thread):
+// No global scratch, no second launch, no atomics, no grid-wide
+// synchronisation. Two arithmetic paths, chosen per tile (the same choice in
+// every thread):
 //
 // Exact path (tiles whose x span at most about 20 binades: the rule is
 // below). Every value is an int64 multiple of 2^E, E chosen per CTA from the
 // largest exponent of the x the tile reads and the number of terms any of its
 // sums can hold, so that no sum overflows and every x converts exactly.
-//   - chain: every row adds its x into itself and its (at most max_chain)
-//     ancestors with shared-memory integer atomics: the pushes of the chain
-//     step, in any order, since integer addition is exact and associative;
-//   - entries: the tile's event-column entries (points, interval start and
-//     end events) dealt evenly over the threads (coalesced), each adding +-z_k
-//     into its column's point sum or event sum (integer atomics);
+//   - chain: each window row adds the x of its descendants (descendant mask),
+//     in integers, so the order does not matter and the sum is exact;
+//   - entries: points and interval start / end events of the thread's
+//     columns, +-z_k into the column's point or event sum;
 //   - the interval sum: an exact integer prefix of the event sums, each warp
 //     starting from the z of the intervals open at its first column (the carry
 //     list of its 128 columns);
-//   - y_j = P_j + I_j, exact, rounded once to FP32.
+//   - y_j = P_j + I_j, exact, rounded once to FP32 (integer rounding to
+//     nearest even, the scale folded into the exponent).
 // Every result is the exactly rounded sum; an interval that opened and closed
 // earlier in the tile leaves nothing behind in the running sum.
 //
@@ -38,11 +39,13 @@
 // an error-free two_sum. Errors stay within a few units in the last place of
 // the column's own terms.
 //
-// Entries whose source row lies outside the window (rare on graphs with
-// locality; flagged per tile at upload) take z from global memory: x of the
-// row and of its descendants (descendant mask). Such tiles first scan their
-// entries so that the exponent range covers those rows too.
+// Tiles that read a row outside their window (rare on graphs with locality;
+// flagged per tile at upload) take the compensated path, where such a row's
+// z comes from global memory: x of the row and of its descendants (its
+// descendant mask), added in the same order as the window rows'.
 #pragma once
+
+#include <cstddef>
 
 #include "kernels.cuh"
 
@@ -51,23 +54,23 @@ namespace bvg {
 constexpr int kFxT = 1024;                 // columns per CTA (a multiple of kCarryTile)
 constexpr int kFxNT = 256;                 // threads per CTA
 constexpr int kFxCPT = kFxT / kFxNT;       // consecutive columns per thread: a warp's 128 = one carry tile
-constexpr int kFxB = 192;                  // window rows before and after the tile
-constexpr int kFxW = kFxT + 2 * kFxB;      // window rows
-constexpr int kFxXR = (kFxW + kHalo + kFxNT - 1) / kFxNT;  // rows pushed per thread
-constexpr int kFxECap = 3584;              // entries per tile with their column expanded in shared memory
+constexpr int kFxW = 1792;                 // most window rows: the span of the rows a tile reads (set at upload)
+constexpr int kFxXR = (kFxW + kHalo + kFxNT - 1) / kFxNT;  // window rows whose x a thread loads
+constexpr int kFxECap = 3584;              // entries per tile staged in shared memory (more: read from global)
 constexpr long long kFxWaitCycles = 4000000000LL;  // bound of an mbarrier wait (about 2 s)
 static_assert(kFxCPT * 32 == kCarryTile, "a warp's columns form one carry tile");
 
 struct FxArgs {
-    const uint8_t* meta;        // n + 32 bytes (padded for the aligned bulk copy)
-    const uint32_t* desc;       // descendant masks
+    const uint32_t* desc;       // descendant masks, padded by 8 words (aligned bulk copies)
     const uint32_t* colp;       // event columns
-    const uint32_t* tent;
+    const uint32_t* tent;       // padded by 4 words (aligned bulk copies)
     const uint32_t* carry_ptr;
     const uint32_t* carry;
     const uint32_t* pcolp;      // point columns (compensated path)
     const uint32_t* pcent;
-    const uint8_t* tile_far;    // per tile of kFxT columns: an entry or carry source lies outside the window
+    const uint4* tile_win;      // per tile of kFxT columns: (first, end) of its row window, and 1 when a row it
+                                // reads lies outside (the rows an entry or open interval comes from span more
+                                // than kFxW rows)
     const float* x;
     int64_t ldx;
     const float* rowscale;      // x_i * rowscale_i (PageRank's 1/outdeg), or NULL
@@ -125,17 +128,6 @@ __device__ __forceinline__ long long fx_of(float v, int eshift) {
     return (b >> 31) ? -(long long)u : (long long)u;
 }
 
-// Exponent field of v (0..255; 255 marks Inf / NaN), and the field that fixes
-// the position of its lowest significand bit (1 for subnormals; 255 for
-// zero, which converts exactly at any scale).
-__device__ __forceinline__ uint32_t expo_of(float v) { return (__float_as_uint(v) >> 23) & 0xffu; }
-__device__ __forceinline__ uint32_t low_expo_of(float v) {
-    const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
-    if (b == 0u) return 255u;
-    const uint32_t f = b >> 23;
-    return f ? f : 1u;
-}
-
 __device__ __forceinline__ long long shfl_xor_ll(long long v, int o) {
     return (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
 }
@@ -147,28 +139,6 @@ template <bool COHERENT>
 __device__ __forceinline__ float fx_load_x(const FxArgs& fa, int64_t r) {
     float v = COHERENT ? __ldcg(fa.x + r * fa.ldx) : __ldg(fa.x + r * fa.ldx);
     if (fa.rowscale) v = __fmul_rn(v, __ldg(fa.rowscale + r));
-    return v;
-}
-
-// Exponent range (largest field, smallest low field) of the x a row outside
-// the window reads: its own and its descendants'.
-template <bool COHERENT>
-__device__ __forceinline__ void fx_far_range(const FxArgs& fa, int64_t k, uint32_t& emax, uint32_t& emin) {
-    float v = fx_load_x<COHERENT>(fa, k);
-    emax = max(emax, expo_of(v));
-    emin = min(emin, low_expo_of(v));
-    for (uint32_t m = __ldg(fa.desc + k); m; m &= m - 1) {
-        v = fx_load_x<COHERENT>(fa, k + __ffs(m));
-        emax = max(emax, expo_of(v));
-        emin = min(emin, low_expo_of(v));
-    }
-}
-
-// z_k of a row outside the window, exact path.
-template <bool COHERENT>
-__device__ __forceinline__ long long fx_far_z(const FxArgs& fa, int64_t k, int eshift) {
-    long long v = fx_of(fx_load_x<COHERENT>(fa, k), eshift);
-    for (uint32_t m = __ldg(fa.desc + k); m; m &= m - 1) v += fx_of(fx_load_x<COHERENT>(fa, k + __ffs(m)), eshift);
     return v;
 }
 
@@ -184,28 +154,50 @@ __device__ __forceinline__ float fl_far_z(const FxArgs& fa, int64_t k) {
 // Bits needed for c (ceil(log2(c + 1))).
 __device__ __forceinline__ int bits_for(uint32_t c) { return 32 - __clz(c); }
 
+// v * 2^E rounded once to FP32 (to nearest, ties to even): the integer's top
+// 24 bits rounded by the rest, the scale folded into the exponent. Results
+// outside the normal range are scaled in two steps (a second rounding only
+// for subnormal results).
+__device__ __forceinline__ float fx_to_float(long long v, int E) {
+    if (v == 0) return 0.f;
+    const uint32_t sgn = v < 0 ? 0x80000000u : 0u;
+    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)u);
+    u <<= lz;  // leading one at bit 63
+    uint32_t m = (uint32_t)(u >> 40);
+    const unsigned long long rem = u & 0xFFFFFFFFFFull, half = 1ull << 39;
+    if (rem > half || (rem == half && (m & 1u))) m++;
+    int p = 63 - lz;
+    if (m == (1u << 24)) {
+        m >>= 1;
+        p++;
+    }
+    const int e = p + E + 127;
+    if (e >= 1 && e <= 254) return __uint_as_float(sgn | ((uint32_t)e << 23) | (m & 0x7fffffu));
+    const int s = p + E, s1 = s / 2, s2 = s - s1;  // |s1|, |s2| <= 126 + 63
+    float f = __uint_as_float(sgn | (127u << 23) | (m & 0x7fffffu));
+    const float f1 = __uint_as_float((uint32_t)min(max(s1 + 127, 1), 254) << 23);
+    const float f2 = __uint_as_float((uint32_t)min(max(s2 + 127, 1), 254) << 23);
+    return __fmul_rn(__fmul_rn(f, f1), f2);
+}
+
 // Shared memory of a tile. The exact path's arrays and the compensated
 // path's arrays overlap (a tile takes one path).
 struct FxSmem {
     union {
-        unsigned long long z[kFxW];     // exact: chain weights
-        float zf[kFxW];                 // compensated: chain weights
+        long long v[kFxW + kHalo];  // exact: x of the window rows as integers, then their chain weights in place
+        struct {
+            float x[kFxW + kHalo];  // compensated: x of the window rows
+            float zf[kFxW];         //   and their chain weights
+        } c;
     } a;
-    union {
-        unsigned long long P[kFxT];     // exact: point sums
-        float x[kFxW + kHalo];          // compensated: x of the window
-    } b;
-    union {
-        unsigned long long D[kFxT];     // exact: event sums
-        uint32_t desc[kFxW];            // compensated: descendant masks of the window
-    } c;
-    uint16_t col[kFxECap];              // exact: the column (in the tile) of each entry
-    uint8_t meta[kFxW + kHalo + 48];
-    uint64_t bar;
+    alignas(16) uint32_t desc[kFxW + 8];    // descendant masks of the window (16-byte aligned superset)
+    alignas(16) uint32_t ent[kFxECap + 8];  // the tile's event-column entries (16-byte aligned superset), exact path
+    uint64_t bar[2];                // mbarriers: [0] masks, [1] entries
     unsigned int emax, emin, state;
 };
-static_assert(sizeof(float) * (kFxW + kHalo) <= sizeof(unsigned long long) * kFxT, "x fits the point sums");
-static_assert(sizeof(uint32_t) * kFxW <= sizeof(unsigned long long) * kFxT, "masks fit the event sums");
+static_assert(sizeof(float) * (2 * kFxW + kHalo) <= sizeof(long long) * (kFxW + kHalo), "x and z fit");
+static_assert(offsetof(FxSmem, desc) % 16 == 0 && offsetof(FxSmem, ent) % 16 == 0, "bulk-copy targets aligned");
 
 // One tile of the fused product. EPI = 0: store y. EPI = 1: PageRank update
 // epilogue (see PrArgs), x = the previous iterate scaled by 1/outdeg.
@@ -216,32 +208,38 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
     const int64_t n = fa.n;
     const int64_t a = blk * kFxT;
     const int64_t tend = a + kFxT < n ? a + kFxT : n;
-    const int64_t w0 = a > kFxB ? a - kFxB : 0;
-    const int64_t w1 = a + kFxT + kFxB < n ? a + kFxT + kFxB : n;
+    const uint4 win = __ldg(fa.tile_win + blk);
+    const int64_t w0 = win.x, w1 = win.y;  // the rows the tile reads: [w0, w1), at most kFxW
+    const bool far = win.z != 0u;
     const int64_t px1 = w1 + kHalo < n ? w1 + kHalo : n;  // rows whose x reaches the window's chain weights
-    const int W = (int)(w1 - w0);
-    const int64_t m0a = w0 & ~(int64_t)15, m1a = (px1 + 15) & ~(int64_t)15;
-    const int moff = (int)(w0 - m0a);
+    const int W = (int)(w1 - w0), PX = (int)(px1 - w0);
+    const int64_t d0a = w0 & ~(int64_t)3, d1a = (w1 + 3) & ~(int64_t)3;  // mask copy: 16-byte aligned rows
+    const int doff = (int)(w0 - d0a);
 
     if (tid == 0) {
-        mbar_init(&S.bar, 1);
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
         S.emax = 0u;
-        S.emin = 255u;
+        S.emin = 0xffffffffu;
         S.state = 0u;
     }
     __syncthreads();
-    if (tid == 0) {
-        const uint32_t bytes = (uint32_t)(m1a - m0a);
-        mbar_expect_tx(&S.bar, bytes);
-        bulk_g2s(S.meta, fa.meta + m0a, bytes, &S.bar);
-    }
     // structure reads that do not depend on x
+    const uint32_t E0 = __ldg(fa.colp + a), E1 = __ldg(fa.colp + tend);
+    const uint32_t e0a = E0 & ~3u, e1a = (E1 + 3u) & ~3u;
+    const bool staged = e1a - e0a <= (uint32_t)(kFxECap + 8);
+    if (tid == 0) {
+        const uint32_t bd = (uint32_t)((d1a - d0a) * 4);
+        mbar_expect_tx(&S.bar[0], bd);
+        bulk_g2s(S.desc, fa.desc + d0a, bd, &S.bar[0]);
+        const uint32_t be = staged ? (e1a - e0a) * 4u : 0u;
+        mbar_expect_tx(&S.bar[1], be);
+        if (be) bulk_g2s(S.ent, fa.tent + e0a, be, &S.bar[1]);
+    }
     const int64_t c0 = a + (int64_t)tid * kFxCPT;
     uint32_t cp[kFxCPT + 1];
 #pragma unroll
     for (int q = 0; q <= kFxCPT; q++) cp[q] = __ldg(fa.colp + (c0 + q < tend ? c0 + q : tend));
-    const uint32_t E0 = __ldg(fa.colp + a), E1 = __ldg(fa.colp + tend);
-    const bool far = __ldg(fa.tile_far + blk) != 0;
     const int64_t wc = a + (int64_t)warp * kCarryTile;  // this warp's first column
     uint32_t cr0 = 0, cr1 = 0, csrc = 0;
     if (wc < n) {
@@ -256,129 +254,128 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         // past convergence or max_iter the update does nothing (the state was
         // written by the previous update; the same value in every thread)
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) {
-            if (!mbar_wait(&S.bar, 0)) atomicExch(fa.err, 1u);  // no copy may stay in flight
+            const bool ok = mbar_wait(&S.bar[0], 0) && mbar_wait(&S.bar[1], 0);  // no copy may stay in flight
+            if (!ok) atomicExch(fa.err, 1u);
             return;
         }
     }
 
-    // x of the rows that reach the window, and their exponent range
+    // x of the rows that reach the window, and their exponent range (the
+    // largest and smallest nonzero magnitude, as bit patterns: their order is
+    // the order of the magnitudes)
     float xv[kFxXR];
-    uint32_t emax = 0u, emin = 255u;
+    uint32_t bmax = 0u, bmin = 0xffffffffu;
 #pragma unroll
     for (int i = 0; i < kFxXR; i++) {
-        const int64_t r = w0 + tid + i * kFxNT;
-        xv[i] = r < px1 ? fx_load_x<COH>(fa, r) : 0.f;
-        emax = max(emax, expo_of(xv[i]));
-        emin = min(emin, low_expo_of(xv[i]));
+        xv[i] = 0.f;
+        const int r = tid + i * kFxNT;
+        if (r >= PX) break;
+        xv[i] = fx_load_x<COH>(fa, w0 + r);
+        const uint32_t b = __float_as_uint(xv[i]) & 0x7fffffffu;
+        bmax = max(bmax, b);
+        bmin = min(bmin, b ? b : 0xffffffffu);
     }
-    if (far) {  // rows outside the window that this tile reads (rare)
-        for (uint32_t e = E0 + tid; e < E1; e += kFxNT) {
-            const int64_t k = id_of(__ldg(fa.tent + e));
-            if (k < w0 || k >= w1) fx_far_range<COH>(fa, k, emax, emin);
-        }
-        for (uint32_t e = ct0 + tid; e < ct1; e += kFxNT) {
-            const int64_t k = __ldg(fa.carry + e);
-            if (k < w0 || k >= w1) fx_far_range<COH>(fa, k, emax, emin);
-        }
-    }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    emin = __reduce_min_sync(0xffffffffu, emin);
+    bmax = __reduce_max_sync(0xffffffffu, bmax);
+    bmin = __reduce_min_sync(0xffffffffu, bmin);
     if (lane == 0) {
-        atomicMax(&S.emax, emax);
-        atomicMin(&S.emin, emin);
-    }
-    if (!mbar_wait(&S.bar, 0)) {
-        atomicExch(fa.err, 1u);
-        atomicOr(&S.state, 1u);
-        mbar_wait(&S.bar, 0);  // once more for the copy in flight
+        atomicMax(&S.emax, bmax);
+        atomicMin(&S.emin, bmin);
     }
     __syncthreads();
-    const uint32_t vmax = S.emax, vmin = S.emin;
+    // exponent fields: the largest (255: a non-finite value), and the one of
+    // the lowest significand bit of the smallest nonzero magnitude (255: no
+    // nonzero value)
+    const uint32_t vmax = S.emax >> 23;
+    const uint32_t vmin = S.emin == 0xffffffffu ? 255u : max(S.emin >> 23, 1u);
     // headroom: a chain weight sums at most kHalo + 1 values, any column or
     // prefix sum at most the tile's entries plus its carry sources
     const int hz = 6 + bits_for((E1 - E0) + (ct1 - ct0) + 1);
     const int eshift = 38 - hz - (int)vmax;  // a significand with exponent field f shifts left by f + eshift
-    // exact path: every nonzero x converts without loss, nothing is
-    // non-finite; the compensated path otherwise (and after a failed copy,
-    // whose outputs are NaN)
-    const bool exact = vmax < 255u && (vmin == 255u || (int)vmin + eshift >= 0) && S.state == 0u;
-    const bool failed = S.state != 0u;
+    // exact path: every source row lies in the window, every nonzero x
+    // converts without loss and nothing is non-finite; the compensated path
+    // otherwise
+    const bool exact = !far && vmax < 255u && (vmin == 255u || (int)vmin + eshift >= 0);
 
     float yv[kFxCPT];
     if (exact) {
-        for (int i = tid; i < kFxW; i += kFxNT) S.a.z[i] = 0ull;
-        for (int i = tid; i < kFxT; i += kFxNT) {
-            S.b.P[i] = 0ull;
-            S.c.D[i] = 0ull;
-        }
-        const bool expand = E1 - E0 <= (uint32_t)kFxECap;
-        if (expand) {  // the column (in the tile) of every entry
-#pragma unroll
-            for (int q = 0; q < kFxCPT; q++)
-                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) S.col[e - E0] = (uint16_t)(tid * kFxCPT + q);
-        }
-        __syncthreads();
-        // chain step: every row adds its x into itself and its ancestors
 #pragma unroll
         for (int i = 0; i < kFxXR; i++) {
-            int r = tid + i * kFxNT;  // relative to w0
-            if (w0 + r >= px1) break;
-            const long long v = fx_of(xv[i], eshift);
-            if (v == 0) continue;
-            if (r < W) atomicAdd(&S.a.z[r], (unsigned long long)v);
-#pragma unroll
-            for (int h = 0; h < kMaxChain; h++) {
-                const int off = S.meta[r + moff] & 7;
-                if (!off) break;
-                r -= off;
-                if (r < 0) break;  // ancestors below the window are not read
-                if (r < W) atomicAdd(&S.a.z[r], (unsigned long long)v);
-            }
+            const int r = tid + i * kFxNT;
+            if (r >= PX) break;
+            S.a.v[r] = fx_of(xv[i], eshift);
+        }
+        if (!mbar_wait(&S.bar[0], 0)) {
+            atomicExch(fa.err, 1u);
+            atomicOr(&S.state, 1u);
+            mbar_wait(&S.bar[0], 0);  // once more for the copy in flight
         }
         __syncthreads();
-        auto zfx = [&](int64_t k) -> long long {
-            const uint64_t rel = (uint64_t)(k - w0);
-            if (rel < (uint64_t)W) return (long long)S.a.z[rel];
-            return fx_far_z<COH>(fa, k, eshift);
+        // chain weights: each window row adds the x of its descendants
+        // (exact, in any order), held until every row has read, then stored
+        // in place
+        long long zr[kFxXR];
+#pragma unroll
+        for (int i = 0; i < kFxXR; i++) {
+            const int r = tid + i * kFxNT;
+            if (r >= W) break;
+            long long z = S.a.v[r];
+            for (uint32_t m = S.desc[r + doff]; m; m &= m - 1) z += S.a.v[r + __ffs(m)];
+            zr[i] = z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kFxXR; i++) {
+            const int r = tid + i * kFxNT;
+            if (r >= W) break;
+            S.a.v[r] = zr[i];
+        }
+        if (!mbar_wait(&S.bar[1], 0)) {
+            atomicExch(fa.err, 1u);
+            atomicOr(&S.state, 1u);
+            mbar_wait(&S.bar[1], 0);
+        }
+        __syncthreads();
+        // (the tile reads no row outside its window: z of any source row is
+        // in shared memory)
+        const long long* zv = S.a.v - w0;
+        // one entry w into (a, d): +-z of its source row into the sum of all
+        // entries and, for an interval event, into the event sum (branch-free)
+        auto add_entry = [&](uint32_t w, long long& sa, long long& d) {
+            long long z = zv[id_of(w)];
+            const long long neg = -(long long)((w >> kIdBits) & 1u);  // a dropped id, or an interval ending here
+            z = (z ^ neg) - neg;
+            sa += z;
+            d += z & -(long long)(w >> (kIdBits + 1));                // an interval start or end event
         };
-        // the entries: +-z into the point or the event sum of their column
-        if (expand) {
-            for (uint32_t e = E0 + tid; e < E1; e += kFxNT) {
-                const uint32_t w = __ldg(fa.tent + e);
-                long long z = zfx(id_of(w));
-                if (w & (1u << kIdBits)) z = -z;  // a dropped id, or an interval that ends here
-                unsigned long long* dst = (w & (2u << kIdBits)) ? S.c.D : S.b.P;
-                atomicAdd(dst + S.col[e - E0], (unsigned long long)z);
-            }
-        } else {  // too many entries to expand: each thread its own columns
+        // this thread's columns: the sum of all entries A_q = P_q + D_q and the
+        // event sum D_q (y_j = P_j + I_j = A_j + I_{j-1})
+        long long A[kFxCPT], D[kFxCPT], tot = 0;
+        if (staged) {
+            const uint32_t* ent = S.ent - e0a;
 #pragma unroll
             for (int q = 0; q < kFxCPT; q++) {
-                long long p = 0, d = 0;
-                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) {
-                    const uint32_t w = __ldg(fa.tent + e);
-                    long long z = zfx(id_of(w));
-                    if (w & (1u << kIdBits)) z = -z;
-                    if (w & (2u << kIdBits)) d += z;
-                    else p += z;
-                }
-                S.b.P[tid * kFxCPT + q] = (unsigned long long)p;
-                S.c.D[tid * kFxCPT + q] = (unsigned long long)d;
+                long long sa = 0, d = 0;
+                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) add_entry(ent[e], sa, d);
+                A[q] = sa;
+                D[q] = d;
+                tot += d;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kFxCPT; q++) {
+                long long sa = 0, d = 0;
+                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) add_entry(__ldg(fa.tent + e), sa, d);
+                A[q] = sa;
+                D[q] = d;
+                tot += d;
             }
         }
-        __syncthreads();
         // running interval sum: this warp's carry, then its columns in order
         long long run = 0;
-        if (cr0 + lane < cr1) run = zfx(csrc);
-        for (uint32_t e = cr0 + 32 + lane; e < cr1; e += 32) run += zfx(__ldg(fa.carry + e));  // rare: > 32 open
+        if (cr0 + lane < cr1) run = zv[csrc];
+        for (uint32_t e = cr0 + 32 + lane; e < cr1; e += 32) run += zv[__ldg(fa.carry + e)];  // rare: > 32 open
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) run += shfl_xor_ll(run, o);
-        long long P[kFxCPT], D[kFxCPT], tot = 0;
-#pragma unroll
-        for (int q = 0; q < kFxCPT; q++) {
-            P[q] = (long long)S.b.P[tid * kFxCPT + q];
-            D[q] = (long long)S.c.D[tid * kFxCPT + q];
-            tot += D[q];
-        }
         long long inc = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -386,36 +383,38 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             if (lane >= o) inc += t;
         }
         run += inc - tot;  // the warp's earlier threads
-        // 2^E as two normal factors (any E in range is then exact)
-        const int E = (int)vmax - 188 + hz;
-        const int Ea = E / 2, Eb = E - Ea;
-        const float fa_ = __uint_as_float((uint32_t)(Ea + 127) << 23), fb_ = __uint_as_float((uint32_t)(Eb + 127) << 23);
+        const int E = (int)vmax - 188 + hz;  // the integers count units of 2^E
 #pragma unroll
         for (int q = 0; q < kFxCPT; q++) {
+            yv[q] = fx_to_float(A[q] + run, E);
             run += D[q];
-            yv[q] = __fmul_rn(__fmul_rn(__ll2float_rn(P[q] + run), fa_), fb_);
         }
     } else {
-        // compensated path: x and the masks of the window into shared memory
+        // compensated path: x of the window into shared memory
 #pragma unroll
         for (int i = 0; i < kFxXR; i++) {
             const int r = tid + i * kFxNT;
-            if (w0 + r < px1) S.b.x[r] = xv[i];
+            if (r < PX) S.a.c.x[r] = xv[i];
         }
-        for (int r = tid; r < W; r += kFxNT) S.c.desc[r] = __ldg(fa.desc + w0 + r);
+        if (!mbar_wait(&S.bar[0], 0) || !mbar_wait(&S.bar[1], 0)) {
+            atomicExch(fa.err, 1u);
+            atomicOr(&S.state, 1u);
+            mbar_wait(&S.bar[0], 0);
+            mbar_wait(&S.bar[1], 0);
+        }
         __syncthreads();
         for (int r = tid; r < W; r += kFxNT) {  // chain weights, as the two-kernel push forms them
-            const uint32_t m1 = S.c.desc[r], m2 = m1 & (m1 - 1), m3 = m2 & (m2 - 1);
-            df acc = {S.b.x[r], 0.f};
-            acc = df_addf(acc, m1 ? S.b.x[r + __ffs(m1)] : 0.f);
-            acc = df_addf(acc, m2 ? S.b.x[r + __ffs(m2)] : 0.f);
-            for (uint32_t mm = m3; mm; mm &= mm - 1) acc = df_addf(acc, S.b.x[r + __ffs(mm)]);
-            S.a.zf[r] = df_val(acc);
+            const uint32_t m1 = S.desc[r + doff], m2 = m1 & (m1 - 1), m3 = m2 & (m2 - 1);
+            df acc = {S.a.c.x[r], 0.f};
+            acc = df_addf(acc, m1 ? S.a.c.x[r + __ffs(m1)] : 0.f);
+            acc = df_addf(acc, m2 ? S.a.c.x[r + __ffs(m2)] : 0.f);
+            for (uint32_t mm = m3; mm; mm &= mm - 1) acc = df_addf(acc, S.a.c.x[r + __ffs(mm)]);
+            S.a.c.zf[r] = df_val(acc);
         }
         __syncthreads();
         auto zfl = [&](int64_t k) -> float {
             const uint64_t rel = (uint64_t)(k - w0);
-            if (rel < (uint64_t)W) return S.a.zf[rel];
+            if (rel < (uint64_t)W) return S.a.c.zf[rel];
             return fl_far_z<COH>(fa, k);
         };
 #pragma unroll
@@ -424,12 +423,15 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             const uint32_t pb = __ldg(fa.pcolp + j), pe = __ldg(fa.pcolp + (c0 + q < tend ? j + 1 : j));
             float P = 0.f, Pe = 0.f;
             for (uint32_t e0 = pb; e0 < pe; e0 += kTailItem) {  // runs of kTailItem in FP32, joined exactly
+                uint32_t w4[kTailItem];
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) w4[t] = e0 + t < pe ? __ldg(fa.pcent + e0 + t) : 0u;
                 float sr = 0.f;
-                const uint32_t e1 = e0 + kTailItem < pe ? e0 + kTailItem : pe;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t w = __ldg(fa.pcent + e);
-                    const float sg = (w >> kIdBits) & 1u ? -1.f : 1.f;
-                    sr = __fmaf_rn(sg, zfl(id_of(w)), sr);
+#pragma unroll
+                for (int t = 0; t < kTailItem; t++) {
+                    if (e0 + t >= pe) break;
+                    const float sg = (w4[t] >> kIdBits) & 1u ? -1.f : 1.f;
+                    sr = __fmaf_rn(sg, zfl(id_of(w4[t])), sr);
                 }
                 float s_, e_;
                 two_sum(P, sr, s_, e_);
@@ -439,6 +441,7 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             yv[q] = __fadd_rn(P, Pe);
         }
     }
+    const bool failed = S.state != 0u;  // a copy ran out of time: NaN outputs
 
     float Ssum = 0.f, Rs = 0.f, Dg = 0.f, dl = 0.f;
     if constexpr (EPI == 1) dl = (float)__ldcg(pa.sc_prev + 1);
@@ -474,7 +477,7 @@ bool use_fused(const bvg_dev_graph* g, int kb);
 FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* y, int64_t ldy);
 
 template <int EPI>
-__global__ void __launch_bounds__(kFxNT) k_push_fx(FxArgs fa, PrArgs pa) {
+__global__ void __launch_bounds__(kFxNT, 6) k_push_fx(FxArgs fa, PrArgs pa) {
     __shared__ __align__(16) FxSmem S;
     if constexpr (EPI == 1) asm volatile("griddepcontrol.launch_dependents;");
     fx_tile<EPI>(blockIdx.x, fa, pa, S);
