@@ -46,19 +46,24 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-graph batch leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-krhs", action="store_true", help="skip the k = 32 leg")
-    ap.add_argument("--config3", action="store_true",
-                    help="run the k = 32 leg on the web-like graph n = 7.4 M, 194 M edges")
+    ap.add_argument("--config3", action="store_true", help="(the default) the k = 32 leg on the web-like graph "
+                                                           "n = 7.4 M, 194 M edges")
+    ap.add_argument("--no-config3", action="store_true", help="run the k = 32 leg on the bench graph instead")
     ap.add_argument("--no-variants", action="store_true", help="skip the A^T-pull and social-graph legs")
-    ap.add_argument("--config5", action="store_true",
-                    help="run the BV-vs-CSR crossover on the social graph n = 5.4 M and the web graph n = 22.7 M "
-                         "(k = 8)")
+    ap.add_argument("--config5", action="store_true", help="(the default) the BV-vs-CSR crossover on the social "
+                                                           "graph n = 5.4 M and the web graph n = 22.7 M (k = 8)")
+    ap.add_argument("--no-config5", action="store_true", help="skip the n = 5.4 M and n = 22.7 M graphs")
+    ap.add_argument("--no-high-compression", action="store_true", help="skip the m/m' >= 5 web graph leg")
     ap.add_argument("--window-sweep", action="store_true",
                     help="encode the bench graph with window W in {1, 3, 5, 7} and chain bound R in {1, 2, 3}: "
                          "compression and both products' speed")
     ap.add_argument("--config4", action="store_true",
                     help="train the warm-start network on 200 generated graphs (n log-uniform in [1e5, 1e6]) and "
                          "evaluate it on the web-like graph n = 18.5 M")
-    return ap.parse_args()
+    a = ap.parse_args()
+    a.config3 = not a.no_config3
+    a.config5 = not a.no_config5
+    return a
 
 
 def workload_spec():
@@ -337,11 +342,20 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
         r = {"n": gs.n, "m": gs.m, "k": k, "m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
              "m_over_words": st["m"] / max(1, st["words"])}
         for name, fn in (("bv_xA", lambda: bvg.bvg_spmv_xA(ds, xs, ys)), ("csr_xA", lambda: bvg.bvg_csr_spmv_xA(cs, xs, ys)),
-                         ("bv_Ax", lambda: bvg.bvg_spmv_Ax(ds, xs, ys)), ("csr_Ax", lambda: bvg.bvg_csr_spmv_Ax(cs, xs, ys))):
+                         ("cusparse_xA", lambda: bvg.bvg_csr_cusparse_xA(cs, xs, ys)),
+                         ("bv_Ax", lambda: bvg.bvg_spmv_Ax(ds, xs, ys)), ("csr_Ax", lambda: bvg.bvg_csr_spmv_Ax(cs, xs, ys)),
+                         ("cusparse_Ax", lambda: bvg.bvg_csr_cusparse_Ax(cs, xs, ys))):
             r[name + "_gedges_s"] = gd(gs.m * k, warm_timed(fn))
+        r["bv_over_best_csr_xA"] = r["bv_xA_gedges_s"] / max(r["csr_xA_gedges_s"], r["cusparse_xA_gedges_s"])
+        r["bv_over_best_csr_Ax"] = r["bv_Ax_gedges_s"] / max(r["csr_Ax_gedges_s"], r["cusparse_Ax_gedges_s"])
+        del ds, cs
         return r
 
     out["social"] = crossover(synth.replace(synth.social_5m4(), n=g.n), 1)
+    if not args.no_high_compression:
+        out["high_compression"] = crossover(synth.web_862k_hc(), 1)
+        out["high_compression"]["graph"] = ("web-like copying model, exact copies with probability 0.93 "
+                                            "(m/m' >= 5, the paper's 'compressed 5x or more' regime)")
     if args.config5:
         out["social_5m4"] = crossover(synth.social_5m4(), 1)
         out["web_22m7_k8"] = crossover(synth.web_22m7(), 8)
@@ -634,8 +648,10 @@ def run_bv(args):
         return timed(fn, args.steps)
 
     csr_ms = warm_timed(lambda: bvg.bvg_csr_spmv_xA(cg, x, y))
+    cusp_ms = warm_timed(lambda: bvg.bvg_csr_cusparse_xA(cg, x, y))
     pull_ms = warm_timed(lambda: bvg.bvg_spmv_Ax(dg, x, y))
     csr_ax_ms = warm_timed(lambda: bvg.bvg_csr_spmv_Ax(cg, x, y))
+    cusp_ax_ms = warm_timed(lambda: bvg.bvg_csr_cusparse_Ax(cg, x, y))
     gedges = lambda ms: g.m * k * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
 
     # ---- end to end through the C ABI with host buffers (pinned)
@@ -691,8 +707,12 @@ def run_bv(args):
                              "buffer (the write's dirty lines reach HBM before the step)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-            "csr_gedges_s": gedges(csr_ms), "bv_over_csr": float(np.sum(csr_ms) / np.sum(step_ms)),
+            "csr_gedges_s": gedges(csr_ms), "cusparse_gedges_s": gedges(cusp_ms),
+            "bv_over_csr": float(np.sum(csr_ms) / np.sum(step_ms)),
+            "bv_over_best_csr": float(min(np.sum(csr_ms), np.sum(cusp_ms)) / np.sum(step_ms)),
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
+            "cusparse_Ax_gedges_s": gedges(cusp_ax_ms),
+            "pull_over_best_csr": float(min(np.sum(csr_ax_ms), np.sum(cusp_ax_ms)) / np.sum(pull_ms)),
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
             "k_rhs": krhs, "batch": batch, "warm_start": warm, "variants": variants, "window_sweep": wsweep,

@@ -507,6 +507,15 @@ int bvg_csr_upload(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, vo
 int bvg_csr_spmv_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 /* y = x A over the CSR of A^T (same kernel, transposed pattern). */
 int bvg_csr_spmv_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+/* The same two products by the vendor library (cusparseSpMV for one
+ * right-hand side with ld = 1, cusparseSpMM on the row-major n x k block
+ * otherwise; values 1.0f, 32-bit indices, the CSR of A^T for x A): the second
+ * uncompressed baseline of the comparison of Sec. 5. The first call creates
+ * the library handle and descriptors, and a call may grow a workspace
+ * (synchronising `stream`). Asynchronous otherwise. Errors: INVALID_ARG,
+ * UNSUPPORTED (2^31 edges or more), OOM, CUDA. */
+int bvg_csr_cusparse_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+int bvg_csr_cusparse_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
 /* -------------------------------------------------------------- tracing */
 

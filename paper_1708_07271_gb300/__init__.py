@@ -42,7 +42,7 @@ EXPORTED = [
     "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
     "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
     "bvg_biclique_gather_lists", "bvg_bitstream_get", "bvg_decode_bits", "bvg_debug_fail_alloc",
-    "bvg_device_check",
+    "bvg_device_check", "bvg_csr_cusparse_Ax", "bvg_csr_cusparse_xA",
 ]
 
 
@@ -192,6 +192,8 @@ def load(build_if_needed: bool = True):
             "bvg_decode_bits": ([_I64, _I64, ctypes.POINTER(EncodeParams), _P, _I64, _P, _P], ctypes.c_int),
             "bvg_debug_fail_alloc": ([_I64], ctypes.c_int),
             "bvg_device_check": ([_P, _P], ctypes.c_int),
+            "bvg_csr_cusparse_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_csr_cusparse_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -479,6 +481,24 @@ def bvg_csr_spmv_xA(g: CsrGraph, x, y, stream=None):
     _fp32_cuda(x, y)
     k, ld = _km(x, g.n)
     _check(load().bvg_csr_spmv_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_csr_spmv_xA")
+    return y
+
+
+def bvg_csr_cusparse_Ax(g: CsrGraph, x, y, stream=None):
+    """y = A x^T by cuSPARSE (the vendor-library baseline)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    _check(load().bvg_csr_cusparse_Ax(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
+           "bvg_csr_cusparse_Ax")
+    return y
+
+
+def bvg_csr_cusparse_xA(g: CsrGraph, x, y, stream=None):
+    """y = x A by cuSPARSE on the CSR of A^T (the vendor-library baseline)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, g.n)
+    _check(load().bvg_csr_cusparse_xA(g.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
+           "bvg_csr_cusparse_xA")
     return y
 
 

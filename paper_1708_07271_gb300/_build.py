@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if log:
                 sys.stderr.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [_nvcc(), *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-lcudart", "-lpthread"]
+    link = [_nvcc(), *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-lcusparse", "-lcudart", "-lpthread"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}\n{r.stderr}")

@@ -239,4 +239,18 @@ struct bvg_csr_graph {
     int32_t* ci = nullptr;
     int64_t* rpt = nullptr; // CSR of A^T
     int32_t* cit = nullptr;
+    // rows longer than the hub threshold, summed by a whole CTA each
+    int32_t* hub = nullptr;  // rows of A
+    int32_t* hubt = nullptr; // rows of A^T
+    int64_t nhub = 0, nhubt = 0;
+    // cuSPARSE: 32-bit row offsets of A and A^T, values 1.0f, handle and
+    // descriptors (created on the first cuSPARSE product), workspace
+    int32_t* rp32 = nullptr;
+    int32_t* rpt32 = nullptr;
+    float* ones = nullptr;
+    void* sp_handle = nullptr;
+    void* sp_mat = nullptr;
+    void* sp_matt = nullptr;
+    void* sp_buf = nullptr;
+    size_t sp_buf_bytes = 0;
 };

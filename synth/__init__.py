@@ -204,6 +204,14 @@ def web_862k(seed: int | None = None) -> GraphSpec:
                      extra_mean=0.35, fresh_mean=17.0, q_run=0.5, gap_mean=24.0)
 
 
+def web_862k_hc(seed: int | None = None) -> GraphSpec:
+    """n = 862,664, ~19 M edges, compressed more than 5x in nnz(A') (Table 1's
+    m / m' measure): rows copy a prototype exactly (fidelity 1) with
+    probability 0.93 and add few extra successors."""
+    return GraphSpec(n=862_664, seed=seed_for(2, 50) if seed is None else seed, p_copy=0.93, fidelity=1.0,
+                     extra_mean=0.03, fresh_mean=23.0, q_run=0.5, gap_mean=24.0)
+
+
 def web_7m4(seed: int | None = None) -> GraphSpec:
     """n = 7.4 M, ~194 M edges (batched personalized PageRank)."""
     return GraphSpec(n=7_400_000, seed=seed_for(3) if seed is None else seed, p_copy=0.8, fidelity=0.985,
@@ -249,5 +257,5 @@ def spec_dict(spec: GraphSpec) -> dict:
 
 __all__ = ["GraphSpec", "Graph", "copying_model", "uniform", "rhs", "nodes", "dyadic_rhs", "signed_rhs", "wide_rhs",
            "signed_dyadic_rhs", "input_kind", "seed_for",
-           "tiny_web", "web_862k", "web_7m4", "web_small", "web_18m5", "web_22m7", "social_5m4",
+           "tiny_web", "web_862k", "web_862k_hc", "web_7m4", "web_small", "web_18m5", "web_22m7", "social_5m4",
            "multi_graph_sizes", "build", "replace"]

@@ -126,6 +126,34 @@ def test_csr_baseline_matches_oracle():
         np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64), rtol=1e-5)
 
 
+@pytest.mark.parametrize("engine", ["own", "cusparse"])
+def test_csr_baselines_with_hub_rows(engine):
+    """Both uncompressed baselines (the hand-written CSR kernel, with hub rows
+    summed by a whole CTA, and cuSPARSE) against the oracle on a graph with
+    hub rows and hub columns of thousands of entries, k in {1, 8, 33}."""
+    g = hub_graph()
+    rows = [np.unique(np.concatenate([g.col[g.row_ptr[i]:g.row_ptr[i + 1]],
+                                      np.arange(0, g.n, 1, dtype=np.int32) if i in (3, 1999) else
+                                      np.zeros(0, np.int32)])) for i in range(g.n)]
+    cols_hub = [np.unique(np.append(r, 17)).astype(np.int32) for r in rows]  # column 17 holds every row
+    rp = np.zeros(g.n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in cols_hub])
+    ci = np.concatenate(cols_hub)
+    cg = bvg.bvg_csr_upload(rp, ci)
+    xa = bvg.bvg_csr_spmv_xA if engine == "own" else bvg.bvg_csr_cusparse_xA
+    ax = bvg.bvg_csr_spmv_Ax if engine == "own" else bvg.bvg_csr_cusparse_Ax
+    for k in (1, 8, 33):
+        x = synth.rhs(g.n, k, 40 + k)
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.full_like(xt, float("nan"))
+        xa(cg, xt, y)
+        np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_xA(rp, ci, x64), rtol=1e-5)
+        y.fill_(float("nan"))
+        ax(cg, xt, y)
+        np.testing.assert_allclose(y.cpu().numpy(), oracle.csr_Ax(rp, ci, x64), rtol=1e-5)
+
+
 @pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("k", [1, 3, 32])
 def test_host_buffer_product(pinned, k):
