@@ -329,7 +329,22 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
     out = {"xA_push_on_A_gedges_s": gd(g.m, push), "xA_pull_on_AT_gedges_s": gd(g.m, pullT),
            "AT_m_over_words": stT["m"] / max(1, stT["words"]), "max_rel_diff_push_vs_pull": rel}
 
-    def crossover(spec, k):
+    def biclique_leg(gs, xs, ys, k):
+        """The biclique format (Sec. 6) on the same graph: its words and both
+        products on the device."""
+        t0 = time.perf_counter()
+        bd = bvg.bvg_biclique_upload(gs.row_ptr, gs.col)
+        enc_s = time.perf_counter() - t0
+        r = {"words": bd.info["words"], "m_over_words": gs.m / max(1, bd.info["words"]),
+             "bicliques": bd.info["bicliques"], "edges_in_bicliques": bd.info["biclique_edges"],
+             "encode_upload_seconds": enc_s}
+        for name, fn in (("xA", lambda: bvg.bvg_biclique_spmv_xA(bd, xs, ys)),
+                         ("Ax", lambda: bvg.bvg_biclique_spmv_Ax(bd, xs, ys))):
+            r[name + "_gedges_s"] = gd(gs.m * k, warm_timed(fn))
+        del bd
+        return r
+
+    def crossover(spec, k, with_biclique=False):
         gs = synth.copying_model(spec)
         hs = bvg.bvg_encode(gs.row_ptr, gs.col)
         st = bvg.bvg_stats(hs)
@@ -349,9 +364,13 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
         r["bv_over_best_csr_xA"] = r["bv_xA_gedges_s"] / max(r["csr_xA_gedges_s"], r["cusparse_xA_gedges_s"])
         r["bv_over_best_csr_Ax"] = r["bv_Ax_gedges_s"] / max(r["csr_Ax_gedges_s"], r["cusparse_Ax_gedges_s"])
         del ds, cs
+        if with_biclique:
+            r["biclique"] = biclique_leg(gs, xs, ys, k)
         return r
 
-    out["social"] = crossover(synth.replace(synth.social_5m4(), n=g.n), 1)
+    out["social"] = crossover(synth.replace(synth.social_5m4(), n=g.n), 1, with_biclique=True)
+    xb = torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
+    out["biclique_bench_graph"] = biclique_leg(g, xb, torch.empty_like(xb), 1)
     if not args.no_high_compression:
         out["high_compression"] = crossover(synth.web_862k_hc(), 1)
         out["high_compression"]["graph"] = ("web-like copying model, exact copies with probability 0.93 "

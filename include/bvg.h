@@ -496,6 +496,26 @@ int bvg_biclique_gather_lists(const bvg_biclique* b, int64_t* row_ptr2, int32_t*
                               int32_t* col_bic, int64_t* rt_ptr, int32_t* rt_row);
 void bvg_free_biclique(bvg_biclique* b);
 
+/* The biclique products on the device. bvg_biclique_upload copies a
+ * decomposition and its gather lists to the current device (synchronising
+ * `stream`); the decomposition may be freed afterwards. Errors: INVALID_ARG,
+ * UNSUPPORTED (2^32 list entries or more), OOM, CUDA. */
+typedef struct bvg_biclique_dev bvg_biclique_dev;
+int bvg_biclique_upload(const bvg_biclique* b, void* stream, bvg_biclique_dev** out);
+/* y = A x^T by the steps of Sec. 6: c_r = sum_{j in C_r} x_j for every
+ * biclique, then y_i = sum of c_r over the bicliques whose S holds i, plus x_j
+ * over row i's residual edges (a gather per row, no atomics; every sum
+ * compensated and rounded once). x, y: device n x k, leading dimension ld.
+ * The first call with a wider column block grows a per-biclique scratch
+ * (synchronising `stream`); asynchronous otherwise. Errors: INVALID_ARG, OOM,
+ * CUDA. */
+int bvg_biclique_spmv_Ax(const bvg_biclique_dev* d, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+/* y = x A, the transpose of the same steps: d_r = sum_{i in S_r} x_i, then
+ * y_j = sum of d_r over the bicliques whose C holds j, plus x_i over the
+ * residual edges into column j. As bvg_biclique_spmv_Ax otherwise. */
+int bvg_biclique_spmv_xA(const bvg_biclique_dev* d, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+void bvg_free_biclique_dev(bvg_biclique_dev* d);
+
 /* --------------------------------------------------- plain CSR baseline */
 
 /* Device CSR of A and of A^T built from a host CSR (same input rules as

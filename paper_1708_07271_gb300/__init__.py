@@ -42,7 +42,8 @@ EXPORTED = [
     "bvg_autotune_cache_store", "bvg_pull_items_size", "bvg_pull_items_fill", "bvg_point_cols_size",
     "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
     "bvg_biclique_gather_lists", "bvg_bitstream_get", "bvg_decode_bits", "bvg_debug_fail_alloc",
-    "bvg_device_check", "bvg_csr_cusparse_Ax", "bvg_csr_cusparse_xA",
+    "bvg_device_check", "bvg_csr_cusparse_Ax", "bvg_csr_cusparse_xA", "bvg_biclique_upload",
+    "bvg_biclique_spmv_Ax", "bvg_biclique_spmv_xA", "bvg_free_biclique_dev",
 ]
 
 
@@ -194,6 +195,10 @@ def load(build_if_needed: bool = True):
             "bvg_device_check": ([_P, _P], ctypes.c_int),
             "bvg_csr_cusparse_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_csr_cusparse_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_biclique_upload": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+            "bvg_biclique_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_biclique_spmv_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_free_biclique_dev": ([_P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -798,3 +803,53 @@ def bvg_biclique_encode(row_ptr, col, passes: int = 8, min_rows: int = 2, min_co
     out["rt_row"] = out["rt_row"][:info.residual]
     out.update({f: getattr(info, f) for f, _ in BicliqueInfo._fields_})
     return out
+
+
+class BicliqueDev:
+    """Device handle of a biclique decomposition (freed with the object)."""
+
+    def __init__(self, ptr, n: int, m: int, info: dict):
+        self.ptr, self.n, self.m, self.info = ptr, n, m, info
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_biclique_dev(self.ptr)
+            self.ptr = None
+
+
+def bvg_biclique_upload(row_ptr, col, passes: int = 8, min_rows: int = 2, min_cols: int = 3, seed: int = 0,
+                        stream=None) -> BicliqueDev:
+    """Decomposes a CSR graph into bicliques and residual edges (Sec. 6, host)
+    and copies the decomposition to the current device."""
+    lib = load()
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    prm = BicliqueParams(passes, min_rows, min_cols, 0, seed)
+    h = _P()
+    _check(lib.bvg_biclique_encode(n, rp.ctypes.data, ci.ctypes.data if len(ci) else None, ctypes.byref(prm),
+                                   ctypes.byref(h)), "bvg_biclique_encode")
+    try:
+        info = BicliqueInfo()
+        _check(lib.bvg_biclique_stats(h, ctypes.byref(info)), "bvg_biclique_stats")
+        d = _P()
+        _check(lib.bvg_biclique_upload(h, _stream(stream), ctypes.byref(d)), "bvg_biclique_upload")
+    finally:
+        lib.bvg_free_biclique(h)
+    return BicliqueDev(d, n, int(rp[-1]), {f: getattr(info, f) for f, _ in BicliqueInfo._fields_})
+
+
+def bvg_biclique_spmv_Ax(d: BicliqueDev, x, y, stream=None):
+    """y = A x^T on the biclique representation (device)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, d.n)
+    _check(load().bvg_biclique_spmv_Ax(d.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
+           "bvg_biclique_spmv_Ax")
+    return y
+
+
+def bvg_biclique_spmv_xA(d: BicliqueDev, x, y, stream=None):
+    """y = x A on the biclique representation (device)."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, d.n)
+    _check(load().bvg_biclique_spmv_xA(d.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
+           "bvg_biclique_spmv_xA")
+    return y

@@ -28,11 +28,6 @@
 
 #include "bvg_internal.h"
 
-struct bvg_biclique {
-    int64_t n = 0, m = 0;
-    std::vector<int64_t> s_ptr{0}, c_ptr{0}, r_ptr;
-    std::vector<int32_t> s_idx, c_idx, r_col;
-};
 
 namespace {
 

@@ -232,6 +232,14 @@ bool use_points(const bvg_dev_graph* g, int kb);
 int check_vec(const bvg_dev_graph* g, const void* p, const char* what);
 }  // namespace bvg
 
+// Biclique decomposition (host; biclique.cpp): bicliques (S_r, C_r) as two
+// CSR-like lists, residual edges by row.
+struct bvg_biclique {
+    int64_t n = 0, m = 0;
+    std::vector<int64_t> s_ptr{0}, c_ptr{0}, r_ptr;
+    std::vector<int32_t> s_idx, c_idx, r_col;
+};
+
 struct bvg_csr_graph {
     int64_t n = 0, m = 0;
     int device = 0;
