@@ -344,7 +344,26 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
         del bd
         return r
 
-    def crossover(spec, k, with_biclique=False):
+    def stream_leg(gs, budget, k):
+        """A·xᵀ with the structure streamed from page-locked host memory through
+        two device slots of half the stated budget each (the resident pull
+        beside it)."""
+        t0 = time.perf_counter()
+        sm = bvg.bvg_stream_create(gs.row_ptr, gs.col, budget)
+        create_s = time.perf_counter() - t0
+        info = bvg.bvg_stream_info(sm)
+        xs = torch.from_numpy(synth.rhs(gs.n, k, synth.seed_for(5, 9))).cuda()
+        if k == 1:
+            xs = xs.reshape(-1)
+        ys = torch.empty_like(xs)
+        ms = warm_timed(lambda: bvg.bvg_stream_spmv(sm, xs, ys))
+        sec = float(np.mean(ms)) * 1e-3
+        del sm
+        return {"budget_bytes": budget, "k": k, "blocks": info["blocks"], "image_bytes": info["image_bytes"],
+                "slot_bytes": info["slot_bytes"], "create_seconds": create_s, "Ax_gedges_s": gs.m * k / sec / 1e9,
+                "ms_per_product": sec * 1e3, "host_to_device_gbs": info["image_bytes"] / sec / 1e9}
+
+    def crossover(spec, k, with_biclique=False, stream_budget=None):
         gs = synth.copying_model(spec)
         hs = bvg.bvg_encode(gs.row_ptr, gs.col)
         st = bvg.bvg_stats(hs)
@@ -366,18 +385,21 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
         del ds, cs
         if with_biclique:
             r["biclique"] = biclique_leg(gs, xs, ys, k)
+        if stream_budget:
+            r["stream"] = stream_leg(gs, stream_budget, k)
         return r
 
     out["social"] = crossover(synth.replace(synth.social_5m4(), n=g.n), 1, with_biclique=True)
     xb = torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
     out["biclique_bench_graph"] = biclique_leg(g, xb, torch.empty_like(xb), 1)
+    out["stream_bench_graph"] = [stream_leg(g, 16 << 20, kk) for kk in (1, 32)]
     if not args.no_high_compression:
         out["high_compression"] = crossover(synth.web_862k_hc(), 1)
         out["high_compression"]["graph"] = ("web-like copying model, exact copies with probability 0.93 "
                                             "(m/m' >= 5, the paper's 'compressed 5x or more' regime)")
     if args.config5:
         out["social_5m4"] = crossover(synth.social_5m4(), 1)
-        out["web_22m7_k8"] = crossover(synth.web_22m7(), 8)
+        out["web_22m7_k8"] = crossover(synth.web_22m7(), 8, stream_budget=512 << 20)
     return out
 
 

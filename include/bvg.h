@@ -518,6 +518,43 @@ void bvg_free_biclique_dev(bvg_biclique_dev* d);
 
 /* --------------------------------------------------- plain CSR baseline */
 
+/* ------------------------------------------------------------ streamed blocks */
+/* y = M x^T for a matrix whose compressed structure need not fit in device
+ * memory (the paper's graphs reach 9e10 edges, Sec. 5, Table 1), and for
+ * many right-hand sides per pass over the structure (the Online
+ * Matrix-Vector setting of Sec. 2). bvg_stream_create cuts the rows of M (M =
+ * A, or A^T when left = 1, for x A) into blocks of about equal edges, encodes
+ * each block on its own (references only among the block's rows, Sec. 4) and
+ * keeps each block's pull image (reference offsets, chain depths, work items,
+ * expanded difference entries) in page-locked host memory; no image exceeds
+ * half of budget_bytes, and the device holds two of them plus item scratch
+ * (max items x 32 floats). Host-side and synchronous; the CSR is copied.
+ * Errors: INVALID_ARG, BAD_GRAPH, UNSUPPORTED (a single row's image over half
+ * the budget), OOM, CUDA. */
+typedef struct bvg_stream bvg_stream;
+typedef struct {
+    int64_t n, m;
+    int32_t left, pad;
+    int64_t blocks;       /* row blocks */
+    int64_t slot_bytes;   /* device bytes of one slot (the largest image) */
+    int64_t image_bytes;  /* page-locked bytes of all images */
+} bvg_stream_info_t;
+int bvg_stream_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t budget_bytes, int32_t left,
+                      const bvg_encode_params* params, bvg_stream** out);
+/* y = M x^T (x A when the stream was created with left = 1), x, y device
+ * n x k of leading dimension ld: the blocks in order, each image copied on a
+ * private copy stream into one of two device slots while the pull kernels of
+ * the previous block run on `stream` (the slot's next copy waits for the
+ * kernels that read it); every column of x is served before the next block
+ * is copied. Asynchronous on `stream`; calls on one handle must be
+ * serialised. Errors: INVALID_ARG (also x or y not memory of the handle's
+ * device), CUDA. */
+int bvg_stream_spmv(bvg_stream* s, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+int bvg_stream_info(const bvg_stream* s, bvg_stream_info_t* out);
+/* The references of the block encodings (rows of M, -1 for none), n ints. */
+int bvg_stream_get_refs(const bvg_stream* s, int32_t* ref);
+void bvg_free_stream(bvg_stream* s);
+
 /* Device CSR of A and of A^T built from a host CSR (same input rules as
  * bvg_encode), for the plain sparse product the compressed one is compared
  * with (Sec. 5 compares A' against A). */

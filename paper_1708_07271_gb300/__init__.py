@@ -43,7 +43,8 @@ EXPORTED = [
     "bvg_point_cols_fill", "bvg_biclique_encode", "bvg_biclique_stats", "bvg_biclique_get", "bvg_free_biclique",
     "bvg_biclique_gather_lists", "bvg_bitstream_get", "bvg_decode_bits", "bvg_debug_fail_alloc",
     "bvg_device_check", "bvg_csr_cusparse_Ax", "bvg_csr_cusparse_xA", "bvg_biclique_upload",
-    "bvg_biclique_spmv_Ax", "bvg_biclique_spmv_xA", "bvg_free_biclique_dev",
+    "bvg_biclique_spmv_Ax", "bvg_biclique_spmv_xA", "bvg_free_biclique_dev", "bvg_stream_create", "bvg_stream_spmv",
+    "bvg_stream_info", "bvg_stream_get_refs", "bvg_free_stream",
 ]
 
 
@@ -85,6 +86,11 @@ class LayoutView(ctypes.Structure):
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
                 ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32), ("push_fused", _I32)]
+
+
+class StreamInfo(ctypes.Structure):
+    _fields_ = [("n", _I64), ("m", _I64), ("left", _I32), ("pad", _I32), ("blocks", _I64), ("slot_bytes", _I64),
+                ("image_bytes", _I64)]
 
 
 class BicliqueParams(ctypes.Structure):
@@ -199,6 +205,12 @@ def load(build_if_needed: bool = True):
             "bvg_biclique_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_biclique_spmv_xA": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_free_biclique_dev": ([_P], None),
+            "bvg_stream_create": ([_I64, _P, _P, _I64, _I32, ctypes.POINTER(EncodeParams), ctypes.POINTER(_P)],
+                                  ctypes.c_int),
+            "bvg_stream_spmv": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_stream_info": ([_P, ctypes.POINTER(StreamInfo)], ctypes.c_int),
+            "bvg_stream_get_refs": ([_P, _P], ctypes.c_int),
+            "bvg_free_stream": ([_P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -853,3 +865,50 @@ def bvg_biclique_spmv_xA(d: BicliqueDev, x, y, stream=None):
     _check(load().bvg_biclique_spmv_xA(d.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)),
            "bvg_biclique_spmv_xA")
     return y
+
+
+class Stream:
+    """Streamed row blocks (freed with the object)."""
+
+    def __init__(self, ptr, n: int, m: int, left: int):
+        self.ptr, self.n, self.m, self.left = ptr, n, m, left
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.bvg_free_stream(self.ptr)
+            self.ptr = None
+
+
+def bvg_stream_create(row_ptr, col, budget_bytes: int, left: bool = False, window=7, max_chain=3,
+                      min_interval=4) -> Stream:
+    """Row blocks of A (or of A^T for x A) whose images stay in page-locked
+    host memory, each at most half of budget_bytes on the device."""
+    lib = load()
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    prm = EncodeParams(window, max_chain, min_interval, 0)
+    out = _P()
+    _check(lib.bvg_stream_create(n, rp.ctypes.data, ci.ctypes.data if len(ci) else None, int(budget_bytes),
+                                 1 if left else 0, ctypes.byref(prm), ctypes.byref(out)), "bvg_stream_create")
+    return Stream(out, n, int(rp[-1]), 1 if left else 0)
+
+
+def bvg_stream_spmv(s: Stream, x, y, stream=None):
+    """y = A x^T (or x A for a left stream), the blocks streamed through the device."""
+    _fp32_cuda(x, y)
+    k, ld = _km(x, s.n)
+    if _km(y, s.n) != (k, ld):
+        raise ValueError("x and y must have the same shape and strides")
+    _check(load().bvg_stream_spmv(s.ptr, x.data_ptr(), y.data_ptr(), k, ld, _stream(stream)), "bvg_stream_spmv")
+    return y
+
+
+def bvg_stream_info(s: Stream) -> dict:
+    info = StreamInfo()
+    _check(load().bvg_stream_info(s.ptr, ctypes.byref(info)), "bvg_stream_info")
+    return {f: getattr(info, f) for f, _ in StreamInfo._fields_ if f != "pad"}
+
+
+def bvg_stream_get_refs(s: Stream):
+    ref = np.empty(s.n, np.int32)
+    _check(load().bvg_stream_get_refs(s.ptr, ref.ctypes.data), "bvg_stream_get_refs")
+    return ref

@@ -491,6 +491,22 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
     return BVG_OK;
 }
 
+// The pull product y = M x^T on a device graph whose pull arrays (meta,
+// irow, istart, pent, lrow, lint, part) may live anywhere the caller put them
+// (the streamed row blocks): column blocks of at most 32, no interval kept
+// whole (no prefix of x). part must hold nitems x 32 floats.
+int pull_view_product(const bvg_dev_graph* gv, const float* x, float* y, int32_t k, int64_t ld, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t c0 = 0; c0 < k;) {
+        const int kb = block_k(k - c0);
+        const int v = pick_v(kb, ld, c0, {x, y});
+        BVG_KV_CASES(launch_pull, gv, x + c0, ld, y + c0, ld, false, st);
+        c0 += kb;
+    }
+    BVG_CUDA_TRY(cudaGetLastError());
+    return BVG_OK;
+}
+
 int check_vec(const bvg_dev_graph* g, const void* p, const char* what) {
     if (!p) return fail(BVG_ERR_INVALID_ARG, "%s is NULL", what);
     if ((uintptr_t)p % 4) return fail(BVG_ERR_INVALID_ARG, "%s is not 4-byte aligned", what);

@@ -97,6 +97,10 @@ struct bvg_host_graph {
 };
 
 namespace bvg {
+// The encoder for a block of n rows over ncols columns (references among the
+// block's rows); bvg_encode is encode_rows(n, n, ...).
+int encode_rows(int64_t n, int64_t ncols, const int64_t* row_ptr, const int32_t* col_idx,
+                const bvg_encode_params* params, bvg_host_graph** out);
 int build_layout(const bvg_host_graph* hg, HostLayout& L);
 int get_layout(const bvg_host_graph* hg, const HostLayout** out);
 }  // namespace bvg
@@ -230,6 +234,8 @@ bool use_points(const bvg_dev_graph* g, int kb);
 // A vector argument of a device product: not NULL, 4-byte aligned, and device
 // (or managed) memory of the graph's device; otherwise INVALID_ARG (api.cu).
 int check_vec(const bvg_dev_graph* g, const void* p, const char* what);
+// The pull on a device graph view whose arrays the caller placed (api.cu).
+int pull_view_product(const bvg_dev_graph* v, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 }  // namespace bvg
 
 // Biclique decomposition (host; biclique.cpp): bicliques (S_r, C_r) as two

@@ -218,13 +218,16 @@ extern "C" int bvg_debug_fail_alloc(int64_t after) {
     return BVG_OK;
 }
 
-extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
-                          const bvg_encode_params* params, bvg_host_graph** out) {
+// The encoder for an n x ncols block of rows (ids in [0, ncols)): references
+// are chosen among the block's own rows. bvg_encode is the square case.
+int bvg::encode_rows(int64_t n, int64_t ncols, const int64_t* row_ptr, const int32_t* col_idx,
+                     const bvg_encode_params* params, bvg_host_graph** out) {
     if (!out) return fail(BVG_ERR_INVALID_ARG, "bvg_encode: out is NULL");
     *out = nullptr;
     if (n < 0 || !row_ptr || (n > 0 && row_ptr[n] > 0 && !col_idx))
         return fail(BVG_ERR_INVALID_ARG, "bvg_encode: bad n or NULL arrays");
-    if (n >= kMaxN) return fail(BVG_ERR_UNSUPPORTED, "bvg_encode: n = %lld exceeds 2^30 - 1", (long long)n);
+    if (n >= kMaxN || ncols >= kMaxN || ncols < 0)
+        return fail(BVG_ERR_UNSUPPORTED, "bvg_encode: n = %lld exceeds 2^30 - 1", (long long)std::max(n, ncols));
     int W = params && params->window ? params->window : 7;
     int R = params && params->max_chain ? params->max_chain : 3;
     int L = params && params->min_interval ? params->min_interval : 4;
@@ -237,7 +240,7 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
     if (row_ptr[0] != 0) return fail(BVG_ERR_BAD_GRAPH, "bvg_encode: row_ptr[0] != 0");
     for (int64_t i = 0; i < n; i++) {
         if (row_ptr[i + 1] < row_ptr[i]) return fail(BVG_ERR_BAD_GRAPH, "bvg_encode: row_ptr decreases at row %lld", (long long)i);
-        if (row_ptr[i + 1] - row_ptr[i] > n)
+        if (row_ptr[i + 1] - row_ptr[i] > ncols)
             return fail(BVG_ERR_BAD_GRAPH, "bvg_encode: row %lld longer than n", (long long)i);
     }
     const int64_t m = n > 0 ? row_ptr[n] : 0;
@@ -246,7 +249,7 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
         for (int64_t i = s; i < e; i++) {
             for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; t++) {
                 int32_t j = col_idx[t];
-                if (j < 0 || j >= n || (t > row_ptr[i] && col_idx[t - 1] >= j)) {
+                if (j < 0 || j >= ncols || (t > row_ptr[i] && col_idx[t - 1] >= j)) {
                     int64_t expect = -1;
                     bad_row.compare_exchange_strong(expect, i);
                     return;
@@ -427,7 +430,7 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
         st.bitstream_bits = g->nbits;
         st.bits_per_edge = m > 0 ? (double)g->nbits / (double)m : 0.0;
         int64_t ends = 0;
-        for (int64_t t = 0; t < st.intervals; t++) ends += (int64_t)g->iv_s[t] + g->iv_len[t] < n;
+        for (int64_t t = 0; t < st.intervals; t++) ends += (int64_t)g->iv_s[t] + g->iv_len[t] < ncols;
         int64_t tiles = (n + kCarryTile - 1) / kCarryTile;
         int64_t carry = 0;
         for (int64_t t = 0; t < st.intervals; t++) {
@@ -443,6 +446,11 @@ extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_
     }
     *out = g;
     return BVG_OK;
+}
+
+extern "C" int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                          const bvg_encode_params* params, bvg_host_graph** out) {
+    return encode_rows(n, n, row_ptr, col_idx, params, out);
 }
 
 // Decodes a bitstream of n rows and m edges written with window W and minimum
