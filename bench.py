@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--no-config5", action="store_true", help="skip the n = 5.4 M and n = 22.7 M graphs")
     ap.add_argument("--no-high-compression", action="store_true", help="skip the m/m' >= 5 web graph leg")
     ap.add_argument("--window-sweep", action="store_true",
-                    help="encode the bench graph with window W in {1, 3, 5, 7} and chain bound R in {1, 2, 3}: "
-                         "compression and both products' speed")
+                    help="encode the bench graph (and one copying among 31 rows) with window W in {1, 3, 7, 15, 31} "
+                         "and chain bound R, W * R <= 32: compression and both products' speed")
     ap.add_argument("--config4", action="store_true",
                     help="train the warm-start network on 200 generated graphs (n log-uniform in [1e5, 1e6]) and "
                          "evaluate it on the web-like graph n = 18.5 M")
@@ -404,28 +404,36 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
 
 
 def window_sweep_leg(args, bvg, torch, timed, g):
-    """The reference window W (Sec. 4) and the chain bound R against
-    compression and speed: the bench graph encoded with W in {1, 3, 5, 7}
-    (the device layout stores r_i as a 3-bit offset, so W <= 7) and R in
-    {1, 2, 3}; x A and A x^T at k = 1, L2 flushed before each product."""
+    """The reference window W (Sec. 4; wider windows are the paper's future
+    work, Sec. 6) and the chain bound R against compression and speed, with
+    W * R <= 32 (one 32-bit descendant mask per row): the bench graph, whose
+    rows copy prototypes among the previous 7 rows, and the same model with
+    prototypes among the previous 31 rows; x A and A x^T at k = 1, L2 flushed
+    before each product."""
     import synth
-    x = torch.from_numpy(synth.rhs(g.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
-    y = torch.empty_like(x)
-    out = []
-    for w in (1, 3, 5, 7):
-        for r in (1, 2, 3):
-            hs = bvg.bvg_encode(g.row_ptr, g.col, window=w, max_chain=r)
-            st = bvg.bvg_stats(hs)
-            ds = bvg.bvg_upload(hs)
-            res = {"window": w, "max_chain": r, "m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
-                   "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"]}
-            for name, fn in (("xA", lambda: bvg.bvg_spmv_xA(ds, x, y)), ("Ax", lambda: bvg.bvg_spmv_Ax(ds, x, y))):
-                for _ in range(args.warmup):
-                    fn()
-                ms = timed(fn, args.steps)
-                res[name + "_gedges_s"] = g.m * len(ms) / (np.sum(ms) * 1e-3) / 1e9
-            out.append(res)
-            del ds
+    out = {}
+    for label, gg in (("copy_window_7", g), ("copy_window_31", synth.copying_model(synth.replace(
+            synth.web_862k(), window=31)))):
+        x = torch.from_numpy(synth.rhs(gg.n, 1, synth.seed_for(2, 1))).cuda().reshape(-1)
+        y = torch.empty_like(x)
+        rows = []
+        for w in (1, 3, 7, 15, 31):
+            for r in (1, 2, 3):
+                if w * r > 32 or (w == 1 and r > 1):
+                    continue
+                hs = bvg.bvg_encode(gg.row_ptr, gg.col, window=w, max_chain=r)
+                st = bvg.bvg_stats(hs)
+                ds = bvg.bvg_upload(hs)
+                res = {"window": w, "max_chain": r, "m_over_mprime": st["m"] / max(1, st["nnz_diff"]),
+                       "m_over_words": st["m"] / max(1, st["words"]), "bits_per_edge": st["bits_per_edge"]}
+                for name, fn in (("xA", lambda: bvg.bvg_spmv_xA(ds, x, y)), ("Ax", lambda: bvg.bvg_spmv_Ax(ds, x, y))):
+                    for _ in range(args.warmup):
+                        fn()
+                    ms = timed(fn, args.steps)
+                    res[name + "_gedges_s"] = gg.m * len(ms) / (np.sum(ms) * 1e-3) / 1e9
+                rows.append(res)
+                del ds
+        out[label] = {"m": gg.m, "sweep": rows}
     return out
 
 

@@ -64,8 +64,9 @@ typedef struct bvg_mlp bvg_mlp;               /* warm-start network 6 -> 64 -> 6
 /* Encoder parameters (Sec. 4: window W; chain bound and interval length are
  * this library's choices). Zero fields take the defaults shown. */
 typedef struct {
-    int32_t window;       /* W, candidates r in [i - W, i - 1]; default 7, max 7 */
-    int32_t max_chain;    /* R, longest reference chain; default 3, max 3 */
+    int32_t window;       /* W, candidates r in [i - W, i - 1]; default 7, max 31 */
+    int32_t max_chain;    /* R, longest reference chain; default 3, max 3; W * R at most 32 (a chain then
+                             spans at most 32 rows: one 32-bit descendant mask per row) */
     int32_t min_interval; /* shortest run stored as an interval; default 4 */
     int32_t threads;      /* host threads for the cost pass; 0 = hardware concurrency */
 } bvg_encode_params;
@@ -151,7 +152,7 @@ int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
  * column), 1 (-1), 2 (an interval of that row starts here), 3 (an interval
  * of that row ended just before this column). carry[carry_ptr[t] ..
  * carry_ptr[t+1]) lists the rows of intervals [s, e) with
- * s < t * carry_tile_cols <= e. meta[i] = (i - r_i, or 0) | depth_i << 3.
+ * s < t * carry_tile_cols <= e. meta[i] = (i - r_i, or 0) | depth_i << 5.
  * Tail items: column j's entries past its first 3 in runs of at most 4,
  * items [titem_ptr[j], titem_ptr[j+1]), each item = start index into the
  * column-major entries | (count - 1) << 30. */

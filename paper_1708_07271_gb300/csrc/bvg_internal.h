@@ -12,12 +12,18 @@
 namespace bvg {
 
 // Largest supported window and chain bound. The device layout packs the
-// reference offset (1..7, 0 = none) in 3 bits and the chain depth in 2 bits.
-constexpr int kMaxWindow = 7;
+// reference offset (1..31, 0 = none) in bits 0-4 of a row's meta byte and the
+// chain depth in bits 5-6; a chain spans at most window * max_chain rows,
+// which the encoder keeps within kMaxSpan so that one 32-bit mask holds a
+// row's descendants (W = 7 with R = 3, W = 15 with R = 2, W = 31 with R = 1).
+constexpr int kMaxWindow = 31;
 constexpr int kMaxChain = 3;
+constexpr int kMaxSpan = 32;
+constexpr uint32_t kMetaOff = 31u;   // meta & kMetaOff: i - r_i (0 = no reference)
+constexpr int kMetaDepthShift = 5;  // meta >> kMetaDepthShift: chain depth
 // Halo of rows a tile needs beyond its own range to resolve reference
-// chains locally: a chain spans at most kMaxWindow * kMaxChain rows.
-constexpr int kHalo = kMaxWindow * kMaxChain;
+// chains locally.
+constexpr int kHalo = kMaxSpan;
 // Granularity (columns) of the interval carry-in lists of the column layout.
 constexpr int kCarryTile = 128;
 // Two tag bits on top of a 30-bit id.

@@ -233,9 +233,10 @@ int bvg::encode_rows(int64_t n, int64_t ncols, const int64_t* row_ptr, const int
     int L = params && params->min_interval ? params->min_interval : 4;
     int threads = params && params->threads > 0 ? params->threads : (int)std::thread::hardware_concurrency();
     if (threads < 1) threads = 1;
-    if (W < 1 || W > kMaxWindow || R < 1 || R > kMaxChain || L < 2)
+    if (W < 1 || W > kMaxWindow || R < 1 || R > kMaxChain || W * R > kMaxSpan || L < 2)
         return fail(BVG_ERR_UNSUPPORTED, "bvg_encode: window %d / max_chain %d / min_interval %d unsupported "
-                                         "(window 1..7, max_chain 1..3, min_interval >= 2)", W, R, L);
+                                         "(window 1..31, max_chain 1..3, window * max_chain <= 32, "
+                                         "min_interval >= 2)", W, R, L);
     // ---- validate CSR
     if (row_ptr[0] != 0) return fail(BVG_ERR_BAD_GRAPH, "bvg_encode: row_ptr[0] != 0");
     for (int64_t i = 0; i < n; i++) {

@@ -287,7 +287,7 @@ __device__ __forceinline__ int pull_chain_of(const uint8_t* __restrict__ meta, i
     int len = 0, cur = r;
     idx[len++] = cur;
     for (int t = 0; t < kMaxChain; t++) {
-        const int off = __ldg(meta + lo + cur) & 7;
+        const int off = __ldg(meta + lo + cur) & kMetaOff;
         if (off == 0 || cur - off < 0) break;
         cur -= off;
         idx[len++] = cur;

@@ -38,7 +38,7 @@ int build_layout(const bvg_host_graph* hg, HostLayout& L) {
         size_t w = 0;
         for (int64_t i = 0; i < n; i++) {
             const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
-            L.meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
+            L.meta[i] = (uint8_t)(off | (hg->depth[i] << kMetaDepthShift));
             // every ancestor r of i on its chain (at most kHalo rows back) gets
             // bit i - r - 1 of its descendant mask
             for (int64_t r = hg->ref[i], hop = 0; r >= 0 && hop < kMaxChain; r = hg->ref[r], hop++)

@@ -245,7 +245,7 @@ __global__ void k_features(const uint8_t* __restrict__ meta, const uint32_t* __r
         }
         const float mean_nbr = od > 0.f ? __ldg(nbrsum + i) / od : 0.f;
         const float2 d = deg[i];
-        float4 a = make_float4(log1pf(d.x), log1pf(od), (float)(__ldg(meta + i) >> 3),
+        float4 a = make_float4(log1pf(d.x), log1pf(od), (float)(__ldg(meta + i) >> kMetaDepthShift),
                                od > 0.f ? (float)members / od : 0.f);
         float4 b = make_float4(log1pf(mean_nbr), log1pf(d.y), 0.f, 0.f);
         *reinterpret_cast<float4*>(feat + i * FSTR) = a;

@@ -72,7 +72,7 @@ int build_block(const int64_t* row_ptr, const int32_t* col, int64_t r0, int64_t 
     b.ref.assign(nb, -1);
     for (int64_t i = 0; i < nb; i++) {
         const int off = hg->ref[i] >= 0 ? (int)(i - hg->ref[i]) : 0;
-        meta[i] = (uint8_t)(off | (hg->depth[i] << 3));
+        meta[i] = (uint8_t)(off | (hg->depth[i] << kMetaDepthShift));
         b.ref[i] = hg->ref[i] >= 0 ? (int32_t)(r0 + hg->ref[i]) : -1;
         for (int64_t t = hg->drop_ptr[i]; t < hg->drop_ptr[i + 1]; t++) ent.push_back(pack(kTagMinus, hg->drop[t]));
         for (int64_t t = hg->res_ptr[i]; t < hg->res_ptr[i + 1]; t++) ent.push_back(pack(kTagPlus, hg->res[t]));

@@ -538,7 +538,7 @@ def test_push_hub_columns(points):
         assert l1(p.cpu().numpy()[:, c], want[:, c]) <= 1e-6, c
 
 
-@pytest.mark.parametrize("window,max_chain", [(1, 1), (3, 2), (5, 3), (7, 1)])
+@pytest.mark.parametrize("window,max_chain", [(1, 1), (3, 2), (5, 3), (7, 1), (10, 3), (15, 2), (31, 1)])
 def test_other_windows_and_chain_bounds(window, max_chain):
     """Encodings with a shorter reference window W (Sec. 4) or chain bound R:
     both products and PageRank match the oracle (the oracle decodes its own

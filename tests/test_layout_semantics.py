@@ -18,8 +18,8 @@ def chain_weights(L, x):
     """z: x pushed down the reference chains (rows in reverse level order),
     checked against the same weights read from the descendant masks."""
     meta = L["meta"].astype(np.int64)
-    off = meta & 7
-    depth = meta >> 3
+    off = meta & 31
+    depth = meta >> 5
     z = x.astype(np.float64).copy()
     # reverse level order: rows of depth d add into their reference
     for d in range(3, 0, -1):
@@ -28,7 +28,7 @@ def chain_weights(L, x):
     # the same weights from the descendant masks (what the chain kernel reads)
     zd = x.astype(np.float64).copy()
     desc = L["desc"].astype(np.int64)
-    for t in range(21):
+    for t in range(32):
         rows = np.nonzero((desc >> t) & 1)[0]
         zd[rows] += x[rows + t + 1]
     np.testing.assert_allclose(zd, z, rtol=1e-12)
@@ -81,7 +81,7 @@ def emulate_Ax(L, x):
                 w += 1
             w += 1
     y = np.zeros_like(c)
-    off = (L["meta"] & 7).astype(np.int64)
+    off = (L["meta"] & 31).astype(np.int64)
     for i in range(n):
         y[i] = c[i] + (y[i - off[i]] if off[i] else 0.0)
     return y
@@ -113,7 +113,7 @@ def emulate_Ax_items(L, P, x, item, min_len):
     rows_of_items = np.repeat(np.arange(n), np.diff(irow))
     assert len(rows_of_items) == len(sizes)
     y = np.zeros_like(c)
-    off = (L["meta"] & 7).astype(np.int64)
+    off = (L["meta"] & 31).astype(np.int64)
     for i in range(n):
         y[i] = c[i] + (y[i - off[i]] if off[i] else 0.0)
     return y
@@ -144,9 +144,9 @@ def test_layout_reproduces_products(name):
     deg = np.diff(g.row_ptr)
     np.testing.assert_array_equal(L["inv_outdeg"], np.where(deg > 0, 1.0 / np.maximum(deg, 1), 0).astype(np.float32))
     ref, depth = bvg.bvg_get_refs(hg)
-    off = (L["meta"] & 7).astype(np.int64)
+    off = (L["meta"] & 31).astype(np.int64)
     np.testing.assert_array_equal(np.where(ref >= 0, np.arange(g.n) - ref, 0), off)
-    np.testing.assert_array_equal(L["meta"] >> 3, depth)
+    np.testing.assert_array_equal(L["meta"] >> 5, depth)
     desc = np.zeros(g.n, np.int64)
     for i in range(g.n):
         r = ref[i]

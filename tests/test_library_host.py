@@ -59,7 +59,7 @@ def test_encoder_matches_oracle_and_round_trips(name, g):
     np.testing.assert_array_equal(ci, g.col)
 
 
-@pytest.mark.parametrize("W,R,L", [(1, 1, 2), (3, 2, 3), (7, 1, 8), (7, 3, 4)])
+@pytest.mark.parametrize("W,R,L", [(1, 1, 2), (3, 2, 3), (7, 1, 8), (7, 3, 4), (10, 3, 4), (15, 2, 5), (31, 1, 4)])
 def test_encoder_parameters(W, R, L):
     g = synth.copying_model(synth.GraphSpec(n=2000, seed=9, p_copy=0.8, fidelity=0.9, extra_mean=1.0,
                                             fresh_mean=10, q_run=0.5, gap_mean=5.0))
@@ -103,9 +103,12 @@ def test_bad_graphs_rejected():
     with pytest.raises(bvg.BvgError) as e:
         bvg.bvg_encode(np.array([1, 2, 3], np.int64), np.array([0, 1, 0], np.int32))
     assert e.value.status == bvg.BVG_ERR_BAD_GRAPH
-    with pytest.raises(bvg.BvgError) as e:
-        bvg.bvg_encode(rp, np.array([0, 1, 1], np.int32), window=8)
-    assert e.value.status == bvg.BVG_ERR_UNSUPPORTED
+    for window, max_chain in ((32, 1), (15, 3), (11, 3), (17, 2)):  # window <= 31 and window * max_chain <= 32
+        with pytest.raises(bvg.BvgError) as e:
+            bvg.bvg_encode(rp, np.array([0, 1, 1], np.int32), window=window, max_chain=max_chain)
+        assert e.value.status == bvg.BVG_ERR_UNSUPPORTED
+    for window, max_chain in ((8, 3), (10, 3), (16, 2), (31, 1)):
+        bvg.bvg_encode(rp, np.array([0, 1, 1], np.int32), window=window, max_chain=max_chain)
 
 
 def test_null_arguments():
