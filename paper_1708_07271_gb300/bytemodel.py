@@ -18,11 +18,12 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
                [+ 4(n+1) + 4*point_tail_items (tail items) when k <= 4, where one lane
                group owns a column and the tail items are shared out] + 4kn (z) + 4kn (y)
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
-  push_fused   (one right-hand side, one kernel) n (meta) + 4(n+1) (column offsets)
-               + 4*col_entries + 4*(carry_tiles+1) + 4*carry_entries + ceil(n/1024)
-               (per-tile flags) + 4n (x) + 4n (y); the chain weights never leave
-               shared memory, and the window rows read by two neighbouring tiles
-               come from L2 the second time
+  push_fused   (one right-hand side, one kernel) 4n (descendant masks) + 4(n+1) (column
+               offsets) + 4*col_entries + 4*(carry_tiles+1) + 4*carry_entries
+               + 16*ceil(n/1024) (per-tile row windows) + 4*32*ceil(n/128) (each warp's
+               column order) + 4n (x) + 4n (y); the chain weights never leave shared
+               memory, and the window rows read by two neighbouring tiles come from
+               L2 the second time
   pr_fused     push_fused + 4n (1/outdeg) [+ 4n (p0) when a teleport vector is
                given]: x is the previous iterate (read once), the new iterate is
                written in place of y
@@ -77,8 +78,8 @@ def pr_gather_pt(L: dict, k: int, with_p0: bool) -> int:
 
 def push_fused(L: dict, k: int) -> int:
     n = L["n"]
-    return (n + 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
-            + (n + 1023) // 1024 + 8 * k * n)
+    return (4 * n + 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
+            + 16 * ((n + 1023) // 1024) + 128 * ((n + 127) // 128) + 8 * k * n)
 
 
 def pr_fused(L: dict, k: int, with_p0: bool = False) -> int:

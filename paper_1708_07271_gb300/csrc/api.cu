@@ -252,6 +252,7 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     fa.pcolp = g->pcolp;
     fa.pcent = g->pcent;
     fa.tile_win = (const uint4*)g->tile_win;
+    fa.lane_cols = g->lane_cols;
     fa.x = x;
     fa.ldx = ldx;
     fa.rowscale = rowscale;
@@ -617,8 +618,28 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             }
             g->fx_tiles = tiles;
             g->fx_far_tiles = nfar;
+            // each warp's columns (a group of kCarryTile) sorted by entry count,
+            // most first, the q-th 32 in lane slot q: a warp's loop over slot q
+            // runs as long as the longest column of that group, and the sum
+            // of those maxima is the least an assignment of 4 columns per lane
+            // gives
+            const int64_t groups = (n + kCarryTile - 1) / kCarryTile;
+            std::vector<uint32_t> lane_cols((size_t)groups * 32, 0u);
+            std::vector<int> ord(kCarryTile);
+            std::vector<uint32_t> cnt(kCarryTile);
+            for (int64_t t = 0; t < groups; t++) {
+                for (int o = 0; o < kCarryTile; o++) {
+                    const int64_t j = t * kCarryTile + o;
+                    cnt[o] = j < n ? L->colp[j + 1] - L->colp[j] : 0u;
+                    ord[o] = o;
+                }
+                std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return cnt[u] > cnt[v]; });
+                for (int l = 0; l < 32; l++)
+                    for (int q = 0; q < kCarryTile / 32; q++)
+                        lane_cols[(size_t)t * 32 + l] |= (uint32_t)ord[q * 32 + l] << (8 * q);
+            }
             uint32_t* dwin = nullptr;
-            if ((rc = upload_vec(&dwin, win, st, &g->bytes)) ||
+            if ((rc = upload_vec(&dwin, win, st, &g->bytes)) || (rc = upload_vec(&g->lane_cols, lane_cols, st, &g->bytes)) ||
                 (rc = dev_alloc((void**)&g->err, sizeof(unsigned int), nullptr))) {
                 if (dwin) cudaFree(dwin);
                 bvg_free_dev(g);
@@ -659,7 +680,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->err};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)

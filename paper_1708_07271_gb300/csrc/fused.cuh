@@ -9,8 +9,14 @@
 //      mbarrier completion), and x of the window rows (coalesced loads);
 //   2. the chain weights z of the window rows;
 //   3. each thread's 4 columns: +-z_k of their entries into the column's
-//      point sum or event sum;
-//   4. the running interval sum and y_j, rounded once.
+//      point sum or event sum. On the exact path a warp's 128 columns are
+//      dealt to its lanes by entry count (the table lane_cols, built at
+//      upload): the longest 32 columns go to slot 0, the next 32 to slot 1,
+//      and so on, so that a warp's four column loops run about as long as
+//      its four longest columns instead of the longest of its lanes' runs
+//      of consecutive columns;
+//   4. the running interval sum (in column order, through shared memory) and
+//      y_j, rounded once.
 // No global scratch, no second launch, no atomics, no grid-wide
 // synchronisation. Two arithmetic paths, chosen per tile (the same choice in
 // every thread):
@@ -56,7 +62,8 @@ constexpr int kFxNT = 256;                 // threads per CTA
 constexpr int kFxCPT = kFxT / kFxNT;       // consecutive columns per thread: a warp's 128 = one carry tile
 constexpr int kFxW = 1792;                 // most window rows: the span of the rows a tile reads (set at upload)
 constexpr int kFxXR = (kFxW + kHalo + kFxNT - 1) / kFxNT;  // window rows whose x a thread loads
-constexpr int kFxECap = 3584;              // entries per tile staged in shared memory (more: read from global)
+constexpr int kFxECap = 3520;              // entries per tile staged in shared memory (more: read from global)
+constexpr int kFxDescW = 2 * kFxT > kFxW + 8 ? 2 * kFxT : kFxW + 8;  // mask words; then one int64 per column
 constexpr long long kFxWaitCycles = 4000000000LL;  // bound of an mbarrier wait (about 2 s)
 static_assert(kFxCPT * 32 == kCarryTile, "a warp's columns form one carry tile");
 
@@ -71,6 +78,9 @@ struct FxArgs {
     const uint4* tile_win;      // per tile of kFxT columns: (first, end) of its row window, and 1 when a row it
                                 // reads lies outside (the rows an entry or open interval comes from span more
                                 // than kFxW rows)
+    const uint32_t* lane_cols;  // per group of kCarryTile columns, 32 words: lane l's four columns (bytes q =
+                                // 0..3, offsets in the group), the group's columns sorted by entry count
+                                // (most first) and the q-th 32 given to slot q
     const float* x;
     int64_t ldx;
     const float* rowscale;      // x_i * rowscale_i (PageRank's 1/outdeg), or NULL
@@ -191,13 +201,15 @@ struct FxSmem {
             float zf[kFxW];         //   and their chain weights
         } c;
     } a;
-    alignas(16) uint32_t desc[kFxW + 8];    // descendant masks of the window (16-byte aligned superset)
+    alignas(16) uint32_t desc[kFxDescW];    // descendant masks of the window (16-byte aligned superset); after
+                                            // the chain weights, the exact path's per-column event sums
     alignas(16) uint32_t ent[kFxECap + 8];  // the tile's event-column entries (16-byte aligned superset), exact path
     uint64_t bar[2];                // mbarriers: [0] masks, [1] entries
     unsigned int emax, emin, state;
 };
 static_assert(sizeof(float) * (2 * kFxW + kHalo) <= sizeof(long long) * (kFxW + kHalo), "x and z fit");
 static_assert(offsetof(FxSmem, desc) % 16 == 0 && offsetof(FxSmem, ent) % 16 == 0, "bulk-copy targets aligned");
+static_assert(kFxDescW * sizeof(uint32_t) >= kFxT * sizeof(long long), "one event sum per column fits the masks");
 
 // One tile of the fused product. EPI = 0: store y. EPI = 1: PageRank update
 // epilogue (see PrArgs), x = the previous iterate scaled by 1/outdeg.
@@ -237,10 +249,18 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         if (be) bulk_g2s(S.ent, fa.tent + e0a, be, &S.bar[1]);
     }
     const int64_t c0 = a + (int64_t)tid * kFxCPT;
-    uint32_t cp[kFxCPT + 1];
-#pragma unroll
-    for (int q = 0; q <= kFxCPT; q++) cp[q] = __ldg(fa.colp + (c0 + q < tend ? c0 + q : tend));
     const int64_t wc = a + (int64_t)warp * kCarryTile;  // this warp's first column
+    // exact path: slot q of this lane is column wc + byte q of oc (columns
+    // balanced over the lanes by entry count); identity: columns c0 + q
+    const uint32_t oid = 0x03020100u + 0x04040404u * (uint32_t)lane;
+    uint32_t oc = wc < n ? __ldg(fa.lane_cols + (wc / kCarryTile) * 32 + lane) : oid;
+    uint32_t cb[kFxCPT], ce[kFxCPT];
+#pragma unroll
+    for (int q = 0; q < kFxCPT; q++) {
+        const int64_t j = wc + ((oc >> (8 * q)) & 0xffu);
+        cb[q] = __ldg(fa.colp + (j < tend ? j : tend));
+        ce[q] = __ldg(fa.colp + (j + 1 < tend ? j + 1 : tend));
+    }
     uint32_t cr0 = 0, cr1 = 0, csrc = 0;
     if (wc < n) {
         cr0 = __ldg(fa.carry_ptr + wc / kCarryTile);
@@ -335,42 +355,51 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             mbar_wait(&S.bar[1], 0);
         }
         __syncthreads();
+        if (S.state != 0u)  // a copy ran out of time: read no staged entry (the outputs are NaN)
+#pragma unroll
+            for (int q = 0; q < kFxCPT; q++) ce[q] = cb[q];
         // (the tile reads no row outside its window: z of any source row is
         // in shared memory)
         const long long* zv = S.a.v - w0;
-        // one entry w into (a, d): +-z of its source row into the sum of all
-        // entries and, for an interval event, into the event sum (branch-free)
-        auto add_entry = [&](uint32_t w, long long& sa, long long& d) {
-            long long z = zv[id_of(w)];
-            const long long neg = -(long long)((w >> kIdBits) & 1u);  // a dropped id, or an interval ending here
-            z = (z ^ neg) - neg;
-            sa += z;
-            d += z & -(long long)(w >> (kIdBits + 1));                // an interval start or end event
+        // this lane's columns (slot q: column wc + byte q of oc): the sum of
+        // all entries A_q = P_q + D_q, and the event sum D_q into shared
+        // memory at the column's place (the masks are no longer read);
+        // y_j = P_j + I_j = A_j + I_{j-1}. +-z of an entry's source row into
+        // the point or the event sum.
+        long long* Ds = reinterpret_cast<long long*>(S.desc) + warp * kCarryTile;
+        long long A[kFxCPT];
+        auto column = [&](auto&& word, int q) {
+            long long p = 0, d = 0;
+            for (uint32_t e = cb[q]; e < ce[q]; e++) {
+                const uint32_t w = word(e);
+                long long z = zv[id_of(w)];
+                if (w & (1u << kIdBits)) z = -z;  // a dropped id, or an interval ending here
+                if (w >> (kIdBits + 1))           // an interval start or end event
+                    d += z;
+                else
+                    p += z;
+            }
+            A[q] = p + d;
+            Ds[(oc >> (8 * q)) & 0xffu] = d;
         };
-        // this thread's columns: the sum of all entries A_q = P_q + D_q and the
-        // event sum D_q (y_j = P_j + I_j = A_j + I_{j-1})
-        long long A[kFxCPT], D[kFxCPT], tot = 0;
         if (staged) {
             const uint32_t* ent = S.ent - e0a;
 #pragma unroll
-            for (int q = 0; q < kFxCPT; q++) {
-                long long sa = 0, d = 0;
-                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) add_entry(ent[e], sa, d);
-                A[q] = sa;
-                D[q] = d;
-                tot += d;
-            }
+            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return ent[e]; }, q);
         } else {
 #pragma unroll
-            for (int q = 0; q < kFxCPT; q++) {
-                long long sa = 0, d = 0;
-                for (uint32_t e = cp[q]; e < cp[q + 1]; e++) add_entry(__ldg(fa.tent + e), sa, d);
-                A[q] = sa;
-                D[q] = d;
-                tot += d;
-            }
+            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return __ldg(fa.tent + e); }, q);
         }
-        // running interval sum: this warp's carry, then its columns in order
+        // running interval sum, in column order: this warp's carry, then its
+        // columns in order; each column's running sum goes back to the lane
+        // holding the column
+        __syncwarp();
+        long long dq[kFxCPT], tot = 0;
+#pragma unroll
+        for (int q = 0; q < kFxCPT; q++) {
+            dq[q] = Ds[lane * kFxCPT + q];
+            tot += dq[q];
+        }
         long long run = 0;
         if (cr0 + lane < cr1) run = zv[csrc];
         for (uint32_t e = cr0 + 32 + lane; e < cr1; e += 32) run += zv[__ldg(fa.carry + e)];  // rare: > 32 open
@@ -382,14 +411,18 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             const long long t = shfl_up_ll(inc, o);
             if (lane >= o) inc += t;
         }
-        run += inc - tot;  // the warp's earlier threads
-        const int E = (int)vmax - 188 + hz;  // the integers count units of 2^E
+        run += inc - tot;  // the warp's earlier lanes
 #pragma unroll
         for (int q = 0; q < kFxCPT; q++) {
-            yv[q] = fx_to_float(A[q] + run, E);
-            run += D[q];
+            Ds[lane * kFxCPT + q] = run;  // the intervals open before the column
+            run += dq[q];
         }
+        __syncwarp();
+        const int E = (int)vmax - 188 + hz;  // the integers count units of 2^E
+#pragma unroll
+        for (int q = 0; q < kFxCPT; q++) yv[q] = fx_to_float(A[q] + Ds[(oc >> (8 * q)) & 0xffu], E);
     } else {
+        oc = oid;  // the compensated path keeps columns c0 + q
         // compensated path: x of the window into shared memory
 #pragma unroll
         for (int i = 0; i < kFxXR; i++) {
@@ -447,7 +480,7 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
     if constexpr (EPI == 1) dl = (float)__ldcg(pa.sc_prev + 1);
 #pragma unroll
     for (int q = 0; q < kFxCPT; q++) {
-        const int64_t j = c0 + q;
+        const int64_t j = wc + ((oc >> (8 * q)) & 0xffu);
         if (failed) yv[q] = __uint_as_float(0x7fc00000u);
         if (j >= tend) continue;
         if constexpr (EPI == 0) {
