@@ -21,7 +21,8 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
   push_fused   (one right-hand side, one kernel) 4n (descendant masks) + 4(n+1) (column
                offsets) + 4*col_entries + 4*(carry_tiles+1) + 4*carry_entries
                + 16*ceil(n/1024) (per-tile row windows) + 4*32*ceil(n/128) (each warp's
-               column order) + 4n (x) + 4n (y); the chain weights never leave shared
+               column order) + 1024*ceil(n/1024) (the chain weights' row order) + 4n (x)
+               + 4n (y); the chain weights never leave shared
                memory, and the window rows read by two neighbouring tiles come from
                L2 the second time
   pr_fused     push_fused + 4n (1/outdeg) [+ 4n (p0) when a teleport vector is
@@ -79,7 +80,7 @@ def pr_gather_pt(L: dict, k: int, with_p0: bool) -> int:
 def push_fused(L: dict, k: int) -> int:
     n = L["n"]
     return (4 * n + 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
-            + 16 * ((n + 1023) // 1024) + 128 * ((n + 127) // 128) + 8 * k * n)
+            + 16 * ((n + 1023) // 1024) + 128 * ((n + 127) // 128) + 1024 * ((n + 1023) // 1024) + 8 * k * n)
 
 
 def pr_fused(L: dict, k: int, with_p0: bool = False) -> int:

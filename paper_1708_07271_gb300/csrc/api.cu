@@ -253,6 +253,8 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     fa.pcent = g->pcent;
     fa.tile_win = (const uint4*)g->tile_win;
     fa.lane_cols = g->lane_cols;
+    fa.row_order = g->row_order;
+    fa.row_groups = g->row_groups;
     fa.x = x;
     fa.ldx = ldx;
     fa.rowscale = rowscale;
@@ -638,8 +640,29 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
                     for (int q = 0; q < kCarryTile / 32; q++)
                         lane_cols[(size_t)t * 32 + l] |= (uint32_t)ord[q * 32 + l] << (8 * q);
             }
+            // the chain weights' row order: each aligned block of kFxNT rows
+            // sorted by descendant count, most first; the q-th 32 rows go to
+            // warp (q + b) mod 8 of block b, so that the heaviest rows fall to
+            // a different warp in each block
+            const int64_t rblocks = (n + kFxNT - 1) / kFxNT;
+            g->row_groups = (rblocks + 3) / 4;
+            std::vector<uint32_t> row_order((size_t)g->row_groups * kFxNT, 0u);
+            std::vector<int> rord(kFxNT), rcnt(kFxNT);
+            for (int64_t b = 0; b < rblocks; b++) {
+                for (int o = 0; o < kFxNT; o++) {
+                    const int64_t r = b * kFxNT + o;
+                    rcnt[o] = r < n ? __builtin_popcount(L->desc[r]) : -1;
+                    rord[o] = o;
+                }
+                std::stable_sort(rord.begin(), rord.end(), [&](int u, int v) { return rcnt[u] > rcnt[v]; });
+                for (int k = 0; k < kFxNT; k++) {
+                    const int pos = (((k >> 5) + (int)(b & 7)) & 7) * 32 + (k & 31);
+                    row_order[(size_t)(b >> 2) * kFxNT + pos] |= (uint32_t)rord[k] << (8 * (int)(b & 3));
+                }
+            }
             uint32_t* dwin = nullptr;
             if ((rc = upload_vec(&dwin, win, st, &g->bytes)) || (rc = upload_vec(&g->lane_cols, lane_cols, st, &g->bytes)) ||
+                (rc = upload_vec(&g->row_order, row_order, st, &g->bytes)) ||
                 (rc = dev_alloc((void**)&g->err, sizeof(unsigned int), nullptr))) {
                 if (dwin) cudaFree(dwin);
                 bvg_free_dev(g);
@@ -680,7 +703,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->err};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)

@@ -219,6 +219,8 @@ struct bvg_dev_graph {
     // entry or a carry source lies outside the tile's row window
     void* tile_win = nullptr;       // uint4 per tile: first and end row of its window, 1 if it reads a row outside
     uint32_t* lane_cols = nullptr;  // fused kernel: 32 words per group of kCarryTile columns, each lane's 4 columns
+    uint32_t* row_order = nullptr;  // fused kernel: the chain weights' row order, 256 words per 4 blocks of 256 rows
+    int64_t row_groups = 0;
     int64_t fx_tiles = 0, fx_far_tiles = 0;
     unsigned int* err = nullptr;    // device word: a bounded wait ran out (read and cleared by bvg_device_check)
     int pcol_state = 0;             // 0 not built, 1 built, -1 too many entries (the event columns serve)

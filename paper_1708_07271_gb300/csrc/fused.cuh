@@ -66,6 +66,7 @@ constexpr int kFxECap = 3520;              // entries per tile staged in shared 
 constexpr int kFxDescW = 2 * kFxT > kFxW + 8 ? 2 * kFxT : kFxW + 8;  // mask words; then one int64 per column
 constexpr long long kFxWaitCycles = 4000000000LL;  // bound of an mbarrier wait (about 2 s)
 static_assert(kFxCPT * 32 == kCarryTile, "a warp's columns form one carry tile");
+static_assert(kFxNT == 256 && kFxXR <= 8, "row_order: one byte per row of a 256-row block, at most 8 blocks per window");
 
 struct FxArgs {
     const uint32_t* desc;       // descendant masks, padded by 8 words (aligned bulk copies)
@@ -81,6 +82,11 @@ struct FxArgs {
     const uint32_t* lane_cols;  // per group of kCarryTile columns, 32 words: lane l's four columns (bytes q =
                                 // 0..3, offsets in the group), the group's columns sorted by entry count
                                 // (most first) and the q-th 32 given to slot q
+    const uint32_t* row_order;  // per 4 aligned blocks of kFxNT rows, kFxNT words: byte (b & 3) of word t is
+                                // the row (offset in block b) that thread t takes for the chain weights; each
+                                // block's rows sorted by descendant count, most first, the q-th 32 given to
+                                // warp (q + b) mod 8
+    int64_t row_groups;         // groups of 4 blocks in row_order
     const float* x;
     int64_t ldx;
     const float* rowscale;      // x_i * rowscale_i (PageRank's 1/outdeg), or NULL
@@ -267,6 +273,11 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         cr1 = __ldg(fa.carry_ptr + wc / kCarryTile + 1);
         if (cr0 + lane < cr1) csrc = __ldg(fa.carry + cr0 + lane);
     }
+    // the chain weights' row order for the window's aligned blocks (at most
+    // 8 blocks: 3 words), into L2 now, read after the window's x
+    const int64_t b0 = w0 >> 8, g0 = b0 >> 2;
+    if (tid < 3 * kFxNT / 32 && g0 + tid / (kFxNT / 32) < fa.row_groups)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(fa.row_order + (g0 + tid / (kFxNT / 32)) * kFxNT + (tid % (kFxNT / 32)) * 32));
     const uint32_t ct0 = __ldg(fa.carry_ptr + a / kCarryTile);
     const uint32_t ct1 = __ldg(fa.carry_ptr + (tend + kCarryTile - 1) / kCarryTile);
     if constexpr (EPI == 1) {
@@ -332,12 +343,26 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         __syncthreads();
         // chain weights: each window row adds the x of its descendants
         // (exact, in any order), held until every row has read, then stored
-        // in place
+        // in place. Rows go by aligned blocks of kFxNT in the row_order
+        // permutation, so that a warp's 32 rows have similar descendant
+        // counts (a warp's loop runs as long as its longest mask).
+        uint32_t ow[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) ow[k] = g0 + k < fa.row_groups ? __ldg(fa.row_order + (g0 + k) * kFxNT + tid) : 0u;
+        const int nb = W > 0 ? (int)(((w1 - 1) >> 8) - b0 + 1) : 0;
+        auto row_of = [&](int i) -> int {  // window row of this thread in block b0 + i (outside: >= W)
+            const int64_t b = b0 + i;
+            const int gk = (int)((b >> 2) - g0);
+            const uint32_t wv = gk == 0 ? ow[0] : (gk == 1 ? ow[1] : ow[2]);
+            return (int)((b << 8) + ((wv >> (8 * (int)(b & 3))) & 0xffu) - w0);
+        };
         long long zr[kFxXR];
 #pragma unroll
         for (int i = 0; i < kFxXR; i++) {
-            const int r = tid + i * kFxNT;
-            if (r >= W) break;
+            if (i >= nb) break;
+            const int r = row_of(i);
+            zr[i] = 0;
+            if ((unsigned)r >= (unsigned)W) continue;
             long long z = S.a.v[r];
             for (uint32_t m = S.desc[r + doff]; m; m &= m - 1) z += S.a.v[r + __ffs(m)];
             zr[i] = z;
@@ -345,9 +370,9 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kFxXR; i++) {
-            const int r = tid + i * kFxNT;
-            if (r >= W) break;
-            S.a.v[r] = zr[i];
+            if (i >= nb) break;
+            const int r = row_of(i);
+            if ((unsigned)r < (unsigned)W) S.a.v[r] = zr[i];
         }
         if (!mbar_wait(&S.bar[1], 0)) {
             atomicExch(fa.err, 1u);
