@@ -32,8 +32,8 @@
 //   - the interval sum: an exact integer prefix of the event sums, each warp
 //     starting from the z of the intervals open at its first column (the carry
 //     list of its 128 columns);
-//   - y_j = P_j + I_j, exact, rounded once to FP32 (integer rounding to
-//     nearest even, the scale folded into the exponent).
+//   - y_j = P_j + I_j, exact, rounded once to FP32 (the integer converted
+//     with rounding to nearest even, then scaled by an exact power of two).
 // Every result is the exactly rounded sum; an interval that opened and closed
 // earlier in the tile leaves nothing behind in the running sum.
 //
@@ -66,6 +66,7 @@ constexpr int kFxECap = 3520;              // entries per tile staged in shared 
 constexpr int kFxDescW = 2 * kFxT > kFxW + 8 ? 2 * kFxT : kFxW + 8;  // mask words; then one int64 per column
 constexpr long long kFxWaitCycles = 4000000000LL;  // bound of an mbarrier wait (about 2 s)
 static_assert(kFxCPT * 32 == kCarryTile, "a warp's columns form one carry tile");
+static_assert(kIdBits == 30, "entry words: bit 30 negates, bit 31 marks an interval event");
 static_assert(kFxNT == 256 && kFxXR <= 8, "row_order: one byte per row of a 256-row block, at most 8 blocks per window");
 
 struct FxArgs {
@@ -132,16 +133,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
 }
 
-// x (FP32) as an int64 multiple of 2^E: the 24-bit significand shifted left by
-// field + eshift (the exact path guarantees a shift >= 0 for nonzero x).
-__device__ __forceinline__ long long fx_of(float v, int eshift) {
-    const uint32_t b = __float_as_uint(v);
-    const int f = (int)((b >> 23) & 0xffu);
-    const uint32_t m = f ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
-    const int sh = (f ? f : 1) + eshift;
-    unsigned long long u = m;
-    u = sh >= 0 ? (u << sh) : 0ull;
-    return (b >> 31) ? -(long long)u : (long long)u;
+// 2^s as FP32, -126 <= s <= 127.
+__device__ __forceinline__ float pow2f(int s) { return __uint_as_float((uint32_t)(s + 127) << 23); }
+
+// x (FP32) as an int64 multiple of 2^E: x * 2^-E, an integer whenever the
+// lowest significand bit of x weighs at least 2^E (the exact path's rule).
+// The scaling by powers of two is exact (its result is an integer below
+// 2^62, a normal float), and so is the conversion.
+__device__ __forceinline__ long long fx_of(float v, int E) {
+    const int s = -E;
+    const float t = s >= -126 && s <= 127 ? __fmul_rn(v, pow2f(s))
+                                          : __fmul_rn(__fmul_rn(v, pow2f(s / 2)), pow2f(s - s / 2));
+    return __float2ll_rn(t);
 }
 
 __device__ __forceinline__ long long shfl_xor_ll(long long v, int o) {
@@ -170,31 +173,14 @@ __device__ __forceinline__ float fl_far_z(const FxArgs& fa, int64_t k) {
 // Bits needed for c (ceil(log2(c + 1))).
 __device__ __forceinline__ int bits_for(uint32_t c) { return 32 - __clz(c); }
 
-// v * 2^E rounded once to FP32 (to nearest, ties to even): the integer's top
-// 24 bits rounded by the rest, the scale folded into the exponent. Results
-// outside the normal range are scaled in two steps (a second rounding only
-// for subnormal results).
+// v * 2^E rounded once to FP32: v converted with rounding to nearest (ties
+// to even), then scaled by 2^E, exactly unless the result is subnormal (a
+// second rounding only then). Scales outside the normal range go in two
+// steps, the first exact.
 __device__ __forceinline__ float fx_to_float(long long v, int E) {
-    if (v == 0) return 0.f;
-    const uint32_t sgn = v < 0 ? 0x80000000u : 0u;
-    unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int lz = __clzll((long long)u);
-    u <<= lz;  // leading one at bit 63
-    uint32_t m = (uint32_t)(u >> 40);
-    const unsigned long long rem = u & 0xFFFFFFFFFFull, half = 1ull << 39;
-    if (rem > half || (rem == half && (m & 1u))) m++;
-    int p = 63 - lz;
-    if (m == (1u << 24)) {
-        m >>= 1;
-        p++;
-    }
-    const int e = p + E + 127;
-    if (e >= 1 && e <= 254) return __uint_as_float(sgn | ((uint32_t)e << 23) | (m & 0x7fffffu));
-    const int s = p + E, s1 = s / 2, s2 = s - s1;  // |s1|, |s2| <= 126 + 63
-    float f = __uint_as_float(sgn | (127u << 23) | (m & 0x7fffffu));
-    const float f1 = __uint_as_float((uint32_t)min(max(s1 + 127, 1), 254) << 23);
-    const float f2 = __uint_as_float((uint32_t)min(max(s2 + 127, 1), 254) << 23);
-    return __fmul_rn(__fmul_rn(f, f1), f2);
+    const float f = __ll2float_rn(v);
+    if (E >= -126 && E <= 127) return __fmul_rn(f, pow2f(E));
+    return __fmul_rn(__fmul_rn(f, pow2f(E / 2)), pow2f(E - E / 2));
 }
 
 // Shared memory of a tile. The exact path's arrays and the compensated
@@ -322,6 +308,7 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
     // prefix sum at most the tile's entries plus its carry sources
     const int hz = 6 + bits_for((E1 - E0) + (ct1 - ct0) + 1);
     const int eshift = 38 - hz - (int)vmax;  // a significand with exponent field f shifts left by f + eshift
+    const int E = -150 - eshift;             // the integers count units of 2^E
     // exact path: every source row lies in the window, every nonzero x
     // converts without loss and nothing is non-finite; the compensated path
     // otherwise
@@ -333,7 +320,7 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         for (int i = 0; i < kFxXR; i++) {
             const int r = tid + i * kFxNT;
             if (r >= PX) break;
-            S.a.v[r] = fx_of(xv[i], eshift);
+            S.a.v[r] = fx_of(xv[i], E);
         }
         if (!mbar_wait(&S.bar[0], 0)) {
             atomicExch(fa.err, 1u);
@@ -394,17 +381,16 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         long long* Ds = reinterpret_cast<long long*>(S.desc) + warp * kCarryTile;
         long long A[kFxCPT];
         auto column = [&](auto&& word, int q) {
-            long long p = 0, d = 0;
-            for (uint32_t e = cb[q]; e < ce[q]; e++) {
+            long long a = 0, d = 0;
+            for (uint32_t e = cb[q]; e < ce[q]; e++) {  // branch-free: the lanes' loops differ in length only
                 const uint32_t w = word(e);
                 long long z = zv[id_of(w)];
-                if (w & (1u << kIdBits)) z = -z;  // a dropped id, or an interval ending here
-                if (w >> (kIdBits + 1))           // an interval start or end event
-                    d += z;
-                else
-                    p += z;
+                const long long ng = (int)(w << 1) >> 31;  // -1: a dropped id, or an interval ending here
+                z = (z ^ ng) - ng;
+                a += z;
+                d += z & (long long)((int)w >> 31);        // an interval start or end event
             }
-            A[q] = p + d;
+            A[q] = a;
             Ds[(oc >> (8 * q)) & 0xffu] = d;
         };
         if (staged) {
@@ -443,7 +429,6 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             run += dq[q];
         }
         __syncwarp();
-        const int E = (int)vmax - 188 + hz;  // the integers count units of 2^E
 #pragma unroll
         for (int q = 0; q < kFxCPT; q++) yv[q] = fx_to_float(A[q] + Ds[(oc >> (8 * q)) & 0xffu], E);
     } else {
