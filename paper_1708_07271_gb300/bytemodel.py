@@ -19,7 +19,7 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
                group owns a column and the tail items are shared out] + 4kn (z) + 4kn (y)
   csr          8(n+1) (row offsets) + 4m (ids) + 4kn (x) + 4kn (y)
   push_fused   (one right-hand side, one kernel) 4n (descendant masks) + 4(n+1) (column
-               offsets) + 4*col_entries + 4*(carry_tiles+1) + 4*carry_entries
+               offsets) + 2*col_entries (16-bit entries) + 4*(carry_tiles+1) + 4*carry_entries
                + 16*ceil(n/1024) (per-tile row windows) + 4*32*ceil(n/128) (each warp's
                column order) + 1024*ceil(n/1024) (the chain weights' row order) + 4n (x)
                + 4n (y); the chain weights never leave shared
@@ -79,7 +79,7 @@ def pr_gather_pt(L: dict, k: int, with_p0: bool) -> int:
 
 def push_fused(L: dict, k: int) -> int:
     n = L["n"]
-    return (4 * n + 4 * (n + 1) + 4 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
+    return (4 * n + 4 * (n + 1) + 2 * L["col_entries"] + 4 * (L["carry_tiles"] + 1) + 4 * L["carry_entries"]
             + 16 * ((n + 1023) // 1024) + 128 * ((n + 127) // 128) + 1024 * ((n + 1023) // 1024) + 8 * k * n)
 
 

@@ -246,7 +246,7 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     FxArgs fa{};
     fa.desc = g->desc;
     fa.colp = g->colp;
-    fa.tent = g->tent;
+    fa.tent16 = g->tent16;
     fa.carry_ptr = g->carry_ptr;
     fa.carry = g->carry;
     fa.pcolp = g->pcolp;
@@ -590,6 +590,9 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
         {
             const int64_t tiles = (n + kFxT - 1) / kFxT;
             std::vector<uint32_t> win((size_t)tiles * 4, 0u);
+            // and the tile's entries as 16-bit window offsets (with the two
+            // flags), for the tiles whose sources lie in their window
+            std::vector<uint16_t> tent16((L->tent.size() + 7) / 8 * 8 + 8, (uint16_t)0);
             int64_t nfar = 0;
             for (int64_t t = 0; t < tiles; t++) {
                 const int64_t a = t * kFxT, e = std::min<int64_t>(n, a + kFxT);
@@ -613,6 +616,9 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
                     lo = std::max<int64_t>(0, std::min<int64_t>(a - (kFxW - kFxT) / 2, n - kFxW));
                     hi = std::min<int64_t>(n, lo + kFxW) - 1;
                 }
+                if (!far)
+                    for (uint32_t q = L->colp[a]; q < L->colp[e]; q++)
+                        tent16[q] = (uint16_t)(((L->tent[q] & kIdMask) - (uint32_t)lo) | ((L->tent[q] >> kIdBits) << 14));
                 win[(size_t)t * 4] = (uint32_t)lo;
                 win[(size_t)t * 4 + 1] = (uint32_t)(hi + 1);
                 win[(size_t)t * 4 + 2] = far;
@@ -663,6 +669,7 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             uint32_t* dwin = nullptr;
             if ((rc = upload_vec(&dwin, win, st, &g->bytes)) || (rc = upload_vec(&g->lane_cols, lane_cols, st, &g->bytes)) ||
                 (rc = upload_vec(&g->row_order, row_order, st, &g->bytes)) ||
+                (rc = upload_vec(&g->tent16, tent16, st, &g->bytes)) ||
                 (rc = dev_alloc((void**)&g->err, sizeof(unsigned int), nullptr))) {
                 if (dwin) cudaFree(dwin);
                 bvg_free_dev(g);
@@ -703,7 +710,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->err};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->tent16, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)

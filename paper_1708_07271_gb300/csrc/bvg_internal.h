@@ -218,6 +218,7 @@ struct bvg_dev_graph {
     // fused one-vector push (fused.cuh): per tile of its columns, 1 if an
     // entry or a carry source lies outside the tile's row window
     void* tile_win = nullptr;       // uint4 per tile: first and end row of its window, 1 if it reads a row outside
+    uint16_t* tent16 = nullptr;     // fused kernel: event-column entries as window offsets (16-bit, see FxArgs)
     uint32_t* lane_cols = nullptr;  // fused kernel: 32 words per group of kCarryTile columns, each lane's 4 columns
     uint32_t* row_order = nullptr;  // fused kernel: the chain weights' row order, 256 words per 4 blocks of 256 rows
     int64_t row_groups = 0;

@@ -5,8 +5,10 @@
 // A CTA owns kFxT consecutive columns [a, a + kFxT) and computes, in shared
 // memory, everything its columns need:
 //   1. the descendant masks of a window of rows around the tile and the
-//      tile's column-major entries, by two TMA bulk copies (cp.async.bulk,
-//      mbarrier completion), and x of the window rows (coalesced loads);
+//      tile's column-major entries (16-bit words: the source row's offset in
+//      the window and two flags, built at upload), by two TMA bulk copies
+//      (cp.async.bulk, mbarrier completion), and x of the window rows
+//      (coalesced loads; the entries' copy is issued once x has arrived);
 //   2. the chain weights z of the window rows;
 //   3. each thread's 4 columns: +-z_k of their entries into the column's
 //      point sum or event sum. On the exact path a warp's 128 columns are
@@ -62,17 +64,20 @@ constexpr int kFxNT = 256;                 // threads per CTA
 constexpr int kFxCPT = kFxT / kFxNT;       // consecutive columns per thread: a warp's 128 = one carry tile
 constexpr int kFxW = 1792;                 // most window rows: the span of the rows a tile reads (set at upload)
 constexpr int kFxXR = (kFxW + kHalo + kFxNT - 1) / kFxNT;  // window rows whose x a thread loads
-constexpr int kFxECap = 3520;              // entries per tile staged in shared memory (more: read from global)
+constexpr int kFxECap = 7040;              // entries per tile staged in shared memory (more: read from global)
+constexpr uint32_t kFxOffMask = 0x3fffu;   // 16-bit entry: the source row's offset in the tile's window
 constexpr int kFxDescW = 2 * kFxT > kFxW + 8 ? 2 * kFxT : kFxW + 8;  // mask words; then one int64 per column
 constexpr long long kFxWaitCycles = 4000000000LL;  // bound of an mbarrier wait (about 2 s)
 static_assert(kFxCPT * 32 == kCarryTile, "a warp's columns form one carry tile");
-static_assert(kIdBits == 30, "entry words: bit 30 negates, bit 31 marks an interval event");
+static_assert(kFxW <= (int)kFxOffMask + 1, "a window offset fits the 16-bit entry");
 static_assert(kFxNT == 256 && kFxXR <= 8, "row_order: one byte per row of a 256-row block, at most 8 blocks per window");
 
 struct FxArgs {
     const uint32_t* desc;       // descendant masks, padded by 8 words (aligned bulk copies)
     const uint32_t* colp;       // event columns
-    const uint32_t* tent;       // padded by 4 words (aligned bulk copies)
+    const uint16_t* tent16;     // the event columns' entries as 16-bit words, for tiles not flagged far: the
+                                // source row's offset in the tile's row window (bits 0-13), negated (bit 14),
+                                // an interval event (bit 15); padded by 8 entries (aligned bulk copies)
     const uint32_t* carry_ptr;
     const uint32_t* carry;
     const uint32_t* pcolp;      // point columns (compensated path)
@@ -195,7 +200,7 @@ struct FxSmem {
     } a;
     alignas(16) uint32_t desc[kFxDescW];    // descendant masks of the window (16-byte aligned superset); after
                                             // the chain weights, the exact path's per-column event sums
-    alignas(16) uint32_t ent[kFxECap + 8];  // the tile's event-column entries (16-byte aligned superset), exact path
+    alignas(16) uint16_t ent[kFxECap + 8];  // the tile's event-column entries (16-byte aligned superset), exact path
     uint64_t bar[2];                // mbarriers: [0] masks, [1] entries
     unsigned int emax, emin, state;
 };
@@ -230,15 +235,12 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
     __syncthreads();
     // structure reads that do not depend on x
     const uint32_t E0 = __ldg(fa.colp + a), E1 = __ldg(fa.colp + tend);
-    const uint32_t e0a = E0 & ~3u, e1a = (E1 + 3u) & ~3u;
+    const uint32_t e0a = E0 & ~7u, e1a = (E1 + 7u) & ~7u;
     const bool staged = e1a - e0a <= (uint32_t)(kFxECap + 8);
     if (tid == 0) {
         const uint32_t bd = (uint32_t)((d1a - d0a) * 4);
         mbar_expect_tx(&S.bar[0], bd);
         bulk_g2s(S.desc, fa.desc + d0a, bd, &S.bar[0]);
-        const uint32_t be = staged ? (e1a - e0a) * 4u : 0u;
-        mbar_expect_tx(&S.bar[1], be);
-        if (be) bulk_g2s(S.ent, fa.tent + e0a, be, &S.bar[1]);
     }
     const int64_t c0 = a + (int64_t)tid * kFxCPT;
     const int64_t wc = a + (int64_t)warp * kCarryTile;  // this warp's first column
@@ -271,7 +273,7 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         // past convergence or max_iter the update does nothing (the state was
         // written by the previous update; the same value in every thread)
         if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) {
-            const bool ok = mbar_wait(&S.bar[0], 0) && mbar_wait(&S.bar[1], 0);  // no copy may stay in flight
+            const bool ok = mbar_wait(&S.bar[0], 0);  // no copy may stay in flight (the entries' is not issued yet)
             if (!ok) atomicExch(fa.err, 1u);
             return;
         }
@@ -299,6 +301,14 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         atomicMin(&S.emin, bmin);
     }
     __syncthreads();
+    // the tile's entries, once the window's x has arrived: the entry copy
+    // lands during the conversion and the chain weights, and the x loads do
+    // not queue behind it
+    if (tid == 0) {
+        const uint32_t be = staged ? (e1a - e0a) * 2u : 0u;
+        mbar_expect_tx(&S.bar[1], be);
+        if (be) bulk_g2s(S.ent, fa.tent16 + e0a, be, &S.bar[1]);
+    }
     // exponent fields: the largest (255: a non-finite value), and the one of
     // the lowest significand bit of the smallest nonzero magnitude (255: no
     // nonzero value)
@@ -384,22 +394,22 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
             long long a = 0, d = 0;
             for (uint32_t e = cb[q]; e < ce[q]; e++) {  // branch-free: the lanes' loops differ in length only
                 const uint32_t w = word(e);
-                long long z = zv[id_of(w)];
-                const long long ng = (int)(w << 1) >> 31;  // -1: a dropped id, or an interval ending here
+                long long z = S.a.v[w & kFxOffMask];
+                const long long ng = (int)(w << 17) >> 31;  // -1: a dropped id, or an interval ending here
                 z = (z ^ ng) - ng;
                 a += z;
-                d += z & (long long)((int)w >> 31);        // an interval start or end event
+                d += z & (long long)((int)(w << 16) >> 31);  // an interval start or end event
             }
             A[q] = a;
             Ds[(oc >> (8 * q)) & 0xffu] = d;
         };
         if (staged) {
-            const uint32_t* ent = S.ent - e0a;
+            const uint16_t* ent = S.ent - e0a;
 #pragma unroll
-            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return ent[e]; }, q);
+            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return (uint32_t)ent[e]; }, q);
         } else {
 #pragma unroll
-            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return __ldg(fa.tent + e); }, q);
+            for (int q = 0; q < kFxCPT; q++) column([&](uint32_t e) { return (uint32_t)__ldg(fa.tent16 + e); }, q);
         }
         // running interval sum, in column order: this warp's carry, then its
         // columns in order; each column's running sum goes back to the lane
