@@ -347,11 +347,12 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
 #pragma unroll
         for (int k = 0; k < 3; k++) ow[k] = g0 + k < fa.row_groups ? __ldg(fa.row_order + (g0 + k) * kFxNT + tid) : 0u;
         const int nb = W > 0 ? (int)(((w1 - 1) >> 8) - b0 + 1) : 0;
-        auto row_of = [&](int i) -> int {  // window row of this thread in block b0 + i (outside: >= W)
-            const int64_t b = b0 + i;
-            const int gk = (int)((b >> 2) - g0);
-            const uint32_t wv = gk == 0 ? ow[0] : (gk == 1 ? ow[1] : ow[2]);
-            return (int)((b << 8) + ((wv >> (8 * (int)(b & 3))) & 0xffu) - w0);
+        // the window's 8 row-order bytes (blocks b0 .. b0 + 7) lined up in two words
+        const int s0 = (int)(b0 & 3);
+        const uint32_t u0 = __funnelshift_r(ow[0], ow[1], 8 * s0), u1 = __funnelshift_r(ow[1], ow[2], 8 * s0);
+        const int rb = (int)((b0 << 8) - w0);  // block b0's first row in the window (-255 .. 0)
+        auto row_of = [&](int i) -> int {     // window row of this thread in block b0 + i (outside: >= W)
+            return rb + (i << 8) + (int)(((i < 4 ? u0 : u1) >> (8 * (i & 3))) & 0xffu);
         };
         long long zr[kFxXR];
 #pragma unroll
