@@ -86,9 +86,15 @@ class RowSharded:
     masked A (full-length vectors, row-major n x k torch tensors on the
     rank's device): the CUDA path on a GPU rank (bvg_spmv_Ax / bvg_spmv_xA on
     the encoding of masked_csr), any stand-in elsewhere. The exchanges:
-      A x^T: each rank forms its own rows; one all-gather of the row blocks;
-      x A:   each rank forms a full-length partial sum over its rows; one
-             all-reduce (sum) of n x k values.
+      A x^T:      each rank forms its own rows; one all-gather of the row
+                  blocks;
+      x A owned:  each rank forms a full-length partial sum over its rows;
+                  one reduce-scatter leaves each rank the sum over all ranks
+                  of its own block of entries (a ring moves (P-1)/P of the
+                  n x k partial per rank);
+      x A:        the same partials, one all-reduce (sum): every rank holds
+                  all of y, twice the bytes of the reduce-scatter; the power
+                  iteration needs the whole iterate on every rank.
     """
 
     def __init__(self, n: int, blocks, rank: int, local_Ax, local_xA):
@@ -112,10 +118,27 @@ class RowSharded:
         return out
 
     def xA(self, x):
+        """All of y = x A on every rank (all-reduce of the partial sums)."""
         import torch.distributed as dist
         y = self.local_xA(x)
         dist.all_reduce(y)
         return y
+
+    def xA_owned(self, x):
+        """This rank's block [lo, hi) of y = x A (reduce-scatter of the
+        partial sums to the block owners; blocks padded to the widest)."""
+        import torch
+        import torch.distributed as dist
+        y = self.local_xA(x)
+        width = max(b - a for a, b in self.blocks)
+        rest = tuple(y.shape[1:])
+        buf = torch.zeros((len(self.blocks) * width,) + rest, dtype=y.dtype, device=y.device)
+        for r, (a, b) in enumerate(self.blocks):
+            buf[r * width:r * width + (b - a)] = y[a:b]
+        out = torch.empty((width,) + rest, dtype=y.dtype, device=y.device)
+        dist.reduce_scatter_tensor(out, buf)
+        lo, hi = self.blocks[self.rank]
+        return out[:hi - lo]
 
     def pagerank(self, inv_outdeg, alpha: float = 0.15, tol: float = 1e-8, max_iter: int = 1000):
         """Power iteration of Eq. 1 (uniform teleport, dangling mass returned

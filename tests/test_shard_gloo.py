@@ -134,16 +134,17 @@ def _row_worker(rank, world, port, q):
         x = torch.from_numpy(synth.rhs(g.n, 3, 9))
         ax = sh.Ax(x).numpy()
         xa = sh.xA(x).numpy()
+        xa_owned = sh.xA_owned(x).numpy()
         deg = np.diff(g.row_ptr)
         inv = torch.from_numpy(np.where(deg > 0, 1.0 / np.maximum(deg, 1), 0).astype(np.float32))
         p, it, res = sh.pagerank(inv, tol=1e-9)
-        q.put((rank, ax, xa, p.numpy(), it, res))
+        q.put((rank, ax, xa, p.numpy(), it, res, xa_owned, blocks[rank]))
     finally:
         dist.destroy_process_group()
 
 
-def test_row_sharded_products_and_pagerank_two_ranks():
-    world = 2
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_sharded_products_and_pagerank(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -158,8 +159,13 @@ def test_row_sharded_products_and_pagerank_two_ranks():
     x = synth.rhs(g.n, 3, 9).astype(np.float64)
     want_ax, want_xa = oracle.csr_Ax(g.row_ptr, g.col, x), oracle.csr_xA(g.row_ptr, g.col, x)
     pstar, _, _ = oracle.pagerank(g.row_ptr, g.col, alpha=0.15, tol=1e-13, max_iter=3000, dangling=1)
-    for rank, ax, xa, p, it, r in res:
+    for rank, ax, xa, p, it, r, xa_owned, (lo, hi) in res:
         np.testing.assert_allclose(ax, want_ax, rtol=1e-5, atol=1e-5)
         np.testing.assert_allclose(xa, want_xa, rtol=1e-5, atol=1e-5)
+        # the reduce-scatter: this rank's block only, the same sums as the all-reduce
+        assert xa_owned.shape == (hi - lo, 3)
+        np.testing.assert_allclose(xa_owned, want_xa[lo:hi], rtol=1e-5, atol=1e-5)
         assert r < 1e-9 and np.abs(p - pstar[:, 0]).sum() <= 1e-6
-    np.testing.assert_array_equal(res[0][2], res[1][2])  # every rank holds the same iterate
+    assert [b for *_, b in res] == shard.row_blocks(g.row_ptr, world)
+    for other in res[1:]:
+        np.testing.assert_array_equal(res[0][3], other[3])  # every rank holds the same iterate
