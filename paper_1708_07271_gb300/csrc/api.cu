@@ -291,11 +291,28 @@ static void launch_gather(const bvg_dev_graph* g, const float* z, int64_t ldz, f
                (const uint32_t*)g->carry_ptr, (const uint32_t*)g->carry, z, ldz, y, ldy,
                g->n, pa);
 }
+// CTAs of `kernel` (nt threads, static shared memory only) resident on the
+// current device at once.
+static int64_t resident_ctas(const void* kernel, int nt) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return INT64_MAX;  // one tile per CTA, as without the loop
+    }
+    return (int64_t)sms * std::max(per_sm, 1);
+}
+
 template <int KB, int V>
 static void launch_gather_pr(const bvg_dev_graph* g, const float* z, int64_t ldz, const PrArgs& pa, cudaStream_t st) {
     const int tile = gather_tile(KB, V, g->cfg);
-    const int64_t grid = (g->n + tile - 1) / tile;
-    if (use_points(g, KB)) {
+    const int64_t tiles = (g->n + tile - 1) / tile;
+    // a resident grid: the CTAs loop over the tiles and reduce once each
+    const bool pt = use_points(g, KB);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, resident_ctas(pt ? (const void*)k_gather_pt<KB, V, 1>
+                                                                                   : (const void*)k_gather<KB, V, 1>,
+                                                                                GatherShape<KB, V>::NT)));
+    if (pt) {
         TraceScope ts(g, "pr_gather_pt", st);
         launch_pdl(g->cfg.gather_pdl, k_gather_pt<KB, V, 1>, grid, GatherShape<KB, V>::NT, st,
                    (const uint32_t*)g->pcolp, (const uint32_t*)g->pcent, (const uint32_t*)g->ptitem_ptr,

@@ -85,13 +85,14 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather_batch(const B
                                                       int64_t c0) {
     const BatchEntry e = tab[find_graph<1>(tab, count, blockIdx.x)];
     PrArgs pa{};
+    df unused = df_zero();
     const int64_t blk = (int64_t)blockIdx.x - e.gather_tile0;
     if (e.points)
         gather_tile<KB, V, 0, false>(blk, e.colp, e.tent, e.titem_ptr, e.titem, nullptr, nullptr, e.long_chunk, e.z, KB,
-                                     e.y + c0, ld, e.n, pa);
+                                     e.y + c0, ld, e.n, pa, unused);
     else
         gather_tile<KB, V, 0, true>(blk, e.colp, e.tent, e.titem_ptr, e.titem, e.carry_ptr, e.carry, nullptr, e.z, KB,
-                                    e.y + c0, ld, e.n, pa);
+                                    e.y + c0, ld, e.n, pa, unused);
 }
 
 }  // namespace bvg

@@ -597,10 +597,12 @@ __device__ __forceinline__ double pr_warp_sum(const double* __restrict__ base, i
 // warp's shuffle tree adds them in FP32 (a few roundings relative to the
 // warp's sum of nonnegative terms); the warps are then combined compensated.
 template <int KB, int V, bool F32WARP = false>
-__device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArgs& pa, bool init) {
+__device__ df pr_block_sum(df (&S)[V], df (&R)[V], df (&Dg)[V]) {
+    // the CTA's sums: thread f * KB + c (< 3 KB) returns quantity f (0: sum
+    // q, 1: sum |q - p_prev|, 2: dangling mass) of right-hand side c, every
+    // other thread zero; ends on a barrier (the shared array may be reused)
     constexpr int G = KB / V;
     __shared__ df sh_part[32][3][KB];
-    __shared__ bool sh_last;
     const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; v++) {
@@ -625,10 +627,23 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
         }
     }
     __syncthreads();
+    df t = df_zero();
     if (threadIdx.x < 3 * KB) {
         const int f = threadIdx.x / KB, c = threadIdx.x % KB;
-        df t = df_zero();
         for (int w = 0; w < NW; w++) t = df_add(t, sh_part[w][f][c]);
+    }
+    __syncthreads();
+    return t;
+}
+
+// The grid's sums from each CTA's (pr_block_sum's t, possibly accumulated
+// over several tiles), and the update's scalars and state.
+template <int KB>
+__device__ void pr_grid_sum(df t, const PrArgs& pa, bool init) {
+    __shared__ bool sh_last;
+    const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+    if (threadIdx.x < 3 * KB) {
+        const int f = threadIdx.x / KB, c = threadIdx.x % KB;
         pa.partial[((int64_t)blockIdx.x * 3 + f) * KB + c] = (double)t.hi + (double)t.lo;
         __threadfence();
     }
@@ -686,6 +701,11 @@ __device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArg
     }
 }
 
+template <int KB, int V, bool F32WARP = false>
+__device__ void pr_block_reduce(df (&S)[V], df (&R)[V], df (&Dg)[V], const PrArgs& pa, bool init) {
+    pr_grid_sum<KB>(pr_block_sum<KB, V, F32WARP>(S, R, Dg), pa, init);
+}
+
 // The FP32 sum sr of one run of point entries [e0, min(e0 + kTailItem, e1))
 // (signs applied by an exact FMA with +-1).
 template <int V>
@@ -714,15 +734,19 @@ __device__ __forceinline__ void point_run(float (&sr)[V], uint32_t e0, uint32_t 
 
 // One tile of the gather (columns [blk * T, blk * T + T)); shared by the
 // one-graph and the multi-graph kernels.
+// Returns false when a PageRank update finds the iteration finished (past
+// convergence or max_iter: nothing done); EPI = 1 adds the tile's block sums
+// (pr_block_sum) into acc.
 template <int KB, int V, int EPI, bool EV>
-__device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restrict__ colp,
+__device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restrict__ colp,
                                             const uint32_t* __restrict__ tent,
                                             const uint32_t* __restrict__ titem_ptr,
                                             const uint32_t* __restrict__ titem,
                                             const uint32_t* __restrict__ carry_ptr,
                                             const uint32_t* __restrict__ carry,
                                             const uint8_t* __restrict__ long_chunk, const float* z, int64_t ldz,
-                                            float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
+                                            float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa,
+                                            df& acc) {
     using Sh = GatherShape<KB, V>;
     constexpr int G = Sh::G, T = Sh::T, CPT = Sh::CPT, NT = Sh::NT, NW = NT / 32;
     constexpr int S = EV ? Sh::S : kPointSlots;
@@ -792,7 +816,7 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");  // z (and the PageRank state) are ready
     if constexpr (EPI == 1) {
-        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+        if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return false;
     }
 
     // running interval sum at column a: the carry sources' z, one thread per
@@ -1184,7 +1208,35 @@ __device__ __forceinline__ void gather_tile(int64_t blk, const uint32_t* __restr
             Rd[v] = {R[v], 0.f};
             Dd[v] = {Dg[v], 0.f};
         }
-        pr_block_reduce<KB, V, true>(Sd, Rd, Dd, pa, false);
+        acc = df_add(acc, pr_block_sum<KB, V, true>(Sd, Rd, Dd));
+    }
+    return true;
+}
+
+// A PageRank update's gather: a resident grid, each CTA taking tiles blk,
+// blk + gridDim.x, ... and adding their block sums, then one grid-wide
+// reduction (one per CTA instead of one per 128-column tile). The product
+// (EPI = 0): one tile per CTA.
+template <int KB, int V, int EPI, bool EV>
+__device__ __forceinline__ void gather_grid(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
+                                           const uint32_t* __restrict__ titem_ptr,
+                                           const uint32_t* __restrict__ titem,
+                                           const uint32_t* __restrict__ carry_ptr,
+                                           const uint32_t* __restrict__ carry,
+                                           const uint8_t* __restrict__ long_chunk, const float* z, int64_t ldz,
+                                           float* __restrict__ y, int64_t ldy, int64_t n, const PrArgs& pa) {
+    df acc = df_zero();
+    if constexpr (EPI == 0) {
+        gather_tile<KB, V, EPI, EV>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, long_chunk, z, ldz, y,
+                                    ldy, n, pa, acc);
+    } else {
+        constexpr int T = GatherShape<KB, V>::T;
+        const int64_t tiles = (n + T - 1) / T;
+        for (int64_t blk = blockIdx.x; blk < tiles; blk += gridDim.x)
+            if (!gather_tile<KB, V, EPI, EV>(blk, colp, tent, titem_ptr, titem, carry_ptr, carry, long_chunk, z, ldz,
+                                             y, ldy, n, pa, acc))
+                return;  // the same answer in every CTA: no CTA reduces
+        pr_grid_sum<KB>(acc, pa, false);
     }
 }
 
@@ -1196,8 +1248,7 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT) k_gather(const uint32_
                                                 const uint32_t* __restrict__ carry, const float* z, int64_t ldz,
                                                 float* __restrict__ y, int64_t ldy, int64_t n,
                                                 PrArgs pa) {
-    gather_tile<KB, V, EPI, true>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, nullptr, z, ldz, y, ldy,
-                                  n, pa);
+    gather_grid<KB, V, EPI, true>(colp, tent, titem_ptr, titem, carry_ptr, carry, nullptr, z, ldz, y, ldy, n, pa);
 }
 
 // The gather over point columns (gather_tile with EV = false)
@@ -1214,8 +1265,7 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT
                                                                        const float* z, int64_t ldz,
                                                                        float* __restrict__ y, int64_t ldy, int64_t n,
                                                                        PrArgs pa) {
-    gather_tile<KB, V, EPI, false>(blockIdx.x, colp, ent, titem_ptr, titem, nullptr, nullptr, long_chunk, z, ldz, y,
-                                   ldy, n, pa);
+    gather_grid<KB, V, EPI, false>(colp, ent, titem_ptr, titem, nullptr, nullptr, long_chunk, z, ldz, y, ldy, n, pa);
 }
 
 // PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
@@ -1256,7 +1306,9 @@ __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_ini
     pr_block_reduce<KB, V>(S, R, Dg, pa, true);
 }
 
-// p_out = q_T / S_T for the final update T (read from the state).
+// p_out = q_T / S_T for the final update T (read from the state): 1/S_T
+// rounded to FP32 once per right-hand side, each value scaled in FP32 (FP64
+// arithmetic runs at a small fraction of the FP32 rate on this part).
 template <int KB, int V>
 __global__ void k_pr_final(const float* __restrict__ q0, const float* __restrict__ q1, int64_t ldq,
                            const double* __restrict__ sc0, const double* __restrict__ sc1,
@@ -1268,10 +1320,13 @@ __global__ void k_pr_final(const float* __restrict__ q0, const float* __restrict
     const int64_t gid = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
     const int lane = threadIdx.x % G;
     const int64_t stride = (int64_t)gridDim.x * (blockDim.x / G);
+    float scv[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) scv[v] = (float)__ldcg(sc + lane * V + v);
     for (int64_t j = gid; j < n; j += stride) {
         Vec<V> qv = ldv_cg<V>(q + j * ldq + lane * V), o;
 #pragma unroll
-        for (int v = 0; v < V; v++) o.v[v] = (float)((double)qv.v[v] * __ldcg(sc + lane * V + v));
+        for (int v = 0; v < V; v++) o.v[v] = __fmul_rn(qv.v[v], scv[v]);
         stv<V>(out + j * ldo + lane * V, o);
     }
 }
