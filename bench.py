@@ -588,8 +588,31 @@ def warmstart_leg(args, bvg, synth, torch, dg, g, pr_s, pr_it):
         runs.append((time.perf_counter() - t0, it, float(res[0]), rc))
     runs.sort()
     s, it, res, rc = runs[len(runs) // 2]
+    # the prediction alone (features, network, normalisation), against the
+    # time of one update, and the net effect on the solve
+    pts = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bvg.bvg_warmstart_predict(net, dg, out=p_init)
+        torch.cuda.synchronize()
+        pts.append(time.perf_counter() - t0)
+    predict_s = float(np.median(pts))
+    per_update = pr_s / max(pr_it, 1)
+    saved = pr_it - it
+    break_even = predict_s / per_update
+    if s >= pr_s:
+        finding = (f"negative result: the learned start saves {saved} of {pr_it} updates, but its features and "
+                   f"prediction take as long as {break_even:.1f} updates, so the solve is {1e3 * (s - pr_s):.2f} ms "
+                   f"slower; the error left after the first updates lies in long-wavelength modes along the id order, "
+                   f"which per-node features do not see")
+    else:
+        finding = (f"the learned start saves {saved} of {pr_it} updates and costs {break_even:.1f} updates' time: "
+                   f"{1e3 * (pr_s - s):.2f} ms faster")
     return {"graph": workload_name(g), "seconds": s, "iterations": it, "l1_resid": res, "status": rc,
-            "uniform_seconds": pr_s, "uniform_iterations": pr_it, "train_seconds": train_s, "train_loss": loss,
+            "uniform_seconds": pr_s, "uniform_iterations": pr_it, "predict_seconds": predict_s,
+            "updates_saved": saved, "break_even_updates": break_even, "finding": finding,
+            "train_seconds": train_s, "train_loss": loss,
             "train_graphs": len(sizes), "train_nodes": int(sum(int(v) for v in sizes))}
 
 

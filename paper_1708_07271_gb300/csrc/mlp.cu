@@ -291,19 +291,26 @@ __global__ void __launch_bounds__(256) k_floor_sum(const float* __restrict__ yha
 }
 
 // p /= sum(partials); a non-finite or non-positive sum falls back to 1/n.
-__global__ void k_normalize(float* __restrict__ p, int64_t n, const double* __restrict__ part, int nparts) {
-    __shared__ double tot;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nparts; i++) s += part[i];
-        tot = s;
-    }
+// Every CTA adds the partials the same way (its threads strided over them,
+// then a fixed tree); each value is scaled by 1/sum rounded once to FP32
+// (FP64 division per value would run at the small FP64 rate of this part).
+__global__ void __launch_bounds__(256) k_normalize(float* __restrict__ p, int64_t n, const double* __restrict__ part,
+                                                   int nparts) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += __ldcg(part + i);
+    sh[threadIdx.x] = s;
     __syncthreads();
-    const double s = tot;
-    const bool ok = s > 0.0 && isfinite(s);
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double tot = sh[0];
+    const bool ok = tot > 0.0 && isfinite(tot);
+    const float inv = ok ? (float)(1.0 / tot) : 0.0f, un = 1.0f / (float)n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = ok ? (float)((double)p[i] / s) : 1.0f / (float)n;
-        p[i] = isfinite(v) ? v : 1.0f / (float)n;
+        const float v = ok ? __fmul_rn(p[i], inv) : un;
+        p[i] = isfinite(v) ? v : un;
     }
 }
 
