@@ -397,6 +397,25 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
         out["high_compression"] = crossover(synth.web_862k_hc(), 1)
         out["high_compression"]["graph"] = ("web-like copying model, exact copies with probability 0.93 "
                                             "(m/m' >= 5, the paper's 'compressed 5x or more' regime)")
+    # column blocks (Sec. 6): a graph whose rows link into two regions of ids
+    # with independent prototypes, A encoded whole and split into 2 and 4
+    # blocks of consecutive columns (each block its own references)
+    g2 = synth.two_region((g.n // 2) // 1024 * 1024, synth.seed_for(6, 1))  # regions of whole 1024-column tiles
+    x2 = torch.from_numpy(synth.rhs(g2.n, 1, synth.seed_for(6, 2))).cuda().reshape(-1)
+    y2 = torch.empty_like(x2)
+    sc2 = torch.empty_like(x2)
+    cols = {"graph": "two regions of ids (n = %d rows, the second half empty), each region's links from its own "
+                     "web-like copying model" % g2.n, "n": g2.n, "m": g2.m, "blocks": []}
+    for nb in (1, 2, 4):
+        cb = bvg.bvg_colblocks_create(g2.row_ptr, g2.col, cuts=bvg.aligned_cuts(g2.n, nb))
+        st2 = cb.stats()
+        r = {"nblocks": nb, "m_over_mprime": g2.m / max(1, st2["nnz_diff"]), "m_over_words": g2.m / max(1, st2["words"]),
+             "bits_per_edge": st2["bits_per_edge"]}
+        r["xA_gedges_s"] = gd(g2.m, warm_timed(lambda: bvg.bvg_spmv_xA_colblocks(cb, x2, y2, scratch=sc2)))
+        r["Ax_gedges_s"] = gd(g2.m, warm_timed(lambda: bvg.bvg_spmv_Ax_colblocks(cb, x2, y2, scratch=sc2)))
+        cols["blocks"].append(r)
+        del cb
+    out["column_blocks"] = cols
     if args.config5:
         out["social_5m4"] = crossover(synth.social_5m4(), 1)
         out["web_22m7_k8"] = crossover(synth.web_22m7(), 8, stream_budget=512 << 20)

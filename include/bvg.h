@@ -575,6 +575,32 @@ int bvg_csr_spmv_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k,
 int bvg_csr_cusparse_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 int bvg_csr_cusparse_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
+/* --------------------------------------------------- column blocks (Sec. 6) */
+
+/* Products over A split into submatrices of consecutive columns, the split
+ * that Sec. 6 proposes so that a reference need only match the part of a row
+ * inside one block: A = sum_b A_b, where A_b holds A's entries in columns
+ * [cuts[b], cuts[b+1]) and is encoded and uploaded on its own (n rows, the
+ * same ids: bvg_encode of the column-restricted CSR, then bvg_upload), so
+ * that each block chooses its own references. All blocks have the same n.
+ * cuts: host array of nblocks + 1 column bounds, cuts[0] = 0, cuts[nblocks]
+ * = n, nondecreasing; block b must hold no entry outside its columns (not
+ * checked: such entries are dropped from x A). scratch: device n x k (leading
+ * dimension ld) owned by the caller, unused when nblocks = 1. x, y: device
+ * n x k. Asynchronous; no allocation beyond what the blocks' own products
+ * make. Errors: INVALID_ARG, and those of bvg_spmv_xA / bvg_spmv_Ax.
+ *   x A:   block b's product goes to scratch, and its rows [cuts[b],
+ *          cuts[b+1]) (the only nonzero ones) are copied into y; with one
+ *          contiguous right-hand side (k = 1, ld = 1) and block bounds that
+ *          are multiples of 1024 (or n), a block whose product runs as the
+ *          one-launch kernel computes just its own columns, into y;
+ *   A x^T: y = sum_b A_b x^T, added in block order in FP32 (one rounding
+ *          more per block). */
+int bvg_spmv_xA_colblocks(const bvg_dev_graph* const* blocks, const int64_t* cuts, int32_t nblocks,
+                          const float* x, float* y, float* scratch, int32_t k, int64_t ld, void* stream);
+int bvg_spmv_Ax_colblocks(const bvg_dev_graph* const* blocks, int32_t nblocks, const float* x, float* y,
+                          float* scratch, int32_t k, int64_t ld, void* stream);
+
 /* -------------------------------------------------------------- tracing */
 
 /* Per-kernel timing: while enabled, every kernel the library launches for

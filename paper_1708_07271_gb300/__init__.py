@@ -44,7 +44,7 @@ EXPORTED = [
     "bvg_biclique_gather_lists", "bvg_bitstream_get", "bvg_decode_bits", "bvg_debug_fail_alloc",
     "bvg_device_check", "bvg_csr_cusparse_Ax", "bvg_csr_cusparse_xA", "bvg_biclique_upload",
     "bvg_biclique_spmv_Ax", "bvg_biclique_spmv_xA", "bvg_free_biclique_dev", "bvg_stream_create", "bvg_stream_spmv",
-    "bvg_stream_info", "bvg_stream_get_refs", "bvg_free_stream",
+    "bvg_stream_info", "bvg_stream_get_refs", "bvg_free_stream", "bvg_spmv_xA_colblocks", "bvg_spmv_Ax_colblocks",
 ]
 
 
@@ -211,6 +211,8 @@ def load(build_if_needed: bool = True):
             "bvg_stream_info": ([_P, ctypes.POINTER(StreamInfo)], ctypes.c_int),
             "bvg_stream_get_refs": ([_P, _P], ctypes.c_int),
             "bvg_free_stream": ([_P], None),
+            "bvg_spmv_xA_colblocks": ([_P, _P, _I32, _P, _P, _P, _I32, _I64, _P], ctypes.c_int),
+            "bvg_spmv_Ax_colblocks": ([_P, _I32, _P, _P, _P, _I32, _I64, _P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -912,3 +914,95 @@ def bvg_stream_get_refs(s: Stream):
     ref = np.empty(s.n, np.int32)
     _check(load().bvg_stream_get_refs(s.ptr, ref.ctypes.data), "bvg_stream_get_refs")
     return ref
+
+
+# ------------------------------------------------------ column blocks (Sec. 6)
+
+def split_columns(row_ptr, col, cuts):
+    """The CSR of A restricted to each column range [cuts[b], cuts[b+1])
+    (n rows and the ids unchanged), one (row_ptr, col) per block."""
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    cuts = np.asarray(cuts, np.int64)
+    row_of = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    out = []
+    for b in range(len(cuts) - 1):
+        sel = (ci >= cuts[b]) & (ci < cuts[b + 1])
+        brp = np.zeros(n + 1, np.int64)
+        brp[1:] = np.cumsum(np.bincount(row_of[sel], minlength=n))
+        out.append((brp, ci[sel].astype(np.int32)))
+    return out
+
+
+class ColumnBlocks:
+    """A split into submatrices of consecutive columns, each block encoded
+    and uploaded on its own (its own references)."""
+
+    def __init__(self, n: int, cuts, hosts, devs):
+        self.n, self.cuts, self.hosts, self.devs = n, np.asarray(cuts, np.int64), hosts, devs
+        self._arr = (_P * len(devs))(*[d.ptr for d in devs]) if devs else None
+
+    def stats(self) -> dict:
+        """The blocks' encoding statistics, summed."""
+        tot = {}
+        for h in self.hosts:
+            for key, v in bvg_stats(h).items():
+                if isinstance(v, (int, float)) and key not in ("n", "bits_per_edge"):
+                    tot[key] = tot.get(key, 0) + v
+        tot["n"] = self.n
+        tot["bits_per_edge"] = tot["bitstream_bits"] / max(tot["m"], 1)
+        return tot
+
+
+def aligned_cuts(n: int, nblocks: int, align: int = 1024):
+    """nblocks column ranges of about equal width, inner bounds rounded down
+    to multiples of `align` (whole 1024-column tiles let the one-vector x A
+    of a block compute just its own columns)."""
+    cuts = [0] + [(n * b // nblocks) // align * align for b in range(1, nblocks)] + [n]
+    return np.maximum.accumulate(np.asarray(cuts, np.int64))
+
+
+def bvg_colblocks_create(row_ptr, col, nblocks: int = 2, cuts=None, window=7, max_chain=3, min_interval=4,
+                         stream=None, upload: bool = True) -> ColumnBlocks:
+    """Splits A at `cuts` (default: aligned_cuts(n, nblocks)), encodes and
+    (unless upload is False: host encodings only) uploads each block."""
+    rp, ci, n = _csr_arrays(row_ptr, col)
+    if cuts is None:
+        cuts = aligned_cuts(n, nblocks)
+    hosts, devs = [], []
+    for brp, bci in split_columns(rp, ci, cuts):
+        h = bvg_encode(brp, bci, window=window, max_chain=max_chain, min_interval=min_interval)
+        hosts.append(h)
+        if upload:
+            devs.append(bvg_upload(h, stream=stream))
+    return ColumnBlocks(n, cuts, hosts, devs)
+
+
+def _colblock_args(cb: ColumnBlocks, x, y, scratch):
+    import torch
+    _fp32_cuda(x, y)
+    if not cb.devs:
+        raise ValueError("the column blocks were not uploaded")
+    k, ld = _km(x, cb.n)
+    if _km(y, cb.n) != (k, ld):
+        raise ValueError("x and y must have the same shape and strides")
+    if scratch is None and len(cb.devs) > 1:
+        scratch = torch.empty_like(y)
+    return k, ld, scratch
+
+
+def bvg_spmv_xA_colblocks(cb: ColumnBlocks, x, y, scratch=None, stream=None):
+    """y = x A over the column blocks (scratch: like y, allocated if not given)."""
+    k, ld, scratch = _colblock_args(cb, x, y, scratch)
+    _check(load().bvg_spmv_xA_colblocks(cb._arr, cb.cuts.ctypes.data, len(cb.devs), x.data_ptr(), y.data_ptr(),
+                                        scratch.data_ptr() if scratch is not None else None, k, ld,
+                                        _stream(stream)), "bvg_spmv_xA_colblocks")
+    return y
+
+
+def bvg_spmv_Ax_colblocks(cb: ColumnBlocks, x, y, scratch=None, stream=None):
+    """y = A x^T over the column blocks (scratch: like y, allocated if not given)."""
+    k, ld, scratch = _colblock_args(cb, x, y, scratch)
+    _check(load().bvg_spmv_Ax_colblocks(cb._arr, len(cb.devs), x.data_ptr(), y.data_ptr(),
+                                        scratch.data_ptr() if scratch is not None else None, k, ld,
+                                        _stream(stream)), "bvg_spmv_Ax_colblocks")
+    return y

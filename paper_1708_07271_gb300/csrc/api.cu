@@ -232,13 +232,14 @@ bool want_points(const bvg_dev_graph* g, int kb) {
 }
 
 // Whether a one-vector column block runs as the fused kernel (fused.cuh): by
-// default when at most 1 in 20 column tiles reads rows outside its window
-// (graphs with locality); it needs the point columns for its compensated
-// path.
+// default when no column tile reads rows outside its window (graphs with
+// locality). The kernel runs as one wave, so a single tile on the slow
+// far-row path sets its time; then the two-kernel product serves. It needs
+// the point columns for its compensated path.
 bool use_fused(const bvg_dev_graph* g, int kb) {
     if (kb != 1 || g->pcol_state != 1 || !g->tile_win) return false;
     if (g->cfg.push_fused == 0) return false;
-    return g->cfg.push_fused == 1 || g->fx_far_tiles * 20 <= g->fx_tiles;
+    return g->cfg.push_fused == 1 || g->fx_far_tiles == 0;
 }
 
 FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const float* rowscale, float* y,
@@ -262,15 +263,32 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     fa.ldy = ldy;
     fa.n = g->n;
     fa.err = g->err;
+    fa.tile0 = 0;
     return fa;
 }
 
 static void launch_fused(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy,
-                         cudaStream_t st) {
-    const int64_t grid = (g->n + kFxT - 1) / kFxT;
+                         cudaStream_t st, int64_t tile0 = 0, int64_t tile1 = -1) {
+    if (tile1 < 0) tile1 = (g->n + kFxT - 1) / kFxT;
     PrArgs pa{};
     TraceScope ts(g, "push_fused", st);
-    k_push_fx<0><<<(unsigned)grid, kFxNT, 0, st>>>(fused_args(g, x, ldx, nullptr, y, ldy), pa);
+    FxArgs fa = fused_args(g, x, ldx, nullptr, y, ldy);
+    fa.tile0 = tile0;
+    k_push_fx<0><<<(unsigned)(tile1 - tile0), kFxNT, 0, st>>>(fa, pa);
+}
+
+// x A (one right-hand side) for the columns [col0, col1) only, when the
+// fused kernel serves this graph and the range is made of whole column
+// tiles (col0 a multiple of kFxT, col1 one too or n): the other columns of y
+// are not written. Returns BVG_ERR_UNSUPPORTED otherwise (nothing launched).
+int spmv_xA_columns(const bvg_dev_graph* g, const float* x, float* y, int64_t col0, int64_t col1, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_fused(g, 1) || col0 < 0 || col1 > g->n || col0 > col1 || col0 % kFxT ||
+        (col1 % kFxT && col1 != g->n))
+        return BVG_ERR_UNSUPPORTED;
+    if (col0 < col1) launch_fused(g, x, 1, y, 1, st, col0 / kFxT, (col1 + kFxT - 1) / kFxT);
+    BVG_CUDA_TRY(cudaGetLastError());
+    return BVG_OK;
 }
 
 template <int KB, int V>

@@ -244,6 +244,10 @@ bool use_points(const bvg_dev_graph* g, int kb);
 // A vector argument of a device product: not NULL, 4-byte aligned, and device
 // (or managed) memory of the graph's device; otherwise INVALID_ARG (api.cu).
 int check_vec(const bvg_dev_graph* g, const void* p, const char* what);
+// x A (one right-hand side, vectors contiguous) for the columns [col0, col1)
+// only; BVG_ERR_UNSUPPORTED (nothing launched) unless the one-launch kernel
+// serves g and the range is made of whole 1024-column tiles (api.cu).
+int spmv_xA_columns(const bvg_dev_graph* g, const float* x, float* y, int64_t col0, int64_t col1, void* stream);
 // The pull on a device graph view whose arrays the caller placed (api.cu).
 int pull_view_product(const bvg_dev_graph* v, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 }  // namespace bvg

@@ -100,6 +100,7 @@ struct FxArgs {
     int64_t ldy;
     int64_t n;
     unsigned int* err;          // set to 1 when a bounded wait ran out
+    int64_t tile0;              // first column tile of the launch (CTA b takes tile tile0 + b)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -534,7 +535,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kFxNT, 6) k_push_fx(FxArgs fa, PrArgs pa) {
     __shared__ __align__(16) FxSmem S;
     if constexpr (EPI == 1) asm volatile("griddepcontrol.launch_dependents;");
-    fx_tile<EPI>(blockIdx.x, fa, pa, S);
+    fx_tile<EPI>(fa.tile0 + blockIdx.x, fa, pa, S);
 }
 
 }  // namespace bvg

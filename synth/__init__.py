@@ -218,6 +218,27 @@ def web_7m4(seed: int | None = None) -> GraphSpec:
                      extra_mean=0.35, fresh_mean=23.0, q_run=0.5, gap_mean=24.0)
 
 
+def two_region(n: int, seed: int) -> Graph:
+    """A 2n x 2n graph whose first n rows link into two regions of ids,
+    [0, n) and [n, 2n), the links of each region from its own web-like
+    copying-model graph (web_small, seeds seed and seed + 1): a row's
+    prototypes in the two regions are drawn independently, so an earlier row
+    that matches one part of the row rarely matches the other. The last n
+    rows are empty. (A web page's links inside its own site and into a second
+    site, copied from different pages.)"""
+    g1 = copying_model(web_small(n, seed))
+    g2 = copying_model(web_small(n, seed + 1))
+    c1, c2 = np.diff(g1.row_ptr), np.diff(g2.row_ptr)
+    rp = np.zeros(2 * n + 1, np.int64)
+    rp[1:n + 1] = np.cumsum(c1 + c2)
+    rp[n + 1:] = rp[n]
+    col = np.empty(int(rp[-1]), np.int32)
+    start = rp[:n]
+    col[np.repeat(start, c1) + (np.arange(g1.m) - np.repeat(g1.row_ptr[:n], c1))] = g1.col
+    col[np.repeat(start + c1, c2) + (np.arange(g2.m) - np.repeat(g2.row_ptr[:n], c2))] = g2.col + n
+    return Graph(2 * n, rp, col)
+
+
 def web_small(n: int, seed: int) -> GraphSpec:
     """Web-like graph of n nodes with mean degree ~20 (multi-graph batches,
     warm-start training sets)."""
