@@ -515,7 +515,7 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
         rc = dev_alloc((void**)&g->s.st, sizeof(PrState), nullptr);
         if (rc) return rc;
         for (int p = 0; p < 2; p++) {
-            rc = dev_alloc((void**)&g->s.sc[p], 3 * 32 * sizeof(double), nullptr);
+            rc = dev_alloc((void**)&g->s.sc[p], sc_bytes(), nullptr);
             if (rc) return rc;
         }
         int64_t cap = max_grid(g) * 3 * 32;

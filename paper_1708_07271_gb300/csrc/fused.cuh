@@ -499,7 +499,8 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
     const bool failed = S.state != 0u;  // a copy ran out of time: NaN outputs
 
     float Ssum = 0.f, Rs = 0.f, Dg = 0.f, dl = 0.f;
-    if constexpr (EPI == 1) dl = (float)__ldcg(pa.sc_prev + 1);
+    const float un = EPI == 1 ? 1.0f / (float)n : 0.0f;
+    if constexpr (EPI == 1) dl = sc_dangling_f32(pa.sc_prev, 0);
 #pragma unroll
     for (int q = 0; q < kFxCPT; q++) {
         const int64_t j = wc + ((oc >> (8 * q)) & 0xffu);
@@ -508,7 +509,6 @@ __device__ __forceinline__ void fx_tile(int64_t blk, const FxArgs& fa, const PrA
         if constexpr (EPI == 0) {
             fa.y[j * fa.ldy] = yv[q];
         } else {
-            const float un = 1.0f / (float)n;
             const float io = __ldg(pa.inv_outdeg + j);
             const float qp = __ldcg(pa.q_prev + j * pa.ldq);
             const float p0j = pa.p0 ? __ldg(pa.p0 + j * pa.ldp0) : un;

@@ -17,6 +17,14 @@ struct PrState {
     double tol;
 };
 
+// The scalars of an update: 3 x 32 doubles, then 32 floats (the dangling
+// mass rounded once, read by every thread of the next update's epilogue).
+constexpr int kScDoubles = 3 * 32;
+__host__ __device__ constexpr size_t sc_bytes() { return kScDoubles * sizeof(double) + 32 * sizeof(float); }
+__device__ __forceinline__ float sc_dangling_f32(const double* sc, int c) {
+    return __ldcg(reinterpret_cast<const float*>(sc + kScDoubles) + c);
+}
+
 struct PrArgs {
     const float* p0;           // teleport vectors (n x k, ld ldp0) or NULL = uniform 1/n
     int64_t ldp0;
@@ -25,7 +33,8 @@ struct PrArgs {
     float* q_new;
     float* x_new;              // q_new / outdeg (the next update's input), or NULL
     int64_t ldq;
-    const double* sc_prev;     // [3][k]: 1/S, dangling mass, resid (of the previous update)
+    const double* sc_prev;     // [3][k]: 1/S, dangling mass, resid (of the previous update), then the
+                               // dangling mass rounded to FP32 (kScDanglingF32, k floats)
     double* sc_new;
     PrState* st;
     double* partial;           // [grid][3][KB]
@@ -683,6 +692,7 @@ __device__ void pr_grid_sum(df t, const PrArgs& pa, bool init) {
             const double Ssum = sh_tot[0][c], Rsum = sh_tot[1][c], Dsum = sh_tot[2][c];
             pa.sc_new[0 * KB + c] = 1.0 / Ssum;
             pa.sc_new[1 * KB + c] = Dsum;
+            reinterpret_cast<float*>(pa.sc_new + kScDoubles)[c] = (float)Dsum;
             pa.sc_new[2 * KB + c] = init ? INFINITY : Rsum;
             if (!(Rsum < pa.st->tol)) conv = false;
             if (!isfinite(Ssum) || !isfinite(Dsum) || (!init && !isfinite(Rsum)) || Ssum <= 0.0) bad = true;
@@ -1153,10 +1163,11 @@ __device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restr
     // terms), then compensated across the warps of the block
     float Ssum[V], R[V], Dg[V];
     float dl[V];  // the previous update's dangling mass, per right-hand side of this lane
+    const float un = EPI == 1 ? 1.0f / (float)n : 0.0f;  // (an int64 conversion: once, not per column)
 #pragma unroll
     for (int v = 0; v < V; v++) {
         Ssum[v] = R[v] = Dg[v] = 0.f;
-        if constexpr (EPI == 1) dl[v] = (float)__ldcg(pa.sc_prev + 1 * KB + lane * V + v);
+        if constexpr (EPI == 1) dl[v] = sc_dangling_f32(pa.sc_prev, lane * V + v);
     }
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
@@ -1175,7 +1186,6 @@ __device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restr
         if constexpr (EPI == 0) {
             stv<V>(y + j * ldy + lane * V, out);
         } else {
-            const float un = 1.0f / (float)n;
             float io;
             Vec<V> qp, qn, p0v;
             if constexpr (kPfRegs) {
