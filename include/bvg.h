@@ -228,13 +228,21 @@ int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int
 /* y = x A (push, Proposition 1 read for the left product): z_k = sum of x_i
  * over rows whose chain passes through k (x pushed down the reference chains
  * in reverse level order), then y = sum_k z_k a'_k, gathered per column with
- * no atomics (deterministic). The gather reads either the event columns
- * (intervals as start / end events and a running sum across columns,
- * bvg_layout_view) or the point columns (bvg_point_cols_size), as the launch
- * configuration's push_points says; the point columns are built and copied
- * to the device (synchronising `stream`) the first time a launch uses them,
- * and if they cannot be built (2^30 entries or more) the event columns
- * serve. x, y: device n x k. Asynchronous. Errors: INVALID_ARG, OOM, CUDA. */
+ * no atomics (deterministic).
+ * One right-hand side (a column block of width 1): by default one launch
+ * computes, per tile of 1024 columns, the chain weights of the tile's row
+ * window and the gather in shared memory, with exact 64-bit fixed-point sums
+ * (y_j is the exact sum rounded once to FP32) where the tile's x spans few
+ * enough binades, compensated sums otherwise; it serves graphs in which no
+ * tile reads a row outside its window (launch configuration push_fused;
+ * otherwise the two launches below). A timed-out internal copy sets the
+ * graph's error word (bvg_device_check) and leaves NaN in y.
+ * Wider column blocks: the chain launch, then the gather over the point
+ * columns (bvg_point_cols_size) or the event columns (intervals as start /
+ * end events and a running sum across columns, bvg_layout_view), as
+ * push_points says; if the point columns cannot be built (2^30 entries or
+ * more) the event columns serve. x, y: device n x k. Asynchronous. Errors:
+ * INVALID_ARG, OOM, CUDA. */
 int bvg_spmv_xA(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 
 /* Same product as bvg_spmv_xA, for callers that must not allocate device
