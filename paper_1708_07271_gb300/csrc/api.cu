@@ -719,7 +719,8 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             bvg_free_dev(g);
             return rc;
         }
-        const size_t ncount = (size_t)(1 + max_grid(g) / kPrGroup + 1);  // global + one per group of CTAs
+        // global + one per group of CTAs + the update gather's tile counter
+        const size_t ncount = (size_t)(1 + max_grid(g) / kPrGroup + 1) + 1;
         if ((rc = ensure_z(g, 1)) || (rc = dev_alloc((void**)&g->s.counter, ncount * sizeof(unsigned int), nullptr))) {
             bvg_free_dev(g);
             return rc;
@@ -1023,6 +1024,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     base.partial = g->s.partial;
     base.counter = g->s.counter;
     base.gcounter = g->s.counter + 1;
+    base.tile_counter = g->s.counter + 1 + max_grid(g) / kPrGroup + 1;
     base.gpartial = g->s.gpartial;
     base.alpha = (float)(1.0 - damping);
     base.dangling_uniform = dangling;

@@ -41,6 +41,8 @@ struct PrArgs {
     unsigned int* counter;     // CTAs groups finished (last-group reduction)
     double* gpartial;          // [groups][3][KB]
     unsigned int* gcounter;    // per group of kPrGroup CTAs: CTAs finished
+    unsigned int* tile_counter;  // the update gather's next tile (reset by the grid reduction's last CTA
+                                 // and by k_pr_init)
     float alpha;
     int dangling_uniform;
     int k;                     // right-hand sides of the solve (== KB)
@@ -707,6 +709,7 @@ __device__ void pr_grid_sum(df t, const PrArgs& pa, bool init) {
             if (conv || bad) pa.st->done = 1;
         }
         *pa.counter = 0u;
+        if (pa.tile_counter) *pa.tile_counter = 0u;  // every CTA has taken its last tile
         __threadfence();
     }
 }
@@ -1223,10 +1226,10 @@ __device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restr
     return true;
 }
 
-// A PageRank update's gather: a resident grid, each CTA taking tiles blk,
-// blk + gridDim.x, ... and adding their block sums, then one grid-wide
-// reduction (one per CTA instead of one per 128-column tile). The product
-// (EPI = 0): one tile per CTA.
+// A PageRank update's gather: a resident grid, each CTA taking tiles from a
+// counter and adding their block sums, then one grid-wide reduction (one per
+// CTA instead of one per 128-column tile). The product (EPI = 0): one tile
+// per CTA.
 template <int KB, int V, int EPI, bool EV>
 __device__ __forceinline__ void gather_grid(const uint32_t* __restrict__ colp, const uint32_t* __restrict__ tent,
                                            const uint32_t* __restrict__ titem_ptr,
@@ -1240,12 +1243,31 @@ __device__ __forceinline__ void gather_grid(const uint32_t* __restrict__ colp, c
         gather_tile<KB, V, EPI, EV>(blockIdx.x, colp, tent, titem_ptr, titem, carry_ptr, carry, long_chunk, z, ldz, y,
                                     ldy, n, pa, acc);
     } else {
+        // tiles handed out one at a time (CTAs whose tiles ran long take
+        // fewer), the same sums whatever CTA takes a tile
         constexpr int T = GatherShape<KB, V>::T;
         const int64_t tiles = (n + T - 1) / T;
-        for (int64_t blk = blockIdx.x; blk < tiles; blk += gridDim.x)
+        __shared__ unsigned int sh_tile;
+        bool took = false;
+        for (;;) {
+            if (threadIdx.x == 0) sh_tile = atomicAdd(pa.tile_counter, 1u);
+            __syncthreads();
+            const int64_t blk = sh_tile;
+            __syncthreads();
+            if (blk >= tiles) break;
+            took = true;
             if (!gather_tile<KB, V, EPI, EV>(blk, colp, tent, titem_ptr, titem, carry_ptr, carry, long_chunk, z, ldz,
                                              y, ldy, n, pa, acc))
                 return;  // the same answer in every CTA: no CTA reduces
+        }
+        if (!took) {
+            // no tile left for this CTA: the other CTAs took them all, or the
+            // update is past convergence or max_iter (such updates return
+            // without resetting the counter, which then holds their fetches);
+            // the state tells
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            if (__ldcg(&pa.st->done) || __ldcg(&pa.st->iter) >= __ldcg(&pa.st->max_iter)) return;
+        }
         pr_grid_sum<KB>(acc, pa, false);
     }
 }
@@ -1283,6 +1305,7 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_init, int64_t ldi, int64_t n,
                                                  int tile, PrArgs pa) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && pa.tile_counter) *pa.tile_counter = 0u;  // a fresh solve
     constexpr int G = KB / V;
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G, lane = threadIdx.x % G;
