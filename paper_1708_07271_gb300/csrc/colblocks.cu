@@ -6,18 +6,40 @@
 // references.
 //   x A: block b's product is zero outside its columns, so y takes rows
 //        [cuts[b], cuts[b+1]) of block b's product: for one right-hand side
-//        with block bounds on whole 1024-column tiles, the one-launch kernel
-//        runs just those tiles into y; otherwise the product goes to scratch
-//        and the rows are copied;
+//        with block bounds on whole 1024-column tiles, one launch runs every
+//        block's own tiles of the one-vector kernel (the blocks' arguments
+//        in the launch's parameters), each CTA a tile of its block, into y;
+//        otherwise each block's product goes to scratch and its rows are
+//        copied;
 //   A x^T: y = sum_b A_b x^T, the blocks' products added in block order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "bvg_internal.h"
-#include "device_common.cuh"
+#include "fused.cuh"
 
 namespace bvg {
+
+// Blocks one launch serves: their one-vector kernel arguments (fa[b].tile0 =
+// the first tile of block b's columns) and the CTAs of each block.
+constexpr int kMaxColBlocks = 16;
+struct FxBlocks {
+    FxArgs fa[kMaxColBlocks];
+    int64_t cta_end[kMaxColBlocks];  // CTAs [cta_end[b - 1], cta_end[b]) run block b's tiles
+    int32_t nb;
+};
+
+__global__ void __launch_bounds__(kFxNT, 6) k_push_fx_blocks(const __grid_constant__ FxBlocks fb) {
+    __shared__ __align__(16) FxSmem S;
+    int b = 0;
+    for (int i = 1; i < fb.nb; i++)
+        if ((int64_t)blockIdx.x >= fb.cta_end[i - 1]) b = i;
+    const int64_t first = b ? fb.cta_end[b - 1] : 0;
+    const FxArgs& fa = fb.fa[b];
+    PrArgs pa{};
+    fx_tile<0>(fa.tile0 + ((int64_t)blockIdx.x - first), fa, pa, S);
+}
 
 // y += s over n rows of k values (leading dimension ld).
 __global__ void k_add_rows(float* __restrict__ y, const float* __restrict__ s, int64_t n, int32_t k, int64_t ld) {
@@ -61,6 +83,25 @@ extern "C" int bvg_spmv_xA_colblocks(const bvg_dev_graph* const* blocks, const i
     if (n == 0) return BVG_OK;
     if (nblocks == 1) return bvg_spmv_xA(blocks[0], x, y, k, ld, stream);
     cudaStream_t st = (cudaStream_t)stream;
+    // one vector, every block served by the one-vector kernel, bounds on whole
+    // tiles: one launch over all blocks' tiles
+    bool one = k == 1 && ld == 1 && nblocks <= kMaxColBlocks;
+    for (int32_t b = 0; one && b < nblocks; b++)
+        one = use_fused(blocks[b], 1) && cuts[b] % kFxT == 0 && (cuts[b + 1] % kFxT == 0 || cuts[b + 1] == n);
+    if (one) {
+        FxBlocks fb{};
+        fb.nb = nblocks;
+        int64_t ctas = 0;
+        for (int32_t b = 0; b < nblocks; b++) {
+            fb.fa[b] = fused_args(blocks[b], x, 1, nullptr, y, 1);
+            fb.fa[b].tile0 = cuts[b] / kFxT;
+            ctas += cuts[b + 1] > cuts[b] ? (cuts[b + 1] + kFxT - 1) / kFxT - cuts[b] / kFxT : 0;
+            fb.cta_end[b] = ctas;
+        }
+        if (ctas > 0) k_push_fx_blocks<<<(unsigned)ctas, kFxNT, 0, st>>>(fb);
+        BVG_CUDA_TRY(cudaGetLastError());
+        return BVG_OK;
+    }
     for (int32_t b = 0; b < nblocks; b++) {
         const int64_t rows = cuts[b + 1] - cuts[b];
         if (rows == 0) continue;
