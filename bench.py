@@ -325,9 +325,16 @@ def variants_leg(args, bvg, synth, torch, timed, dg, g, cg):
     pullT = warm_timed(lambda: bvg.bvg_spmv_Ax(dgT, x, y2))
     torch.cuda.synchronize()
     rel = float(((y - y2).abs().max() / y.abs().max()).item())
+    # and the other way round: A x^T as the push (x A^T) on A^T's encoding
+    pull = warm_timed(lambda: bvg.bvg_spmv_Ax(dg, x, y))
+    pushT = warm_timed(lambda: bvg.bvg_spmv_xA(dgT, x, y2))
+    torch.cuda.synchronize()
+    relT = float(((y - y2).abs().max() / y.abs().max()).item())
     gd = lambda m, ms: m * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
     out = {"xA_push_on_A_gedges_s": gd(g.m, push), "xA_pull_on_AT_gedges_s": gd(g.m, pullT),
-           "AT_m_over_words": stT["m"] / max(1, stT["words"]), "max_rel_diff_push_vs_pull": rel}
+           "AT_m_over_words": stT["m"] / max(1, stT["words"]), "max_rel_diff_push_vs_pull": rel,
+           "Ax_pull_on_A_gedges_s": gd(g.m, pull), "Ax_push_on_AT_gedges_s": gd(g.m, pushT),
+           "max_rel_diff_pull_vs_push_on_AT": relT}
 
     def biclique_leg(gs, xs, ys, k):
         """The biclique format (Sec. 6) on the same graph: its words and both

@@ -226,3 +226,34 @@ def web862k_fused():
     hg = bvg.bvg_encode(g.row_ptr, g.col)
     ref, _ = bvg.bvg_get_refs(hg)
     return g, hg, bvg.bvg_upload(hg), ref
+
+
+def transpose(g):
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    order = np.lexsort((src, g.col))
+    tp = np.zeros(g.n + 1, np.int64)
+    tp[1:] = np.cumsum(np.bincount(g.col, minlength=g.n))
+    return tp, src[order].astype(np.int32)
+
+
+@pytest.mark.parametrize("name", ["tiny_web", "ragged_1037", "web_50k"])
+def test_products_through_the_transpose(name):
+    """A x^T as the push on an encoding of A^T (x A^T), and x A as the pull on
+    it (the paper's own PageRank choice): both against the oracle's products
+    of A."""
+    g = GRAPHS[name]()
+    tp, tc = transpose(g)
+    hgT = bvg.bvg_encode(tp, tc)
+    refT, _ = bvg.bvg_get_refs(hgT)
+    dgT = bvg.bvg_upload(hgT)
+    for kind in ("uniform", "signed"):
+        x = synth.input_kind(kind, g.n, 1, synth.seed_for(8, 120 + len(kind)))
+        x64 = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        y = torch.empty_like(xt)
+        bvg.bvg_spmv_xA(dgT, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_Ax(g.row_ptr, g.col, x64),
+                    oracle.bv_xA(tp, tc, refT, x64, absval=True), f"A x^T as push on A^T {kind} {name}")
+        bvg.bvg_spmv_Ax(dgT, xt, y)
+        check_close(y.cpu().numpy(), oracle.csr_xA(g.row_ptr, g.col, x64),
+                    oracle.bv_Ax(tp, tc, refT, x64, absval=True), f"x A as pull on A^T {kind} {name}")
