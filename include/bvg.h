@@ -396,8 +396,12 @@ typedef struct {
                                the tile, whose error is bounded relative to that running sum, not to the column's
                                own terms), 1 always */
     int32_t push_fused;     /* x A for one right-hand side in one kernel (exact fixed-point sums, TMA-staged
-                               structure): -1 when at most 5% of its column tiles read rows outside their window
-                               (default), 0 never, 1 always */
+                               structure): -1 when no column tile reads rows outside its window (default), 0
+                               never, 1 always */
+    int32_t pull_fused;     /* A x^T for one right-hand side in one kernel (the x window of each tile of 1024
+                               rows in shared memory, work items of at most 8 entries, exact fixed-point sums):
+                               -1 or 1 whenever every tile's x window (at most 1792 columns) and work items (at
+                               most 2048) fit the kernel (default -1), 0 never */
 } bvg_launch_config;
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);

@@ -85,7 +85,8 @@ class LayoutView(ctypes.Structure):
 
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pull_tile", _I32), ("pull_prefix", _I32), ("prefix_min_len", _I32), ("gather_pdl", _I32),
-                ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32), ("push_fused", _I32)]
+                ("col_block", _I32), ("pull_item", _I32), ("push_points", _I32), ("push_fused", _I32),
+                ("pull_fused", _I32)]
 
 
 class StreamInfo(ctypes.Structure):
@@ -744,7 +745,7 @@ def bvg_autotune_cache_lookup(path, key: str):
 
 
 def bvg_autotune_cache_store(path, key: str, config: dict, push_us: float = 0.0, pull_us: float = 0.0):
-    c = LaunchConfig(**{f: int(config.get(f, -1) if f in ("push_points", "push_fused") else config[f])
+    c = LaunchConfig(**{f: int(config.get(f, -1) if f in ("push_points", "push_fused", "pull_fused") else config[f])
                         for f, _ in LaunchConfig._fields_})
     _check(load().bvg_autotune_cache_store(os.fsencode(path), key.encode(), ctypes.byref(c), push_us, pull_us),
            "bvg_autotune_cache_store")

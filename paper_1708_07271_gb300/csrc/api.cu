@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "fused.cuh"
+#include "pull_fused.cuh"
 
 using namespace bvg;
 
@@ -265,6 +266,27 @@ FxArgs fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, const flo
     fa.err = g->err;
     fa.tile0 = 0;
     return fa;
+}
+
+// Whether the one-vector pull runs as one kernel (pull_fused.cuh): its tables
+// were built (every row tile's x window and work items fit the kernel).
+bool use_pull_fused(const bvg_dev_graph* g, int kb) {
+    return kb == 1 && g->cfg.pull_fused != 0 && g->px_ok;
+}
+
+PxArgs pull_fused_args(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy) {
+    PxArgs pa{};
+    pa.irow = g->px_irow;
+    pa.istart = g->px_istart;
+    pa.pent = g->px_pent;
+    pa.ptile = (const uint2*)g->px_tile;
+    pa.meta = g->meta;
+    pa.x = x;
+    pa.ldx = ldx;
+    pa.y = y;
+    pa.ldy = ldy;
+    pa.n = g->n;
+    return pa;
 }
 
 static void launch_fused(const bvg_dev_graph* g, const float* x, int64_t ldx, float* y, int64_t ldy,
@@ -713,6 +735,54 @@ extern "C" int bvg_upload(const bvg_host_graph* hg, void* stream, bvg_dev_graph*
             g->tile_win = dwin;
             BVG_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(unsigned int), st));
         }
+        // the one-vector pull (pull_fused.cuh): work items with every interval
+        // expanded, each row tile's x window, and each entry as the offset of
+        // its column in the window of the tile that owns its row
+        {
+            PullItems P;
+            if ((rc = build_pull_items(L->rowp.data(), L->ent.data(), n, kPxItem, INT32_MAX, P, false))) {
+                bvg_free_dev(g);
+                return rc;
+            }
+            const int64_t ptiles = (n + kPxT - 1) / kPxT;
+            std::vector<uint32_t> pwin((size_t)ptiles * 2, 0u);
+            bool ok = P.lint.empty();
+            for (int64_t t = 0; t < ptiles && ok; t++) {
+                const int64_t a = t * kPxT, lo = std::max<int64_t>(0, a - kHalo), e = std::min<int64_t>(n, a + kPxT);
+                const uint32_t k0 = P.irow[lo], k1 = P.irow[e];
+                if (k1 - k0 > (uint32_t)kPxItemCap) ok = false;
+                int64_t cmin = INT64_MAX, cmax = -1;
+                for (uint32_t q = P.istart[k0]; q < P.istart[k1]; q++) {
+                    const int64_t c = P.pent[q] & 0x7fffffffu;
+                    cmin = std::min(cmin, c);
+                    cmax = std::max(cmax, c);
+                }
+                if (cmax < 0) cmin = cmax = a;
+                else cmax += 1;
+                if (cmax - cmin > kPxW) ok = false;
+                pwin[(size_t)t * 2] = (uint32_t)cmin;
+                pwin[(size_t)t * 2 + 1] = (uint32_t)cmax;
+            }
+            std::vector<uint16_t> pd(ok ? P.pent.size() : 0);
+            for (int64_t r = 0; r < n && ok; r++) {
+                const int64_t w0 = pwin[(size_t)(r / kPxT) * 2];
+                for (uint32_t q = P.istart[P.irow[r]]; q < P.istart[P.irow[r + 1]]; q++)
+                    pd[q] = (uint16_t)(((P.pent[q] & 0x7fffffffu) - w0) | ((P.pent[q] >> 31) << 15));
+            }
+            if (ok) {
+                uint32_t* dtile = nullptr;
+                if ((rc = upload_vec(&g->px_irow, P.irow, st, &g->bytes)) ||
+                    (rc = upload_vec(&g->px_istart, P.istart, st, &g->bytes)) ||
+                    (rc = upload_vec(&g->px_pent, pd, st, &g->bytes)) || (rc = upload_vec(&dtile, pwin, st, &g->bytes))) {
+                    if (dtile) cudaFree(dtile);
+                    bvg_free_dev(g);
+                    return rc;
+                }
+                g->px_tile = dtile;
+                g->px_ok = 1;
+                BVG_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
+            }
+        }
         // the point columns (the gather of every column block, and the fused
         // kernel's compensated path)
         if ((rc = ensure_points(g, st))) {
@@ -746,7 +816,8 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
                     g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
-                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->tent16, g->err};
+                    g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->tent16, g->px_irow, g->px_istart,
+                    g->px_pent, g->px_tile, g->err};
     drop_pr_graph(g);
     if (g->s.cap_stream) cudaStreamDestroy((cudaStream_t)g->s.cap_stream);
     for (void* p : ptrs)
@@ -824,6 +895,7 @@ extern "C" int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out) {
     out->pull_item = g->cfg.pull_item;
     out->push_points = g->cfg.push_points;
     out->push_fused = g->cfg.push_fused;
+    out->pull_fused = g->cfg.pull_fused;
     return BVG_OK;
 }
 
@@ -833,11 +905,12 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
         in->pull_prefix < -1 || in->pull_prefix > 1 || in->prefix_min_len < 1 || in->gather_pdl < 0 ||
         in->gather_pdl > 1 || in->col_block < 1 || in->col_block > 32 || (in->col_block & (in->col_block - 1)) ||
         (in->pull_item != 4 && in->pull_item != 8 && in->pull_item != 16) || in->push_points < -1 ||
-        in->push_points > 1 || in->push_fused < -1 || in->push_fused > 1)
+        in->push_points > 1 || in->push_fused < -1 || in->push_fused > 1 || in->pull_fused < -1 ||
+        in->pull_fused > 1)
         return fail(BVG_ERR_INVALID_ARG, "bvg_set_config: pull_tile a power of two in [64, 2048], pull_prefix in "
                                          "{-1,0,1}, prefix_min_len >= 1, gather_pdl in {0,1}, col_block a power "
-                                         "of two in [1, 32], pull_item in {4, 8, 16}, push_points and push_fused "
-                                         "in {-1,0,1}");
+                                         "of two in [1, 32], pull_item in {4, 8, 16}, push_points, push_fused "
+                                         "and pull_fused in {-1,0,1}");
     if (in->pull_item != g->pull_built_item || in->prefix_min_len != g->pull_built_minlen ||
         (in->pull_prefix < 0 ? 1 : 0) != g->pull_built_auto) {
         int rc = build_pull_items(g, in->pull_item, in->prefix_min_len, in->pull_prefix, nullptr);
@@ -854,6 +927,7 @@ extern "C" int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in) {
     g->cfg.pull_item = in->pull_item;
     g->cfg.push_points = in->push_points;
     g->cfg.push_fused = in->push_fused;
+    g->cfg.pull_fused = in->pull_fused;
     return BVG_OK;
 }
 
@@ -885,6 +959,12 @@ extern "C" int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int
     if (x == y) return fail(BVG_ERR_INVALID_ARG, "bvg_spmv_Ax: x and y must not alias");
     cudaStream_t st = (cudaStream_t)stream;
     bvg_dev_graph* gm = const_cast<bvg_dev_graph*>(g);
+    if (k == 1 && use_pull_fused(g, 1)) {  // one vector: one launch
+        TraceScope ts(g, "pull_fused", st);
+        k_pull_fx<<<(unsigned)((g->n + kPxT - 1) / kPxT), kPxNT, 0, st>>>(pull_fused_args(g, x, ld, y, ld));
+        BVG_CUDA_TRY(cudaGetLastError());
+        return BVG_OK;
+    }
     const bool prefix = use_prefix(g);
     for (int64_t c0 = 0; c0 < k; ) {
         const int kb = block_k(std::min<int64_t>(k - c0, g->cfg.col_block));

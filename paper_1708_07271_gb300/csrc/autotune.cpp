@@ -95,7 +95,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                     if (!sc.eat('{')) return false;
                     std::string key;
                     CacheEntry e{};
-                    e.cfg = {512, -1, 32, 1, 32, 8, -1, -1};
+                    e.cfg = {512, -1, 32, 1, 32, 8, -1, -1, -1};
                     int fields = 0;
                     do {
                         std::string f;
@@ -114,6 +114,7 @@ bool parse_cache(const std::string& text, std::map<std::string, CacheEntry>& out
                         else if (f == "pull_item") e.cfg.pull_item = (int32_t)v, fields++;
                         else if (f == "push_points") e.cfg.push_points = (int32_t)v;  // absent in older files: -1
                         else if (f == "push_fused") e.cfg.push_fused = (int32_t)v;    // absent in older files: -1
+                        else if (f == "pull_fused") e.cfg.pull_fused = (int32_t)v;    // absent in older files: -1
                         else if (f == "push_us") e.push_us = v;
                         else if (f == "pull_us") e.pull_us = v;
                     } while (sc.eat(','));
@@ -164,9 +165,10 @@ int write_cache(const char* path, const std::map<std::string, CacheEntry>& m) {
         std::snprintf(buf, sizeof buf,
                       "%s\n  {\"key\": \"%s\", \"pull_tile\": %d, \"pull_prefix\": %d, \"prefix_min_len\": %d, "
                       "\"gather_pdl\": %d, \"col_block\": %d, \"pull_item\": %d, \"push_points\": %d, "
-                      "\"push_fused\": %d, \"push_us\": %.3f, \"pull_us\": %.3f}",
+                      "\"push_fused\": %d, \"pull_fused\": %d, \"push_us\": %.3f, \"pull_us\": %.3f}",
                       first ? "" : ",", json_escape(kv.first).c_str(), c.pull_tile, c.pull_prefix, c.prefix_min_len,
-                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, c.push_fused, kv.second.push_us,
+                      c.gather_pdl, c.col_block, c.pull_item, c.push_points, c.push_fused, c.pull_fused,
+                      kv.second.push_us,
                       kv.second.pull_us);
         o << buf;
         first = false;

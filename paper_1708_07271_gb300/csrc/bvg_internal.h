@@ -125,7 +125,9 @@ struct LaunchCfg {
     int push_points = -1;       // x A gather over point columns: -1 every column block (default), 0 never (event
                                 // columns), 1 always
     int push_fused = -1;        // x A for one right-hand side in one fused kernel (fused.cuh): -1 when the graph
-                                // has locality (few tiles read rows outside their window), 0 never, 1 always
+                                // has locality (no tile reads rows outside its window), 0 never, 1 always
+    int pull_fused = -1;        // A x^T for one right-hand side in one kernel (pull_fused.cuh): -1 or 1 whenever
+                                // every tile's x window fits, 0 never
 };
 
 struct TuneInfo {
@@ -219,6 +221,12 @@ struct bvg_dev_graph {
     // entry or a carry source lies outside the tile's row window
     void* tile_win = nullptr;       // uint4 per tile: first and end row of its window, 1 if it reads a row outside
     uint16_t* tent16 = nullptr;     // fused kernel: event-column entries as window offsets (16-bit, see FxArgs)
+    // one-vector pull (pull_fused.cuh): work items with every interval expanded, 16-bit window entries
+    uint32_t* px_irow = nullptr;
+    uint32_t* px_istart = nullptr;
+    uint16_t* px_pent = nullptr;
+    void* px_tile = nullptr;        // uint2 per tile of 1024 rows: its x window
+    int px_ok = 0;                  // built, and every tile's window and items fit the kernel
     uint32_t* lane_cols = nullptr;  // fused kernel: 32 words per group of kCarryTile columns, each lane's 4 columns
     uint32_t* row_order = nullptr;  // fused kernel: the chain weights' row order, 256 words per 4 blocks of 256 rows
     int64_t row_groups = 0;

@@ -8,7 +8,7 @@ import pytest
 import paper_1708_07271_gb300 as bvg
 
 CFG = {"pull_tile": 256, "pull_prefix": 1, "prefix_min_len": 8, "gather_pdl": 0, "col_block": 16, "pull_item": 4,
-       "push_points": 1, "push_fused": 0}
+       "push_points": 1, "push_fused": 0, "pull_fused": 0}
 
 
 def test_store_lookup_overwrite(tmp_path):
@@ -46,10 +46,10 @@ def test_file_written_by_hand_is_read(tmp_path):
         {"key": "gpu/sm1/abc/k4", "pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1,
          "col_block": 4, "pull_item": 16, "push_us": 1e2, "pull_us": 2.5e2}]}, indent=2))
     got = bvg.bvg_autotune_cache_lookup(path, "gpu/sm1/abc/k4")
-    # a file without push_points or push_fused (written before those settings existed) reads them as -1,
-    # the defaults
+    # a file without push_points, push_fused or pull_fused (written before those settings existed) reads them
+    # as -1, the defaults
     assert got == {"pull_tile": 128, "pull_prefix": 0, "prefix_min_len": 16, "gather_pdl": 1, "col_block": 4,
-                   "pull_item": 16, "push_points": -1, "push_fused": -1}
+                   "pull_item": 16, "push_points": -1, "push_fused": -1, "pull_fused": -1}
 
 
 def test_bad_arguments(tmp_path):
