@@ -68,10 +68,19 @@ def traced(dg, fn):
     return set(tr)
 
 
-@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("name", ["tiny_web", "ragged_1037", "web_50k"])
 def test_default_is_one_launch(name):
     g, hg, dg, ref = graph(name)
     assert traced(dg, lambda: run_Ax(dg, synth.rhs(g.n, 1, 3))) == {"pull_fused"}
+
+
+def test_long_runs_keep_two_launches():
+    """Runs of up to 900 ids make some row tiles' x windows wider than the
+    kernel holds: that graph keeps the two-launch pull (its parity with the
+    oracle is in test_pull_fused_matches_oracle)."""
+    g, hg, dg, ref = graph("long_runs")
+    tr = traced(dg, lambda: run_Ax(dg, synth.rhs(g.n, 1, 3)))
+    assert "pull_fused" not in tr and {"pull_items", "pull_rows"} <= tr
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
