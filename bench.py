@@ -217,7 +217,7 @@ def profile_traffic(kernel: str, source_digest: str, k: int = 1):
 
 # Sources that define or launch the product kernels; a change to any of them
 # retires the DRAM traffic recorded under profiles/.
-PRODUCT_SOURCES = ("kernels.cuh", "device_common.cuh", "bvg_internal.h", "api.cu", "fused.cuh")
+PRODUCT_SOURCES = ("kernels.cuh", "device_common.cuh", "bvg_internal.h", "api.cu", "fused.cuh", "pull_fused.cuh")
 
 
 def kernel_source_digest():
@@ -748,6 +748,18 @@ def run_bv(args):
     csr_ms = warm_timed(lambda: bvg.bvg_csr_spmv_xA(cg, x, y))
     cusp_ms = warm_timed(lambda: bvg.bvg_csr_cusparse_xA(cg, x, y))
     pull_ms = warm_timed(lambda: bvg.bvg_spmv_Ax(dg, x, y))
+    bvg.bvg_trace_enable(dg, True)
+    bvg.bvg_trace_read(dg)
+    bvg.bvg_spmv_Ax(dg, x, y)
+    pull_kernels = sorted(bvg.bvg_trace_read(dg))
+    bvg.bvg_trace_enable(dg, False)
+    pull_roofline = None
+    if pull_kernels == ["pull_fused"]:  # one launch per product: its time is the step's
+        pb = bytemodel.pull_fused(L, k)
+        pull_gbs = pb / (float(np.mean(pull_ms)) * 1e-3) / 1e9
+        pull_roofline = {"kernel": "pull_fused", "algorithmic_bytes": pb, "avg_us": 1e3 * float(np.mean(pull_ms)),
+                         "achieved_gbs": pull_gbs, "frac": pull_gbs / peak,
+                         "traffic": profile_traffic("pull_fused", kernel_source_digest(), k)}
     csr_ax_ms = warm_timed(lambda: bvg.bvg_csr_spmv_Ax(cg, x, y))
     cusp_ax_ms = warm_timed(lambda: bvg.bvg_csr_cusparse_Ax(cg, x, y))
     gedges = lambda ms: g.m * k * len(ms) / (np.sum(ms) * 1e-3) / 1e9  # noqa: E731
@@ -811,6 +823,7 @@ def run_bv(args):
             "pull_gedges_s": gedges(pull_ms), "csr_Ax_gedges_s": gedges(csr_ax_ms),
             "cusparse_Ax_gedges_s": gedges(cusp_ax_ms),
             "pull_over_best_csr": float(min(np.sum(csr_ax_ms), np.sum(cusp_ax_ms)) / np.sum(pull_ms)),
+            "pull_kernels": pull_kernels, "pull_roofline": pull_roofline,
             "pagerank": {"seconds": pr_s, "iterations": pr_it, "l1_resid": pr_res, "status": pr_rc,
                          "start": "uniform", "k": 1},
             "k_rhs": krhs, "batch": batch, "warm_start": warm, "variants": variants, "window_sweep": wsweep,

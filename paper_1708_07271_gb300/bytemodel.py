@@ -25,6 +25,11 @@ Per launch with k right-hand sides (n rows, layout sizes from bvg_dev_layout):
                + 4n (y); the chain weights never leave shared
                memory, and the window rows read by two neighbouring tiles come from
                L2 the second time
+  pull_fused   (one right-hand side, one kernel; every interval expanded, so the layout's
+               pull_items / pull_entries are its items and entries) n (meta) + 4(n+1) (item
+               offsets per row) + 4(items+1) (item starts) + 2*pull_entries (16-bit entries)
+               + 8*ceil(n/1024) (per-tile column windows) + 4n (x) + 4n (y); the items' and
+               rows' sums never leave shared memory
   pr_fused     push_fused + 4n (1/outdeg) [+ 4n (p0) when a teleport vector is
                given]: x is the previous iterate (read once), the new iterate is
                written in place of y
@@ -83,6 +88,12 @@ def push_fused(L: dict, k: int) -> int:
             + 16 * ((n + 1023) // 1024) + 128 * ((n + 127) // 128) + 1024 * ((n + 1023) // 1024) + 8 * k * n)
 
 
+def pull_fused(L: dict, k: int) -> int:
+    n = L["n"]
+    return (n + 4 * (n + 1) + 4 * (L["pull_items"] + 1) + 2 * L["pull_entries"] + 8 * ((n + 1023) // 1024)
+            + 8 * k * n)
+
+
 def pr_fused(L: dict, k: int, with_p0: bool = False) -> int:
     n = L["n"]
     return push_fused(L, k) + 4 * n + (4 * k * n if with_p0 else 0)
@@ -93,4 +104,4 @@ def xA_total(L: dict, k: int) -> int:
 
 
 KERNELS = {"push_gather": push_gather, "push_gather_pt": push_gather_pt, "push_chain": push_chain, "pull": pull,
-           "push_fused": push_fused}
+           "push_fused": push_fused, "pull_fused": pull_fused}
