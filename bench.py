@@ -220,11 +220,20 @@ def profile_traffic(kernel: str, source_digest: str, k: int = 1):
 PRODUCT_SOURCES = ("kernels.cuh", "device_common.cuh", "bvg_internal.h", "api.cu", "fused.cuh", "pull_fused.cuh")
 
 
+def code_only(text: str) -> str:
+    """C/CUDA source without its comments and blank lines (string literals in
+    these files hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_digest():
+    """Digest of the product's CUDA code; a comment-only edit keeps it."""
     import hashlib
     h = hashlib.sha256()
     for fn in PRODUCT_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1708_07271_gb300", "csrc", fn), "rb").read())
+        h.update(code_only(open(os.path.join(ROOT, "paper_1708_07271_gb300", "csrc", fn)).read()).encode())
     return h.hexdigest()[:16]
 
 

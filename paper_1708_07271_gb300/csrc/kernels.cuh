@@ -1244,7 +1244,9 @@ __device__ __forceinline__ void gather_grid(const uint32_t* __restrict__ colp, c
                                     ldy, n, pa, acc);
     } else {
         // tiles handed out one at a time (CTAs whose tiles ran long take
-        // fewer), the same sums whatever CTA takes a tile
+        // fewer); each tile's block sums are the same whatever CTA takes it,
+        // but which tiles a CTA adds up varies from run to run, so the FP64
+        // totals can differ in their last bits
         constexpr int T = GatherShape<KB, V>::T;
         const int64_t tiles = (n + T - 1) / T;
         __shared__ unsigned int sh_tile;
