@@ -292,6 +292,20 @@ int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host,
 int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0, const float* p_init,
                  int32_t k, float* p_out, int32_t* iters_out, double* resid_out, void* stream);
 
+/* Personalised PageRank, Eq. (1) with one-hot teleport vectors: column c of
+ * p0 is e_{seeds[c]} (1 at node seeds[c], 0 elsewhere), given by its node
+ * instead of n x k floats. seeds: HOST array of k int64, each in [0, n),
+ * read before the call returns (the caller keeps ownership). Same results as
+ * bvg_pagerank with those dense vectors (the same arithmetic on the same
+ * values); for k >= 2 the updates read no teleport vectors from memory.
+ * p_init, k, p_out, iters_out, resid_out, stream and the synchronisation as
+ * in bvg_pagerank. Errors: INVALID_ARG (NULL seeds, a seed outside [0, n),
+ * or as bvg_pagerank), UNSUPPORTED (k), CUDA, NOT_CONVERGED (outputs valid),
+ * NUMERIC. */
+int bvg_pagerank_seeds(const bvg_dev_graph* g, const bvg_pr_params* params, const int64_t* seeds,
+                       const float* p_init, int32_t k, float* p_out, int32_t* iters_out, double* resid_out,
+                       void* stream);
+
 /* ------------------------------------------------------ multi-graph batch */
 
 /* A batch of device graphs whose products run in one grid: the chain step

@@ -32,7 +32,7 @@ BVG_ERR_UNSUPPORTED = -9
 
 EXPORTED = [
     "bvg_encode", "bvg_decode", "bvg_stats", "bvg_get_refs", "bvg_host_size", "bvg_upload", "bvg_spmv_Ax",
-    "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
+    "bvg_spmv_xA", "bvg_spmv_xA_host", "bvg_pagerank", "bvg_pagerank_seeds", "bvg_dev_size", "bvg_csr_upload", "bvg_csr_spmv_Ax",
     "bvg_csr_spmv_xA", "bvg_free_host", "bvg_free_dev", "bvg_free_csr", "bvg_status_string", "bvg_last_error",
     "bvg_trace_enable", "bvg_trace_read", "bvg_dev_layout", "bvg_layout_view_get", "bvg_spmv_xA_noalloc",
     "bvg_get_config", "bvg_set_config", "bvg_mlp_create", "bvg_mlp_param_count", "bvg_mlp_set_params",
@@ -147,6 +147,8 @@ def load(build_if_needed: bool = True):
             "bvg_spmv_xA_noalloc": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
             "bvg_pagerank": ([_P, ctypes.POINTER(PrParams), _P, _P, _I32, _P, ctypes.POINTER(_I32),
                               _P, _P], ctypes.c_int),
+            "bvg_pagerank_seeds": ([_P, ctypes.POINTER(PrParams), _P, _P, _I32, _P, ctypes.POINTER(_I32),
+                                    _P, _P], ctypes.c_int),
             "bvg_dev_size": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
             "bvg_csr_upload": ([_I64, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
             "bvg_csr_spmv_Ax": ([_P, _P, _P, _I32, _I64, _P], ctypes.c_int),
@@ -479,6 +481,29 @@ def bvg_pagerank(g: DevGraph, p0=None, p_init=None, k=1, damping=0.85, tol=1e-8,
                              resid.ctypes.data, _stream(stream))
     _check(rc, "bvg_pagerank", allow=(BVG_ERR_NOT_CONVERGED,))
     return out, iters.value, resid, rc
+
+
+def bvg_pagerank_seeds(g: DevGraph, seeds, p_init=None, damping=0.85, tol=1e-8, max_iter=1000, dangling=0,
+                       out=None, stream=None):
+    """Personalised PageRank (Eq. 1) with one-hot teleport vectors: column c
+    teleports to node seeds[c] (k = len(seeds)). Returns (p (n x k),
+    iterations, residuals, status) as bvg_pagerank."""
+    import torch
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.int64).reshape(-1))
+    k = int(sd.size)
+    if out is None:
+        out = torch.empty((g.n, k), dtype=torch.float32, device="cuda")
+    for t in (p_init, out):
+        if t is not None and (not t.is_contiguous()):
+            raise ValueError("PageRank vectors must be contiguous n x k")
+    prm = PrParams(damping, tol, max_iter, dangling)
+    iters = _I32()
+    resid = np.zeros(max(k, 1), np.float64)
+    rc = load().bvg_pagerank_seeds(g.ptr, ctypes.byref(prm), sd.ctypes.data if k else None,
+                                   None if p_init is None else p_init.data_ptr(), k, out.data_ptr(),
+                                   ctypes.byref(iters), resid.ctypes.data, _stream(stream))
+    _check(rc, "bvg_pagerank_seeds", allow=(BVG_ERR_NOT_CONVERGED,))
+    return out, iters.value, resid[:k], rc
 
 
 def bvg_csr_upload(row_ptr, col, stream=None) -> CsrGraph:

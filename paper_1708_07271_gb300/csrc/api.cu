@@ -536,6 +536,8 @@ static int ensure_pr(bvg_dev_graph* g, int kb) {
     if (!g->s.st) {
         rc = dev_alloc((void**)&g->s.st, sizeof(PrState), nullptr);
         if (rc) return rc;
+        rc = dev_alloc((void**)&g->s.seed, 32 * sizeof(int64_t), nullptr);
+        if (rc) return rc;
         for (int p = 0; p < 2; p++) {
             rc = dev_alloc((void**)&g->s.sc[p], sc_bytes(), nullptr);
             if (rc) return rc;
@@ -813,7 +815,7 @@ extern "C" void bvg_free_dev(bvg_dev_graph* g) {
     if (!g) return;
     void* ptrs[] = {g->meta, g->desc, g->rowp, g->ent, g->colp, g->tent, g->titem_ptr, g->titem, g->carry_ptr, g->carry,
                     g->inv_outdeg, g->s.z,
-                    g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.partial, g->s.counter, g->s.hx,
+                    g->s.q[0], g->s.q[1], g->s.sc[0], g->s.sc[1], g->s.st, g->s.seed, g->s.partial, g->s.counter, g->s.hx,
                     g->s.hy, g->s.p0, g->s.pre[0], g->s.pre[1], g->s.pre[2], g->s.pre[3],
                     g->s.feat_tmp, g->s.wfeat, g->s.gpartial, g->pent, g->istart, g->irow, g->lrow, g->lint, g->part,
                     g->pcolp, g->pcent, g->ptitem_ptr, g->ptitem, g->plong, g->tile_win, g->lane_cols, g->row_order, g->tent16, g->px_irow, g->px_istart,
@@ -1059,14 +1061,23 @@ extern "C" int bvg_device_check(const bvg_dev_graph* gc, void* stream) {
 }
 
 // =================================================================== PageRank
-extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params, const float* p0,
-                            const float* p_init, int32_t k, float* p_out, int32_t* iters_out, double* resid_out,
-                            void* stream) {
+// The solve behind bvg_pagerank (dense teleport vectors p0, or uniform) and
+// bvg_pagerank_seeds (one-hot teleport vectors given by their nodes, host
+// array `seeds`; p0 is then NULL).
+static int pagerank_run(const bvg_dev_graph* gc, const bvg_pr_params* params, const float* p0, const int64_t* seeds,
+                        const float* p_init, int32_t k, float* p_out, int32_t* iters_out, double* resid_out,
+                        void* stream) {
     bvg_dev_graph* g = const_cast<bvg_dev_graph*>(gc);
     if (!g || !p_out) return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: NULL graph or output");
     if (k != 1 && k != 2 && k != 4 && k != 8 && k != 16 && k != 32)
         return fail(BVG_ERR_UNSUPPORTED, "bvg_pagerank: k must be 1, 2, 4, 8, 16 or 32 (got %d)", k);
-    if (!p0 && k != 1) return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: uniform teleport (p0 = NULL) needs k = 1");
+    if (!p0 && !seeds && k != 1)
+        return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank: uniform teleport (p0 = NULL) needs k = 1");
+    if (seeds)
+        for (int c = 0; c < k; c++)
+            if (seeds[c] < 0 || seeds[c] >= g->n)
+                return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank_seeds: seed %d is %lld, outside [0, %lld)", c,
+                            (long long)seeds[c], (long long)g->n);
     const double damping = params && params->damping > 0 ? params->damping : 0.85;
     const double tol = params ? params->tol_l1 : 1e-8;
     const int max_iter = params && params->max_iter > 0 ? params->max_iter : 1000;
@@ -1090,14 +1101,27 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     PrState hs{0, 0, 0, max_iter, tol};
     PrState* pst = (PrState*)g->s.st;
     BVG_CUDA_TRY(cudaMemcpyAsync(pst, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-    // the update graph reads the teleport vectors from the handle's own copy
-    if (p0)
+    // the update graph reads the teleport vectors from the handle's own copy:
+    // dense vectors copied; one-hot vectors as their k nodes (k >= 2), or
+    // written out densely for one vector (the one-launch update reads p0)
+    static const float kOne = 1.0f;
+    const float* p0_dev = nullptr;
+    bool use_seed = false;
+    if (p0) {
         BVG_CUDA_TRY(cudaMemcpyAsync(g->s.p0, p0, (size_t)g->n * kb * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    const float* p0_in = p0;
-    p0 = p0 ? g->s.p0 : nullptr;
+        p0_dev = g->s.p0;
+    } else if (seeds && kb == 1) {
+        BVG_CUDA_TRY(cudaMemsetAsync(g->s.p0, 0, (size_t)g->n * sizeof(float), st));
+        BVG_CUDA_TRY(cudaMemcpyAsync(g->s.p0 + seeds[0], &kOne, sizeof(float), cudaMemcpyHostToDevice, st));
+        p0_dev = g->s.p0;
+    } else if (seeds) {
+        BVG_CUDA_TRY(cudaMemcpyAsync(g->s.seed, seeds, (size_t)kb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        use_seed = true;
+    }
     PrArgs base{};
-    base.p0 = p0;
+    base.p0 = p0_dev;
     base.ldp0 = kb;
+    base.seed = use_seed ? g->s.seed : nullptr;
     base.inv_outdeg = g->inv_outdeg;
     base.ldq = kb;
     base.st = pst;
@@ -1109,12 +1133,12 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     base.alpha = (float)(1.0 - damping);
     base.dangling_uniform = dangling;
     base.k = k;
-    // start: q[0] = p_init / p0 / uniform, scalars into sc[0]
+    // start: q[0] = p_init / p0 / the seeds / uniform, scalars into sc[0]
     {
         PrArgs pa = base;
         pa.q_new = g->s.q[0];
         pa.sc_new = g->s.sc[0];
-        const float* start = p_init ? p_init : p0_in;
+        const float* start = p_init ? p_init : p0_dev;
         BVG_KV_CASES(launch_pr_init, g, start, kb, pa, st);
     }
     // A chunk of kChunk updates (even, so it starts on parity 0 every time)
@@ -1122,7 +1146,7 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     // updates past convergence or max_iter return at once.
     constexpr int kChunk = 8;
     const bool fused = use_fused(g, kb);
-    const int key[6] = {kb, v, dangling, p0 != nullptr, use_points(g, kb) ? 1 : 0, fused ? 1 : 0};
+    const int key[7] = {kb, v, dangling, p0_dev != nullptr, use_points(g, kb) ? 1 : 0, fused ? 1 : 0, use_seed};
     if (g->s.pr_exec && (memcmp(key, g->s.pr_key, sizeof(key)) || g->s.pr_key_alpha != base.alpha ||
                          g->s.pr_key_ptr != g->s.q[0] || g->s.pr_key_z != g->s.z))
         drop_pr_graph(g);
@@ -1233,4 +1257,17 @@ extern "C" int bvg_pagerank(const bvg_dev_graph* gc, const bvg_pr_params* params
     if (hst->numeric) return fail(BVG_ERR_NUMERIC, "bvg_pagerank: non-finite value at update %d", hst->iter);
     if (!hst->done) return fail(BVG_ERR_NOT_CONVERGED, "bvg_pagerank: not converged after %d updates", hst->iter);
     return BVG_OK;
+}
+
+extern "C" int bvg_pagerank(const bvg_dev_graph* g, const bvg_pr_params* params, const float* p0,
+                            const float* p_init, int32_t k, float* p_out, int32_t* iters_out, double* resid_out,
+                            void* stream) {
+    return pagerank_run(g, params, p0, nullptr, p_init, k, p_out, iters_out, resid_out, stream);
+}
+
+extern "C" int bvg_pagerank_seeds(const bvg_dev_graph* g, const bvg_pr_params* params, const int64_t* seeds,
+                                  const float* p_init, int32_t k, float* p_out, int32_t* iters_out,
+                                  double* resid_out, void* stream) {
+    if (!seeds) return fail(BVG_ERR_INVALID_ARG, "bvg_pagerank_seeds: NULL seeds");
+    return pagerank_run(g, params, nullptr, seeds, p_init, k, p_out, iters_out, resid_out, stream);
 }

@@ -141,6 +141,7 @@ struct DevScratch {
     float* q[2] = {nullptr, nullptr};   // PageRank iterates (unnormalised), n x pr_kcap
     double* sc[2] = {nullptr, nullptr}; // PageRank scalars per parity: [3][32] (1/S, dangling, resid)
     void* st = nullptr;                 // PageRank state (kernels.cuh PrState)
+    int64_t* seed = nullptr;            // PageRank one-hot teleport nodes (32)
     double* partial = nullptr;          // per-CTA FP64 partial sums
     double* gpartial = nullptr;         // per group of CTAs (two-level reduction)
     unsigned int* counter = nullptr;    // [0]: groups finished; [1 + g]: CTAs of group g finished
@@ -157,7 +158,7 @@ struct DevScratch {
     // CUDA graph of a chunk of PageRank updates, and what it was built for
     void* pr_exec = nullptr;            // cudaGraphExec_t
     void* cap_stream = nullptr;         // private stream the update graph is captured on
-    int pr_key[6] = {0, 0, 0, 0, 0, 0}; // kb, v, dangling, has p0, point columns, fused update
+    int pr_key[7] = {0, 0, 0, 0, 0, 0, 0}; // kb, v, dangling, has p0, point columns, fused update, seeds
     float pr_key_alpha = 0.f;
     const void* pr_key_ptr = nullptr;   // q[0] when captured
     const void* pr_key_z = nullptr;     // z when captured

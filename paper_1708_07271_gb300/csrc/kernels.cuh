@@ -26,8 +26,9 @@ __device__ __forceinline__ float sc_dangling_f32(const double* sc, int c) {
 }
 
 struct PrArgs {
-    const float* p0;           // teleport vectors (n x k, ld ldp0) or NULL = uniform 1/n
+    const float* p0;           // teleport vectors (n x k, ld ldp0) or NULL: seed, else uniform 1/n
     int64_t ldp0;
+    const int64_t* seed;       // with p0 NULL: k nodes, teleport vector c = e_seed[c] (one-hot), or NULL
     const float* inv_outdeg;   // 0 marks a row without successors
     const float* q_prev;       // previous iterate, unnormalised (n x k, ld ldq)
     float* q_new;
@@ -1165,12 +1166,16 @@ __device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restr
     // FP32 adds (a few roundings, relative to partial sums of nonnegative
     // terms), then compensated across the warps of the block
     float Ssum[V], R[V], Dg[V];
-    float dl[V];  // the previous update's dangling mass, per right-hand side of this lane
+    float dl[V];     // the previous update's dangling mass, per right-hand side of this lane
+    int64_t sd[V];   // one-hot teleport nodes of this lane's right-hand sides
     const float un = EPI == 1 ? 1.0f / (float)n : 0.0f;  // (an int64 conversion: once, not per column)
 #pragma unroll
     for (int v = 0; v < V; v++) {
         Ssum[v] = R[v] = Dg[v] = 0.f;
-        if constexpr (EPI == 1) dl[v] = sc_dangling_f32(pa.sc_prev, lane * V + v);
+        if constexpr (EPI == 1) {
+            dl[v] = sc_dangling_f32(pa.sc_prev, lane * V + v);
+            sd[v] = pa.seed ? __ldg(pa.seed + lane * V + v) : -1;
+        }
     }
 #pragma unroll
     for (int q = 0; q < CPT; q++) {
@@ -1202,7 +1207,7 @@ __device__ __forceinline__ bool gather_tile(int64_t blk, const uint32_t* __restr
             }
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                const float p0j = pa.p0 ? p0v.v[v] : un;
+                const float p0j = pa.p0 ? p0v.v[v] : pa.seed ? (j == sd[v] ? 1.0f : 0.0f) : un;
                 const float gj = pa.dangling_uniform ? un : p0j;
                 const float qj = pa.alpha * p0j + (1.0f - pa.alpha) * (out.v[v] + dl[v] * gj);
                 qn.v[v] = qj;
@@ -1302,7 +1307,7 @@ __global__ void __launch_bounds__(GatherShape<KB, V>::NT, GatherShape<KB, V>::NT
     gather_grid<KB, V, EPI, false>(colp, ent, titem_ptr, titem, nullptr, nullptr, long_chunk, z, ldz, y, ldy, n, pa);
 }
 
-// PageRank start: q_0 = p_init (or p0, or uniform), and the scalars of the
+// PageRank start: q_0 = p_init (or p0, or the one-hot seeds, or uniform), and the scalars of the
 // start (1/S_0, dangling mass) by the same deterministic reduction.
 template <int KB, int V>
 __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_init, int64_t ldi, int64_t n,
@@ -1320,7 +1325,10 @@ __global__ void __launch_bounds__(256) k_pr_init(const float* __restrict__ p_ini
     for (int64_t j = a + g; j < end; j += NG) {
         Vec<V> pv;
         if (p_init) pv = ldv<V>(p_init + j * ldi + lane * V);
-        else {
+        else if (pa.seed) {
+#pragma unroll
+            for (int v = 0; v < V; v++) pv.v[v] = j == __ldg(pa.seed + lane * V + v) ? 1.0f : 0.0f;
+        } else {
 #pragma unroll
             for (int v = 0; v < V; v++) pv.v[v] = un;
         }
