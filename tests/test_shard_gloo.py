@@ -143,7 +143,7 @@ def _row_worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_row_sharded_products_and_pagerank(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
