@@ -57,6 +57,8 @@ static int check_blocks(const bvg_dev_graph* const* blocks, int32_t nblocks, con
     for (int32_t b = 0; b < nblocks; b++) {
         if (!blocks[b]) return fail(BVG_ERR_INVALID_ARG, "%s: NULL block %d", what, b);
         if (blocks[b]->n != blocks[0]->n) return fail(BVG_ERR_INVALID_ARG, "%s: blocks of different n", what);
+        if (blocks[b]->device != blocks[0]->device)
+            return fail(BVG_ERR_INVALID_ARG, "%s: blocks on different devices", what);
     }
     if (blocks[0]->n == 0) return BVG_OK;
     int rc;
