@@ -363,6 +363,23 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
         return rc;
     }
     double best_pull = 1e300;
+    // one right-hand side: the one-launch pull where every row tile fits it
+    // (it has no item size, tile or interval rule to choose), against the
+    // two-kernel pull's settings below
+    const bool px = kpow == 1 && g->px_ok;
+    if (px) {
+        bvg_launch_config c = best;
+        c.pull_fused = 1;
+        double us = 0;
+        if ((rc = bvg_set_config(g, &c)) || (rc = time_op(pull, st, t, &us))) {
+            bvg_set_config(g, &base);
+            release();
+            return rc;
+        }
+        g->tune.candidates++;
+        best_pull = us;
+        b2 = c;
+    }
     std::vector<int> minlens = {32};
     if (g->mean_interval > 0) minlens.insert(minlens.end(), {16, 1 << 20});  // 1 << 20: expand every interval
     for (int ml : minlens) {
@@ -373,6 +390,7 @@ extern "C" int bvg_autotune(bvg_dev_graph* g, int32_t k, const char* cache_path,
                 c.pull_item = item;
                 c.prefix_min_len = ml;
                 c.pull_prefix = -1;
+                if (px) c.pull_fused = 0;
                 double us = 0;
                 if ((rc = bvg_set_config(g, &c)) || (rc = time_op(pull, st, t, &us))) {
                     bvg_set_config(g, &base);

@@ -44,6 +44,8 @@ def test_autotune_and_cache(tmp_path, k):
     assert res["from_cache"] == 0 and res["candidates"] > 0
     assert res["pull_tile"] in (128, 256, 512, 1024) and res["gather_pdl"] in (0, 1)
     assert res["col_block"] <= max(1, k) and res["push_us_best"] > 0 and res["pull_us_best"] > 0
+    if k == 1:  # the graph's row tiles fit the one-launch pull: the search chose between the two pulls
+        assert res["pull_fused"] in (0, 1)
     check(g, ref, dg, k)
     key = bvg.bvg_autotune_key(dg, k)
     assert key.endswith(f"/k{k}")
