@@ -231,6 +231,27 @@ def test_pagerank_dense_solve(seed):
         assert abs(p.sum() - 1.0) < 1e-12
 
 
+def test_pagerank_one_hot_columns_dense_solve():
+    """Personalised PageRank with one-hot teleport vectors (e_s, the input
+    form of bvg_pagerank_seeds), several columns in one run: each column is
+    the dense linear solve for its own seed, for both dangling policies."""
+    n = 150
+    rp, col = random_graph(n, 0.012, 905)
+    assert (np.diff(rp) == 0).any()
+    A = dense_matrix(rp, col)
+    seeds = np.array([0, 17, 17, 149, int(np.nonzero(np.diff(rp) == 0)[0][0])])  # a repeat, the last row, a dangling row
+    P0 = np.zeros((n, len(seeds)))
+    P0[seeds, np.arange(len(seeds))] = 1.0
+    for dangling in (0, 1):
+        p, it, res = oracle.pagerank(rp, col, alpha=ALPHA, p0=P0, tol=1e-14, max_iter=10_000, dangling=dangling)
+        assert (res < 1e-14).all()
+        for c, s in enumerate(seeds):
+            e = np.zeros(n)
+            e[s] = 1.0
+            np.testing.assert_allclose(p[:, c], pagerank_solve(A, ALPHA, e, dangling), rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(p[:, 1], p[:, 2])
+
+
 def test_pagerank_mass_linearity_contraction_start():
     g = synth.copying_model(synth.tiny_web())
     n = g.n
