@@ -109,9 +109,10 @@ int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
  * Errors: INVALID_ARG, CORRUPT. */
 int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx);
 
-/* The encoding's bitstream (Sec. 4 representation written with the codes of
- * R4: gamma-coded reference offsets, copy blocks, interval and residual
- * counts, delta-coded gaps), most significant bit first in 64-bit words.
+/* The encoding's bitstream (the Sec. 4 representation; the paper fixes no
+ * codes, this library writes gamma-coded reference offsets, copy blocks,
+ * interval and residual counts, and delta-coded gaps), most significant bit
+ * first in 64-bit words.
  * *nbits gets its length; if words != NULL the first ceil(nbits / 64) words
  * are copied there (cap_words at least that, else INVALID_ARG). Host only. */
 int bvg_bitstream_get(const bvg_host_graph* g, uint64_t* words, int64_t cap_words, int64_t* nbits);
@@ -134,14 +135,17 @@ int bvg_decode_bits(int64_t n, int64_t m, const bvg_encode_params* params, const
  * the products. after < 0 disables the hook (the default). Always BVG_OK. */
 int bvg_debug_fail_alloc(int64_t after);
 
-/* Fills *out with the sizes of the encoding. */
+/* Fills *out with the sizes of the encoding (Sec. 4's split of the
+ * difference rows; nnz_diff is Table 1's m'). Host only. Errors:
+ * INVALID_ARG. */
 int bvg_stats(const bvg_host_graph* g, bvg_graph_stats* out);
 
-/* Copies the reference vector (r_i, or -1 for none; n entries) and, if
- * depth != NULL, the chain depth of every row. */
+/* Copies the reference vector (Sec. 4's r_i, or -1 for none; n entries)
+ * and, if depth != NULL, the chain depth of every row, into caller host
+ * arrays. Errors: INVALID_ARG. */
 int bvg_get_refs(const bvg_host_graph* g, int32_t* ref, int32_t* depth);
 
-/* Number of rows n and edges m of an encoding. */
+/* Number of rows n and edges m of an encoding. Errors: INVALID_ARG. */
 int bvg_host_size(const bvg_host_graph* g, int64_t* n, int64_t* m);
 
 /* Read-only host view of the device layout that bvg_upload copies to the GPU
@@ -204,9 +208,10 @@ int bvg_pull_items_fill(const bvg_host_graph* g, int32_t item, int32_t min_len, 
 int bvg_point_cols_size(const bvg_host_graph* g, int64_t* entries, int64_t* tail_items);
 int bvg_point_cols_fill(const bvg_host_graph* g, uint32_t* colp, uint32_t* ent, uint32_t* titem_ptr, uint32_t* titem);
 
-/* Builds the device layout of `g` (row-major difference rows for A x^T, the
- * same entries grouped by column for x A, per-row reference offsets and
- * chain depths, 1/outdeg) and copies it to the current device on `stream`.
+/* Builds the device layout of `g` (Sec. 4's difference rows: row-major for
+ * A x^T, the same entries grouped by column for x A, per-row reference
+ * offsets and chain depths, 1/outdeg for Eq. (1)) and copies it to the
+ * current device on `stream`.
  * Also allocates the scratch of one-column products. The first product with
  * a wider column block grows that scratch, and the first x A with a column
  * block of 4 or more (under the default launch configuration) builds the
@@ -216,11 +221,19 @@ int bvg_point_cols_fill(const bvg_host_graph* g, uint32_t* colp, uint32_t* ent, 
  * is owned by the caller (bvg_free_dev). Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_upload(const bvg_host_graph* g, void* stream, bvg_dev_graph** out);
 
-/* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j. The row sums
- * sum_j A'_ij x_j are formed per work item (bvg_pull_items_size), then each
- * row tile adds its rows' partials and resolves the chains in shared memory
- * (a row with more than 32 items, a hub of a power-law graph, is summed by
- * the whole tile's threads).
+/* y = A x^T (pull, Sec. 4): y_i = y_{r_i} + sum_j A'_ij x_j.
+ * One right-hand side (a column block of width 1), by default: one launch
+ * per product where every tile of 1024 rows fits it (the columns its rows'
+ * entries reference, and those of the 32 rows before it, span at most 1792
+ * ids; at most 2048 work items; no interval kept whole): x of the tile's
+ * column window, the work items' sums, the row sums and the chains in shared
+ * memory, with exact 64-bit fixed-point sums (y_i is the exact sum rounded
+ * once to FP32) where the window's x spans few enough binades, compensated
+ * sums otherwise (launch configuration pull_fused).
+ * Otherwise: the row sums sum_j A'_ij x_j are formed per work item
+ * (bvg_pull_items_size), then each row tile adds its rows' partials and
+ * resolves the chains in shared memory (a row with more than 32 items, a hub
+ * of a power-law graph, is summed by the whole tile's threads).
  * x, y: device n x k, leading dimension ld. Asynchronous. Errors:
  * INVALID_ARG, OOM (first call with a wider column block), CUDA. */
 int bvg_spmv_Ax(const bvg_dev_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
@@ -272,15 +285,17 @@ int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float* y, int32_
  * BVG_OK. The paper has no counterpart. */
 int bvg_device_check(const bvg_dev_graph* g, void* stream);
 
-/* Same as bvg_spmv_xA with x and y in HOST memory (page-locked, which copies
- * fastest, or pageable), n x k, ld == k: copies x to device scratch, runs the
- * product, copies y back, and synchronises `stream` before returning.
+/* Same as bvg_spmv_xA (Proposition 1 read for the left product) with x and
+ * y in HOST memory (page-locked, which copies fastest, or pageable), n x k,
+ * ld == k: copies x to device scratch, runs the product, copies y back, and
+ * synchronises `stream` before returning. The caller keeps both buffers.
  * Errors: INVALID_ARG (also when x and y alias), OOM, CUDA. */
 int bvg_spmv_xA_host(const bvg_dev_graph* g, const float* x_host, float* y_host, int32_t k, void* stream);
 
 /* PageRank by power iteration, Eq. (1): p_t = alpha p0 + (1 - alpha) p_{t-1} M,
- * M = D^-1 A, for k teleport vectors at once (columns of p0, device n x k;
- * NULL = uniform 1/n, then k must be 1). p_init (device n x k or NULL =
+ * M = D^-1 A, for k teleport vectors at once (k = 1, 2, 4, 8, 16 or 32, else
+ * UNSUPPORTED; columns of p0, device n x k; NULL = uniform 1/n, then k must
+ * be 1). p_init (device n x k or NULL =
  * start from p0) is the starting iterate. Iterates are FP32; the dangling
  * mass, the normalisation sum and the L1 change are FP64 on the device.
  * Stops after the first update with ||p_t - p_{t-1}||_1 < tol in every
@@ -316,7 +331,8 @@ int bvg_pagerank_seeds(const bvg_dev_graph* g, const bvg_pr_params* params, cons
  * `stream` is unused (creation does no device work). Errors: INVALID_ARG,
  * OOM, CUDA. */
 int bvg_batch_create(const bvg_dev_graph* const* gs, int32_t count, void* stream, bvg_batch** out);
-/* Number of graphs, total rows and total edges of a batch. */
+/* Number of graphs, total rows and total edges of a batch. Errors:
+ * INVALID_ARG. */
 int bvg_batch_size(const bvg_batch* b, int32_t* count, int64_t* total_n, int64_t* total_m);
 /* y_i = x_i A_i for every graph i: xs[i], ys[i] (host arrays of `count`
  * DEVICE pointers) are row-major n_i x k with leading dimension k, 4-byte
@@ -352,12 +368,14 @@ void bvg_free_batch(bvg_batch* b);
 /* New network with He-style initial weights drawn from `seed` (splitmix64 +
  * Box-Muller), zero biases. Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_mlp_create(uint64_t seed, bvg_mlp** out);
-/* Number of parameters (4673). */
+/* Number of parameters (4673); returns the count, not a status. */
 int bvg_mlp_param_count(void);
 /* Copies count (= 4673) host floats into the network, resets Adam, rounds
- * the BF16 copy. Synchronises the device. */
+ * the BF16 copy. Synchronises the device. Errors: INVALID_ARG (NULL, or
+ * count != 4673), CUDA. */
 int bvg_mlp_set_params(bvg_mlp* net, const float* host, int64_t count);
-/* Copies the FP32 parameters to host memory. Synchronises the device. */
+/* Copies the FP32 parameters to host memory (count = 4673 floats).
+ * Synchronises the device. Errors: INVALID_ARG, CUDA. */
 int bvg_mlp_get_params(const bvg_mlp* net, float* host, int64_t count);
 /* Node features of g into feat (device, n x 8 floats, 16-byte aligned):
  * log1p(in-degree), log1p(out-degree), reference-chain depth (Sec. 4),
@@ -365,31 +383,36 @@ int bvg_mlp_get_params(const bvg_mlp* net, float* host, int64_t count);
  * (Sec. 4), log1p(mean out-degree of the out-neighbours), log1p(weighted
  * in-degree sum_{j -> i} 1/outdeg(j)), 0, 0. The degrees come from two
  * compressed products: (1, 1/outdeg) A with k = 2, and A outdeg^T.
- * May grow the graph's scratch. Asynchronous on `stream`. */
+ * May grow the graph's scratch. Asynchronous on `stream`. Errors:
+ * INVALID_ARG (NULL, feat not 16-byte aligned), OOM, CUDA. */
 int bvg_features(const bvg_dev_graph* g, float* feat, void* stream);
 /* yhat (device, n floats) for features feat (device n x 8, 16-byte aligned).
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. */
 int bvg_mlp_predict(const bvg_mlp* net, const float* feat, int64_t n, float* yhat, void* stream);
 /* Mean squared error of yhat against target (device, n floats) and its
  * gradient with respect to the FP32 parameters (rounding steps pass
  * gradients straight through). *loss (may be NULL) gets the loss; grad_host
  * (may be NULL, else 4673 host floats) the gradient, which also stays in the
- * handle for bvg_mlp_adam. Synchronises `stream`. */
+ * handle for bvg_mlp_adam. Synchronises `stream`. Errors: INVALID_ARG, OOM,
+ * CUDA. */
 int bvg_mlp_grad(bvg_mlp* net, const float* feat, const float* target, int64_t n, double* loss,
                  float* grad_host, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
- * the gradient of the last bvg_mlp_grad, then re-rounds the BF16 weights. */
+ * the gradient of the last bvg_mlp_grad, then re-rounds the BF16 weights.
+ * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. */
 int bvg_mlp_adam(bvg_mlp* net, float lr, void* stream);
 /* Trains on `count` graphs with known PageRank vectors p_star[i] (device,
  * n_i floats): targets n p*, `epochs` passes over the nodes
  * in chunks of `batch` (>= 128) nodes, one Adam step per chunk. *loss (may
  * be NULL) gets the mean loss of the last pass. Allocates temporaries for
- * the features and frees them before returning. Synchronises `stream`. */
+ * the features and frees them before returning. Synchronises `stream`.
+ * Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_warmstart_train(bvg_mlp* net, const bvg_dev_graph* const* gs, const float* const* p_star, int32_t count,
                         int32_t epochs, float lr, int64_t batch, double* loss, void* stream);
 /* p_init (device, n floats) = max(yhat, 0.05) normalised to sum 1 (FP64
  * sum) for g, a starting iterate for bvg_pagerank (uniform 1/n where the sum
- * is not finite). May grow the graph's scratch. Asynchronous on `stream`. */
+ * is not finite). May grow the graph's scratch. Asynchronous on `stream`.
+ * Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_warmstart_predict(const bvg_mlp* net, const bvg_dev_graph* g, float* p_init, void* stream);
 void bvg_free_mlp(bvg_mlp* net);
 
@@ -417,18 +440,24 @@ typedef struct {
                                -1 or 1 whenever every tile's x window (at most 1792 columns) and work items (at
                                most 2048) fit the kernel (default -1), 0 never */
 } bvg_launch_config;
+/* The graph's configuration into *out. Errors: INVALID_ARG. */
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
+/* Applies *in (each field in the range its comment gives, else INVALID_ARG;
+ * a new pull_item or prefix_min_len rebuilds the pull's work items: OOM,
+ * CUDA). */
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
 
 /* Autotuner. Times the products of g with k right-hand sides under each
  * candidate launch configuration (CUDA events on `stream`, median of 7 after
  * 2 warm-up calls, warm caches): first the push (x A) over the widest column
  * block (the largest power of two <= min(k, 32) and up to three halvings)
- * times gather overlap on/off times event or point columns, then the pull
- * (A x^T) over entries per work item {4, 8, 16} times rows per CTA of the
- * row pass {256, 512} times the length from which
- * intervals stay unexpanded (32; also 16 and "never" when the graph has
- * intervals; rebuilding the items is part of the search).
+ * times gather overlap on/off times event or point columns, and for one
+ * right-hand side the one-launch x A kernel too; then the pull (A x^T): for
+ * one right-hand side the one-launch kernel where the graph fits it, and
+ * the two-kernel pull over entries per work item {4, 8, 16} times rows per
+ * CTA of the row pass {256, 512} times the length from which intervals stay
+ * unexpanded (32; also 16 and "never" when the graph has intervals;
+ * rebuilding the items is part of the search).
  * It applies the fastest choice to g (bvg_get_config shows it). With
  * cache_path != NULL it first looks the choice up in that JSON file under
  * the key "<device name>/sm<count>/<layout fingerprint>/k<k>" and, after a
@@ -446,17 +475,22 @@ typedef struct {
     double pull_us_default;  /* A x^T likewise */
     double pull_us_best;
 } bvg_autotune_info;
+/* The last search's counts and timings. Errors: INVALID_ARG. */
 int bvg_autotune_info_get(const bvg_dev_graph* g, bvg_autotune_info* out);
-/* The cache key bvg_autotune uses for g and k (NUL-terminated, into buf of cap bytes). */
+/* The cache key bvg_autotune uses for g and k (NUL-terminated, into buf of
+ * cap bytes). Errors: INVALID_ARG (also when buf is too small), CUDA. */
 int bvg_autotune_key(const bvg_dev_graph* g, int32_t k, char* buf, int32_t cap);
 /* Host-only access to the cache file (no GPU needed): *found = 1 and *out
- * set when `key` is present; a missing or unreadable file gives *found = 0. */
+ * set when `key` is present; a missing or unreadable file gives *found = 0.
+ * Errors: INVALID_ARG. */
 int bvg_autotune_cache_lookup(const char* path, const char* key, bvg_launch_config* out, int32_t* found);
-/* Inserts or replaces `key` (with the timings it was chosen by, in us). */
+/* Inserts or replaces `key` (with the timings it was chosen by, in us).
+ * Errors: INVALID_ARG (also when the file cannot be written or renamed into
+ * place). */
 int bvg_autotune_cache_store(const char* path, const char* key, const bvg_launch_config* cfg, double push_us,
                              double pull_us);
 
-/* Number of rows n of a device graph. */
+/* Number of rows n and edges m of a device graph. Errors: INVALID_ARG. */
 int bvg_dev_size(const bvg_dev_graph* g, int64_t* n, int64_t* m);
 
 /* Sizes of the device layout, for byte models: 32-bit words of the row-major
@@ -468,6 +502,7 @@ typedef struct {
     int64_t tail_items;                                /* the push gather's tail items (bvg_layout_view) */
     int64_t point_entries, point_tail_items;           /* the point columns (bvg_point_cols_size); 0 until built */
 } bvg_layout_info;
+/* Errors: INVALID_ARG. */
 int bvg_dev_layout(const bvg_dev_graph* g, bvg_layout_info* out);
 
 /* ------------------------------------------ biclique representation */
@@ -504,13 +539,15 @@ typedef struct {
  * (bvg_free_biclique). Synchronous. Errors: INVALID_ARG, OOM. */
 int bvg_biclique_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                         const bvg_biclique_params* params, bvg_biclique** out);
+/* Sizes of the decomposition. Errors: INVALID_ARG. */
 int bvg_biclique_stats(const bvg_biclique* b, bvg_biclique_info* out);
 /* The decomposition into caller buffers sized from bvg_biclique_stats:
  * s_ptr[bicliques + 1], s_idx[s_total] (the rows of biclique r are
  * s_idx[s_ptr[r], s_ptr[r + 1]), increasing), c_ptr[bicliques + 1],
  * c_idx[c_total] (its columns, increasing), r_ptr[n + 1], r_col[residual]
  * (the residual edges of row i, increasing). The bicliques and the residual
- * edges are disjoint and together are exactly the edges of A. */
+ * edges are disjoint and together are exactly the edges of A. Errors:
+ * INVALID_ARG. */
 int bvg_biclique_get(const bvg_biclique* b, int64_t* s_ptr, int32_t* s_idx, int64_t* c_ptr, int32_t* c_idx,
                      int64_t* r_ptr, int32_t* r_col);
 /* The lists a device product gathers from, into caller buffers: row_ptr2
@@ -542,8 +579,6 @@ int bvg_biclique_spmv_Ax(const bvg_biclique_dev* d, const float* x, float* y, in
  * residual edges into column j. As bvg_biclique_spmv_Ax otherwise. */
 int bvg_biclique_spmv_xA(const bvg_biclique_dev* d, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 void bvg_free_biclique_dev(bvg_biclique_dev* d);
-
-/* --------------------------------------------------- plain CSR baseline */
 
 /* ------------------------------------------------------------ streamed blocks */
 /* y = M x^T for a matrix whose compressed structure need not fit in device
@@ -577,19 +612,27 @@ int bvg_stream_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
  * serialised. Errors: INVALID_ARG (also x or y not memory of the handle's
  * device), CUDA. */
 int bvg_stream_spmv(bvg_stream* s, const float* x, float* y, int32_t k, int64_t ld, void* stream);
+/* Sizes of the streamed encoding. Errors: INVALID_ARG. */
 int bvg_stream_info(const bvg_stream* s, bvg_stream_info_t* out);
-/* The references of the block encodings (rows of M, -1 for none), n ints. */
+/* The references of the block encodings (rows of M, -1 for none), n ints
+ * into a caller host array. Errors: INVALID_ARG. */
 int bvg_stream_get_refs(const bvg_stream* s, int32_t* ref);
 void bvg_free_stream(bvg_stream* s);
 
+/* --------------------------------------------------- plain CSR baseline */
+
 /* Device CSR of A and of A^T built from a host CSR (same input rules as
  * bvg_encode), for the plain sparse product the compressed one is compared
- * with (Sec. 5 compares A' against A). */
+ * with (Sec. 5 compares A' against A). *out is owned by the caller
+ * (bvg_free_csr). Errors: INVALID_ARG, BAD_GRAPH, OOM, CUDA. */
 int bvg_csr_upload(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, void* stream,
                    bvg_csr_graph** out);
-/* y = A x^T over the CSR of A (row per thread group, no atomics). */
+/* y = A x^T over the CSR of A (a row per thread group, a hub row by a whole
+ * CTA, no atomics). x, y: device n x k, leading dimension ld. Asynchronous.
+ * Errors: INVALID_ARG, CUDA. */
 int bvg_csr_spmv_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
-/* y = x A over the CSR of A^T (same kernel, transposed pattern). */
+/* y = x A over the CSR of A^T (same kernel, transposed pattern). As
+ * bvg_csr_spmv_Ax otherwise. */
 int bvg_csr_spmv_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 /* The same two products by the vendor library (cusparseSpMV for one
  * right-hand side with ld = 1, cusparseSpMM on the row-major n x k block
@@ -608,7 +651,8 @@ int bvg_csr_cusparse_xA(const bvg_csr_graph* g, const float* x, float* y, int32_
  * inside one block: A = sum_b A_b, where A_b holds A's entries in columns
  * [cuts[b], cuts[b+1]) and is encoded and uploaded on its own (n rows, the
  * same ids: bvg_encode of the column-restricted CSR, then bvg_upload), so
- * that each block chooses its own references. All blocks have the same n.
+ * that each block chooses its own references. All blocks have the same n and
+ * were uploaded on the same device.
  * cuts: host array of nblocks + 1 column bounds, cuts[0] = 0, cuts[nblocks]
  * = n, nondecreasing; block b must hold no entry outside its columns (not
  * checked: such entries are dropped from x A). scratch: device n x k (leading
@@ -618,8 +662,10 @@ int bvg_csr_cusparse_xA(const bvg_csr_graph* g, const float* x, float* y, int32_
  *   x A:   block b's product goes to scratch, and its rows [cuts[b],
  *          cuts[b+1]) (the only nonzero ones) are copied into y; with one
  *          contiguous right-hand side (k = 1, ld = 1) and block bounds that
- *          are multiples of 1024 (or n), a block whose product runs as the
- *          one-launch kernel computes just its own columns, into y;
+ *          are multiples of 1024 (or n), one launch computes every block's
+ *          own column tiles into y when all blocks (at most 16) run the
+ *          one-launch kernel, and otherwise each block that does computes
+ *          just its own columns, into y;
  *   A x^T: y = sum_b A_b x^T, added in block order in FP32 (one rounding
  *          more per block). */
 int bvg_spmv_xA_colblocks(const bvg_dev_graph* const* blocks, const int64_t* cuts, int32_t nblocks,
@@ -638,15 +684,19 @@ typedef struct {
 } bvg_trace_entry;
 
 /* Turns tracing on (enable != 0) or off. Enabling allocates a pool of events
- * (host-side setup; call outside any stream capture). */
+ * (host-side setup; call outside any stream capture). The paper has no
+ * counterpart. Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_trace_enable(bvg_dev_graph* g, int enable);
 /* Waits for the recorded events, aggregates them per kernel family into out
  * (at most cap entries; *count = families written) and clears the record.
- * Launches beyond the pool (65536 per read) are not recorded. */
+ * Launches beyond the pool (65536 per read) are not recorded. Errors:
+ * INVALID_ARG, CUDA. */
 int bvg_trace_read(bvg_dev_graph* g, bvg_trace_entry* out, int32_t cap, int32_t* count);
 
 /* ------------------------------------------------------------- lifetime */
 
+/* Release a handle and the memory it owns (host, device and page-locked);
+ * NULL is ignored. No call may use the handle afterwards. */
 void bvg_free_host(bvg_host_graph* g);
 void bvg_free_dev(bvg_dev_graph* g);
 void bvg_free_csr(bvg_csr_graph* g);
