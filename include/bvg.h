@@ -104,8 +104,9 @@ typedef struct {
 int bvg_encode(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                const bvg_encode_params* params, bvg_host_graph** out);
 
-/* Decodes the bitstream of `g` back into CSR. row_ptr (n+1) and col_idx (m)
- * are caller-allocated host arrays. decode(encode(A)) == A bit for bit.
+/* Decodes the bitstream of `g` back into CSR (each row rebuilt from its
+ * reference row and difference, Sec. 4). row_ptr (n+1) and col_idx (m) are
+ * caller-allocated host arrays. decode(encode(A)) == A bit for bit.
  * Errors: INVALID_ARG, CORRUPT. */
 int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx);
 
@@ -114,7 +115,8 @@ int bvg_decode(const bvg_host_graph* g, int64_t* row_ptr, int32_t* col_idx);
  * interval and residual counts, and delta-coded gaps), most significant bit
  * first in 64-bit words.
  * *nbits gets its length; if words != NULL the first ceil(nbits / 64) words
- * are copied there (cap_words at least that, else INVALID_ARG). Host only. */
+ * are copied there (cap_words at least that, else INVALID_ARG). Host only.
+ * Errors: INVALID_ARG. */
 int bvg_bitstream_get(const bvg_host_graph* g, uint64_t* words, int64_t cap_words, int64_t* nbits);
 
 /* Decodes a caller-provided bitstream of n rows and m edges, written with
@@ -175,6 +177,8 @@ typedef struct {
     const uint32_t* titem_ptr;
     const uint32_t* titem;
 } bvg_layout_view;
+/* Fills *out; the arrays belong to g. Errors: INVALID_ARG, OOM (building the
+ * layout), UNSUPPORTED (2^32 words or 2^30 column entries or more). */
 int bvg_layout_view_get(const bvg_host_graph* g, bvg_layout_view* out);
 
 /* -------------------------------------------------------------- device side */
@@ -282,7 +286,7 @@ int bvg_spmv_xA_noalloc(const bvg_dev_graph* g, const float* x, float* y, int32_
  * graph (the fused x A kernel waits for its TMA copies at most about 2 s and
  * then marks the graph and writes NaN outputs rather than hang): synchronises
  * `stream`, returns BVG_ERR_TIMEOUT (and clears the mark) if one did, else
- * BVG_OK. The paper has no counterpart. */
+ * BVG_OK. The paper has no counterpart. Errors: INVALID_ARG, TIMEOUT, CUDA. */
 int bvg_device_check(const bvg_dev_graph* g, void* stream);
 
 /* Same as bvg_spmv_xA (Proposition 1 read for the left product) with x and
@@ -334,7 +338,8 @@ int bvg_batch_create(const bvg_dev_graph* const* gs, int32_t count, void* stream
 /* Number of graphs, total rows and total edges of a batch. Errors:
  * INVALID_ARG. */
 int bvg_batch_size(const bvg_batch* b, int32_t* count, int64_t* total_n, int64_t* total_m);
-/* y_i = x_i A_i for every graph i: xs[i], ys[i] (host arrays of `count`
+/* y_i = x_i A_i for every graph i (the push of Proposition 1 on each graph's
+ * own encoding): xs[i], ys[i] (host arrays of `count`
  * DEVICE pointers) are row-major n_i x k with leading dimension k, 4-byte
  * aligned (16-byte alignment and k % 4 == 0 enable 128-bit accesses). The
  * pointer table is staged through pinned memory and copied on `stream`
@@ -401,7 +406,8 @@ int bvg_mlp_grad(bvg_mlp* net, const float* feat, const float* target, int64_t n
  * the gradient of the last bvg_mlp_grad, then re-rounds the BF16 weights.
  * Asynchronous on `stream`. Errors: INVALID_ARG, CUDA. */
 int bvg_mlp_adam(bvg_mlp* net, float lr, void* stream);
-/* Trains on `count` graphs with known PageRank vectors p_star[i] (device,
+/* Trains on `count` graphs with known PageRank vectors p_star[i] (Eq. (1)'s
+ * fixed points; the paper has no learned part) (device,
  * n_i floats): targets n p*, `epochs` passes over the nodes
  * in chunks of `batch` (>= 128) nodes, one Adam step per chunk. *loss (may
  * be NULL) gets the mean loss of the last pass. Allocates temporaries for
@@ -410,9 +416,10 @@ int bvg_mlp_adam(bvg_mlp* net, float lr, void* stream);
 int bvg_warmstart_train(bvg_mlp* net, const bvg_dev_graph* const* gs, const float* const* p_star, int32_t count,
                         int32_t epochs, float lr, int64_t batch, double* loss, void* stream);
 /* p_init (device, n floats) = max(yhat, 0.05) normalised to sum 1 (FP64
- * sum) for g, a starting iterate for bvg_pagerank (uniform 1/n where the sum
- * is not finite). May grow the graph's scratch. Asynchronous on `stream`.
- * Errors: INVALID_ARG, OOM, CUDA. */
+ * sum; uniform 1/n where the sum is not finite) for g: a starting iterate
+ * for bvg_pagerank (Eq. (1) reaches the same fixed point from any start; the
+ * paper has no learned part). May grow the graph's scratch. Asynchronous on
+ * `stream`. Errors: INVALID_ARG, OOM, CUDA. */
 int bvg_warmstart_predict(const bvg_mlp* net, const bvg_dev_graph* g, float* p_init, void* stream);
 void bvg_free_mlp(bvg_mlp* net);
 
@@ -442,16 +449,18 @@ typedef struct {
 } bvg_launch_config;
 /* The graph's configuration into *out. Errors: INVALID_ARG. */
 int bvg_get_config(const bvg_dev_graph* g, bvg_launch_config* out);
-/* Applies *in (each field in the range its comment gives, else INVALID_ARG;
- * a new pull_item or prefix_min_len rebuilds the pull's work items: OOM,
- * CUDA). */
+/* Applies *in; a new pull_item or prefix_min_len rebuilds the pull's work
+ * items. Errors: INVALID_ARG (a field outside the range its comment gives),
+ * OOM, CUDA. */
 int bvg_set_config(bvg_dev_graph* g, const bvg_launch_config* in);
 
-/* Autotuner. Times the products of g with k right-hand sides under each
- * candidate launch configuration (CUDA events on `stream`, median of 7 after
- * 2 warm-up calls, warm caches): first the push (x A) over the widest column
- * block (the largest power of two <= min(k, 32) and up to three halvings)
- * times gather overlap on/off times event or point columns, and for one
+/* Autotuner (the paper has no counterpart; its products and results are
+ * those of Sec. 4 under every setting). Times the products of g with k
+ * right-hand sides under each candidate launch configuration (CUDA events
+ * on `stream`, median of 7 after 2 warm-up calls, warm caches): first the
+ * push (x A) over the widest column block (the largest power of two
+ * <= min(k, 32) and up to three halvings) times gather overlap on/off
+ * times event or point columns, and for one
  * right-hand side the one-launch x A kernel too; then the pull (A x^T): for
  * one right-hand side the one-launch kernel where the graph fits it, and
  * the two-kernel pull over entries per work item {4, 8, 16} times rows per
@@ -576,7 +585,8 @@ int bvg_biclique_upload(const bvg_biclique* b, void* stream, bvg_biclique_dev** 
 int bvg_biclique_spmv_Ax(const bvg_biclique_dev* d, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 /* y = x A, the transpose of the same steps: d_r = sum_{i in S_r} x_i, then
  * y_j = sum of d_r over the bicliques whose C holds j, plus x_i over the
- * residual edges into column j. As bvg_biclique_spmv_Ax otherwise. */
+ * residual edges into column j. As bvg_biclique_spmv_Ax otherwise. Errors:
+ * as bvg_biclique_spmv_Ax. */
 int bvg_biclique_spmv_xA(const bvg_biclique_dev* d, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 void bvg_free_biclique_dev(bvg_biclique_dev* d);
 
@@ -601,10 +611,13 @@ typedef struct {
     int64_t slot_bytes;   /* device bytes of one slot (the largest image) */
     int64_t image_bytes;  /* page-locked bytes of all images */
 } bvg_stream_info_t;
+/* Creates the streamed encoding described above; *out is owned by the caller
+ * (bvg_free_stream). Errors: INVALID_ARG, BAD_GRAPH, UNSUPPORTED, OOM, CUDA. */
 int bvg_stream_create(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t budget_bytes, int32_t left,
                       const bvg_encode_params* params, bvg_stream** out);
-/* y = M x^T (x A when the stream was created with left = 1), x, y device
- * n x k of leading dimension ld: the blocks in order, each image copied on a
+/* y = M x^T (x A when the stream was created with left = 1; the pull of
+ * Sec. 4 on each row block), x, y device n x k of leading dimension ld: the
+ * blocks in order, each image copied on a
  * private copy stream into one of two device slots while the pull kernels of
  * the previous block run on `stream` (the slot's next copy waits for the
  * kernels that read it); every column of x is served before the next block
@@ -632,7 +645,7 @@ int bvg_csr_upload(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, vo
  * Errors: INVALID_ARG, CUDA. */
 int bvg_csr_spmv_Ax(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 /* y = x A over the CSR of A^T (same kernel, transposed pattern). As
- * bvg_csr_spmv_Ax otherwise. */
+ * bvg_csr_spmv_Ax otherwise. Errors: INVALID_ARG, CUDA. */
 int bvg_csr_spmv_xA(const bvg_csr_graph* g, const float* x, float* y, int32_t k, int64_t ld, void* stream);
 /* The same two products by the vendor library (cusparseSpMV for one
  * right-hand side with ld = 1, cusparseSpMM on the row-major n x k block
